@@ -1,0 +1,293 @@
+"""FP64 CPU oracle for the RBF neural-field method (Shaw, Kilpatrick & Avitabile).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library and never imports it.
+
+The arithmetic lives in ``nf_oracle.c`` (plain C, double precision, no contraction);
+this module only marshals numpy arrays through ctypes.  Each function cites the
+paper passage it follows:
+
+* :func:`knn`              §3.1 stencil of an element: k nearest nodes to its centre
+* :func:`tri_r3`, :func:`tri_mono`   §3.2 analytic integrals of the basis over a triangle
+* :func:`element_weights_local`      §3.2 Eqs. (3.4)-(3.5) one element's RBF-QF weights
+* :func:`quad_weights`     §3.2 Eq. (3.5) node weights (flat), §3.3 Eq. (3.6) (surfaces)
+* :func:`nonlocal_sum`     §2.2 Eq. (2.9) I_i = sum_j w(x_i, x_j) mu_j f(u_j)
+* :func:`rk4`              classical RK4 on Eq. (2.9)
+* :func:`adjoint`          discrete adjoint of that RK4 map
+* :func:`mms_sphere_eigs`  Funk-Hecke eigenvalues for the manufactured solution (§4, Eq. (4.5))
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.or_knn.argtypes = [_dp, C.c_int64, C.c_int, _ip, C.c_int64, _lp, C.c_int64, C.c_int, _ip]
+        L.or_tri_r3.argtypes = [_dp, _dp]
+        L.or_tri_r3.restype = C.c_double
+        L.or_tri_mono.argtypes = [C.c_int, C.c_int, _dp]
+        L.or_tri_mono.restype = C.c_double
+        L.or_element_weights_local.argtypes = [_dp, C.c_int, _dp, C.c_int, _dp]
+        L.or_quad_weights.argtypes = [_dp, _dp, C.c_int64, C.c_int, _ip, C.c_int64, _ip, C.c_int, C.c_int,
+                                      _dp, _dp, _lp]
+        L.or_tri_neighbors.argtypes = [_ip, C.c_int64, _lp]
+        L.or_projection_point.argtypes = [_dp, _dp, _ip, _lp, C.c_int64, _dp]
+        L.or_surface_element_weights.argtypes = [_dp, _dp, _ip, _lp, C.c_int64, _ip, C.c_int, C.c_int, _dp, _dp,
+                                                 C.POINTER(C.c_int)]
+        L.or_nonlocal.argtypes = [_dp, _dp, C.c_int64, _dp, C.c_int, _dp, _dp, _dp, _lp, C.c_int64, _dp]
+        L.or_rk4.argtypes = [_dp, _dp, C.c_int64, _dp, C.c_int, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp,
+                             _dp, _dp]
+        L.or_adjoint.argtypes = [_dp, _dp, C.c_int64, _dp, C.c_int, C.c_double, C.c_double, C.c_int, _dp, _dp,
+                                 _dp, _dp, _dp, _dp, _dp]
+        L.or_loss.argtypes = [_dp, _dp, C.c_int64, _dp, C.c_int, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp,
+                              _dp, _dp]
+        L.or_loss.restype = C.c_double
+        L.or_mms_sphere_eigs.argtypes = [_dp, _dp]
+        L.or_mms_sphere_solution.argtypes = [_dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                             C.c_double, _dp]
+        L.or_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+def _i64(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(_lp)
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+# ---------------------------------------------------------------------------- §3.1
+
+def knn(nodes, tris, k, elems=None):
+    """Stencils S(E): for each element (or each of ``elems``) the k nodes nearest to its
+    centroid, ordered by (squared distance, index) ascending.  nodes: n x dim."""
+    nodes, pn = _d(nodes)
+    n, dim = nodes.shape
+    tris, pt = _i32(tris)
+    m = tris.shape[0]
+    if elems is None:
+        ne, pe = m, None
+    else:
+        elems, pe = _i64(elems)
+        ne = elems.shape[0]
+    out = np.empty((ne, k), dtype=np.int32)
+    rc = lib().or_knn(pn, n, dim, pt, m, pe, ne, k, out.ctypes.data_as(_ip))
+    if rc != 0:
+        raise ValueError("or_knn: bad arguments")
+    return out
+
+
+# ---------------------------------------------------------------------------- §3.2
+
+def tri_r3(p, tri):
+    """Integral over the planar triangle ``tri`` (3 x 2) of |x - p|^3."""
+    p, pp = _d(p)
+    tri, pt = _d(tri)
+    return float(lib().or_tri_r3(pp, pt))
+
+
+def tri_mono(a, b, tri):
+    """Integral over the planar triangle ``tri`` (3 x 2) of x^a y^b."""
+    tri, pt = _d(tri)
+    return float(lib().or_tri_mono(int(a), int(b), pt))
+
+
+def element_weights_local(xi, tri, deg):
+    """RBF-QF weights of one element in its own (scaled) coordinates, Eq. (3.5)."""
+    xi, px = _d(xi)
+    tri, pt = _d(tri)
+    k = xi.shape[0]
+    w = np.empty(k)
+    rc = lib().or_element_weights_local(px, k, pt, int(deg), w.ctypes.data_as(_dp))
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"singular element system (rc={rc})")
+    return w
+
+
+def tri_neighbors(tris):
+    tris, pt = _i32(tris)
+    nbr = np.empty((tris.shape[0], 3), dtype=np.int64)
+    lib().or_tri_neighbors(pt, tris.shape[0], nbr.ctypes.data_as(_lp))
+    return nbr
+
+
+def projection_point(nodes, normals, tris, nbr, e):
+    """Projection point p_E of §3.3 (None when the cutting planes are near parallel)."""
+    nodes, pn = _d(nodes)
+    normals, pN = _d(normals)
+    tris, pt = _i32(tris)
+    nbr, pb = _i64(nbr)
+    p = np.empty(3)
+    ok = lib().or_projection_point(pn, pN, pt, pb, int(e), p.ctypes.data_as(_dp))
+    return p if ok else None
+
+
+def surface_element_weights(nodes, normals, tris, nbr, e, stencil, deg):
+    """Weights (including the Jacobian of mu_E) and Jacobians of one surface element."""
+    nodes, pn = _d(nodes)
+    normals, pN = _d(normals)
+    tris, pt = _i32(tris)
+    nbr, pb = _i64(nbr)
+    sten, ps = _i32(stencil)
+    k = sten.shape[0]
+    w = np.empty(k)
+    jac = np.empty(k)
+    central = C.c_int(0)
+    rc = lib().or_surface_element_weights(pn, pN, pt, pb, int(e), ps, k, int(deg), w.ctypes.data_as(_dp),
+                                          jac.ctypes.data_as(_dp), C.byref(central))
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"singular element system (rc={rc})")
+    return w, jac, bool(central.value)
+
+
+def quad_weights(nodes, tris, stencils, deg, normals=None, return_elem=False):
+    """Quadrature weights mu_j (Eq. (3.5) flat, §3.3 surfaces).  nodes: n x dim."""
+    nodes, pn = _d(nodes)
+    n, dim = nodes.shape
+    tris, pt = _i32(tris)
+    st, ps = _i32(stencils)
+    m, k = st.shape
+    if normals is not None:
+        normals, pN = _d(normals)
+    else:
+        pN = None
+    q = np.empty(n)
+    W = np.empty((m, k))
+    bad = C.c_int64(-1)
+    rc = lib().or_quad_weights(pn, pN, n, dim, pt, m, ps, k, int(deg), q.ctypes.data_as(_dp),
+                               W.ctypes.data_as(_dp), C.byref(bad))
+    if rc < 0:
+        raise ValueError("or_quad_weights: bad arguments")
+    if rc > 0:
+        raise np.linalg.LinAlgError(f"singular element system at element {bad.value}")
+    return (q, W) if return_elem else q
+
+
+# ---------------------------------------------------------------------------- §2.2
+
+def nonlocal_sum(x, q, u, kernel, beta, theta, rows=None):
+    """I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]) for all rows (or ``rows``).
+    x: n x 3, u: B x n (or n), kernel: (A1, s1, A2, s2)."""
+    x, px = _d(x)
+    q, pq = _d(q)
+    u = np.atleast_2d(u)
+    u, pu = _d(u)
+    B, n = u.shape
+    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
+    th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
+    if rows is None:
+        I = np.empty((B, n))
+        lib().or_nonlocal(px, pq, n, pu, B, pk, pbe, pth, None, 0, I.ctypes.data_as(_dp))
+    else:
+        rows, pr = _i64(rows)
+        I = np.empty((B, rows.shape[0]))
+        lib().or_nonlocal(px, pq, n, pu, B, pk, pbe, pth, pr, rows.shape[0], I.ctypes.data_as(_dp))
+    return I
+
+
+def _forcing_arr(forcing):
+    if forcing is None:
+        return None, None
+    f = np.asarray([forcing["kind"], forcing["c"], forcing["a0"], *forcing["lam"]], dtype=np.float64)
+    return _d(f)
+
+
+def rk4(x, q, u0, kernel, beta, theta, t0, dt, nsteps, forcing=None, return_stages=False):
+    """Classical RK4 for Eq. (2.9); returns u(t0 + nsteps dt) (B x n)."""
+    x, px = _d(x)
+    q, pq = _d(q)
+    u = np.array(np.atleast_2d(u0), dtype=np.float64, order="C")
+    B, n = u.shape
+    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
+    th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
+    f, pf = _forcing_arr(forcing)
+    st = np.empty((nsteps, 4, B, n)) if return_stages else None
+    lib().or_rk4(px, pq, n, u.ctypes.data_as(_dp), B, t0, dt, nsteps, pk, pbe, pth, pf,
+                 st.ctypes.data_as(_dp) if st is not None else None)
+    return (u, st) if return_stages else u
+
+
+def adjoint(x, q, u0, kernel, beta, theta, t0, dt, nsteps, lam_T, forcing=None):
+    """Discrete RK4 adjoint: returns (dL/du0 (B x n), dL/d(A1,s1,A2,s2) (B x 4))."""
+    x, px = _d(x)
+    q, pq = _d(q)
+    u0 = np.atleast_2d(u0)
+    u0, pu = _d(u0)
+    B, n = u0.shape
+    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
+    th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
+    f, pf = _forcing_arr(forcing)
+    lam, pl = _d(np.atleast_2d(lam_T))
+    gu = np.empty((B, n))
+    gk = np.empty((B, 4))
+    lib().or_adjoint(px, pq, n, pu, B, t0, dt, nsteps, pk, pbe, pth, pf, pl, gu.ctypes.data_as(_dp),
+                     gk.ctypes.data_as(_dp))
+    return gu, gk
+
+
+def loss(x, q, u0, kernel, beta, theta, t0, dt, nsteps, target, forcing=None):
+    """L = sum (u_N - target)^2 after nsteps RK4 steps."""
+    x, px = _d(x)
+    q, pq = _d(q)
+    u0 = np.atleast_2d(u0)
+    u0, pu = _d(u0)
+    B, n = u0.shape
+    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
+    th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
+    f, pf = _forcing_arr(forcing)
+    tg, ptg = _d(np.atleast_2d(target))
+    return float(lib().or_loss(px, pq, n, pu, B, t0, dt, nsteps, pk, pbe, pth, pf, ptg))
+
+
+def mms_sphere_eigs(kernel):
+    """Funk-Hecke eigenvalues (lambda_0, lambda_1, lambda_2) of the radial kernel on the
+    unit sphere, by composite Gauss-Legendre quadrature."""
+    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    lam = np.empty(3)
+    lib().or_mms_sphere_eigs(pk, lam.ctypes.data_as(_dp))
+    return lam
+
+
+def mms_sphere_forcing(kernel, c=0.5, a0=0.3):
+    """Forcing descriptor for the manufactured sphere solution (kind 1)."""
+    return {"kind": 1, "c": c, "a0": a0, "lam": tuple(mms_sphere_eigs(kernel))}
+
+
+def mms_sphere_solution(x, t, beta, theta, c=0.5, a0=0.3):
+    x, px = _d(x)
+    u = np.empty(x.shape[0])
+    lib().or_mms_sphere_solution(px, x.shape[0], t, c, a0, beta, theta, u.ctypes.data_as(_dp))
+    return u
