@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the RBF neural-field hot path on one GB300.
+
+Workload (the precision configuration): torus R = 1, r = 0.4 with n = 100,000
+jittered spiral-lattice nodes, k = 48 stencils, PHS r^3 + degree-4 polynomials,
+Mexican-hat kernel (1, 0.1, 0.5, 0.2), sigmoid beta = 50, theta = 0.2, six bumps as
+u0, RK4 with dt = 0.05, one trajectory.  Stencils and quadrature weights are built
+on the GPU first (setup, not timed in `value`).
+
+A step is one RK4 step (four stages, each: nonlocal sum of Eq. (2.9) over all
+n^2 pairs + fused stage update).  `value` is pair evaluations per second
+(4 n^2 per step) of the fastest path; every path is reported under `paths`:
+  mf          matrix-free FP32 pair kernel (TMA-staged tiles, SFU exponentials)
+  dense_fp32  precomputed W diag(q) in FP32, HBM-streamed GEMV
+  bf16x2      precomputed W diag(q)/s_i as bf16 hi + lo planes, FP32 accumulate
+Timing: CUDA events on the launching stream around each step, L2 flushed (a
+256 MiB write) between timed steps; the dominant kernel is timed live by events
+captured around it inside the step graph.  With --gpus N under torchrun every rank
+runs an independent replica (the single-trajectory path does not shard without a
+per-stage all-gather), value = all ranks' pairs / max time ("weak" scaling).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload: a step is one nonlocal stage over a row sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PATHS = {"mf": 0, "dense_fp32": 1, "bf16x2": 2}
+METRIC = "pair-evals/s & RK4 steps/s at N=1e5, mixed/batched vs plain FP32, same GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--paths", default="mf,dense_fp32,bf16x2")
+    ap.add_argument("--n", type=int, default=100000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while a region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [r[0] for r in rows]
+        mx = max(r[1] for r in rows)
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        out.update(sm_mhz=float(np.median(loaded)), sm_max_mhz=mx, reasons=reasons, samples=len(rows))
+        return out
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# MUFU.EX2 lane-ops per clock per SM (measured: see the pair-kernel profile summary)
+EX2_PER_CLK_SM = 16.0
+
+
+def run_reference(args, rank, world):
+    """FP64 CPU oracle on bounded row samples of the same workload."""
+    import oracle
+    from nodesets import workloads as W
+
+    if rank != 0:
+        return None
+    wl = W.precision(args.n)
+    x = wl.ns.nodes.astype(np.float32).astype(np.float64)
+    q = np.full(wl.n, wl.ns.area / wl.n)
+    u = wl.u0.astype(np.float32).astype(np.float64)
+    kern = tuple(float(np.float32(v)) for v in wl.kernel)
+    rng = np.random.default_rng(0)
+    # calibrate a row sample to about (cpu-seconds / steps) per step
+    t = time.perf_counter()
+    oracle.nonlocal_sum(x, q, u, kern, wl.beta, wl.theta, rows=np.arange(32))
+    per_row = (time.perf_counter() - t) / 32
+    budget = max(1.0, args.cpu_seconds * 2 / max(1, args.steps + args.warmup))
+    rows_per_step = int(min(wl.n, max(16, budget / per_row)))
+    for _ in range(args.warmup):
+        oracle.nonlocal_sum(x, q, u, kern, wl.beta, wl.theta, rows=rng.choice(wl.n, rows_per_step, replace=False))
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.nonlocal_sum(x, q, u, kern, wl.beta, wl.theta, rows=rng.choice(wl.n, rows_per_step, replace=False))
+    dt = time.perf_counter() - t
+    value = rows_per_step * wl.n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"precision torus n={wl.n}", "rows_per_step": rows_per_step, "B": 1},
+        "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{rows_per_step} random rows x {wl.n} columns of one nonlocal stage per step"},
+        "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+def cpu_baseline(wl, q, seconds):
+    import oracle
+
+    x = wl.ns.nodes.astype(np.float32).astype(np.float64)
+    u = wl.u0.astype(np.float32).astype(np.float64)
+    kern = tuple(float(np.float32(v)) for v in wl.kernel)
+    t = time.perf_counter()
+    oracle.nonlocal_sum(x, q, u, kern, wl.beta, wl.theta, rows=np.arange(32))
+    per_row = (time.perf_counter() - t) / 32
+    rows = int(min(wl.n, max(64, seconds / per_row)))
+    sel = np.random.default_rng(1).choice(wl.n, rows, replace=False)
+    t = time.perf_counter()
+    oracle.nonlocal_sum(x, q, u, kern, wl.beta, wl.theta, rows=sel)
+    dt = time.perf_counter() - t
+    return {"value": rows * wl.n / dt, "unit": "pair-evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one nonlocal stage on {rows} random rows x {wl.n} columns (FP64, {dt:.1f} s)"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2504_13379_gb300 as nf
+    from nodesets import workloads as W
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    wl = W.precision(args.n)
+    n = wl.n
+    # ---- setup on the GPU: stencils and quadrature weights (§3.1-3.3)
+    nodes = torch.as_tensor(wl.ns.nodes, device=dev)
+    tris = torch.as_tensor(wl.ns.tris, device=dev)
+    normals = torch.as_tensor(wl.ns.normals, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st = nf.nf_build_stencils(nodes, tris, wl.k)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    q = nf.nf_quad_weights(nodes, tris, st, wl.deg, normals=normals)
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    setup = {"stencils_ms": 1e3 * (t1 - t0), "weights_ms": 1e3 * (t2 - t1),
+             "sum_q_minus_area_rel": float((q.sum().item() - wl.ns.area) / wl.ns.area)}
+    x32 = torch.as_tensor(wl.ns.nodes.astype(np.float32), device=dev)
+    q32 = q.to(torch.float32).contiguous()
+    u0 = torch.as_tensor(wl.u0.astype(np.float32), device=dev)
+    beta, theta = float(wl.beta[0]), float(wl.theta[0])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    results = {}
+    clocks_all = []
+    launches_total = 0
+    for pname in [p for p in args.paths.split(",") if p]:
+        path = PATHS[pname]
+        torch.cuda.synchronize(dev)
+        tb = time.perf_counter()
+        op = nf.Operator(x32, q32, wl.kernel, path)
+        torch.cuda.synchronize(dev)
+        build_ms = 1e3 * (time.perf_counter() - tb)
+        op.profile(True)
+        u = u0.clone()
+        t_sim = 0.0
+        for _ in range(args.warmup):
+            nf.nf_rk4_advance(op, u, t_sim, wl.dt, 1, beta, theta)
+            t_sim += wl.dt
+        op.check()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(dev.index if dev.index is not None else 0)
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        kern_ms = 0.0
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            nf.nf_rk4_advance(op, u, t_sim, wl.dt, 1, beta, theta)
+            ev[k][1].record(stream)
+            t_sim += wl.dt
+            kern_ms += sum(op.kernel_ms())
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        clocks_all.append(clocks)
+        op.check()
+        step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        launches_per_step = 2 + 4 * 2  # prep + clock, then 4 x (nonlocal, stage) for one trajectory
+        launches_total += launches_per_step * args.steps
+        # ---- end to end through the public API with host buffers
+        uh = torch.empty_like(u, device="cpu").pin_memory()
+        uh.copy_(u0.cpu())
+        uo = torch.empty_like(uh).pin_memory()
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            e2e_ev[k][0].record(stream)
+            u.copy_(uh, non_blocking=True)
+            nf.nf_rk4_advance(op, u, t_sim, wl.dt, 1, beta, theta)
+            uo.copy_(u, non_blocking=True)
+            e2e_ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+        res = {"ms_per_step": step_ms, "rk4_steps_per_s": 1e3 / step_ms,
+               "pair_evals_per_s": 4.0 * n * n / (step_ms * 1e-3),
+               "kernel_ms_per_launch": kern_ms / (4 * args.steps), "build_ms": build_ms,
+               "e2e_ms_per_step": e2e_ms, "clocks": clocks}
+        results[pname] = res
+        op.close()
+        del op
+        torch.cuda.empty_cache()
+    # ---- aggregate over ranks (max time)
+    best = min(results, key=lambda p: results[p]["ms_per_step"])
+    r = results[best]
+    step_ms = r["ms_per_step"]
+    e2e_ms = r["e2e_ms_per_step"]
+    if world > 1:
+        t = torch.tensor([step_ms, e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms, e2e_ms = float(t[0]), float(t[1])
+    value = world * 4.0 * n * n / (step_ms * 1e-3)
+    pk = peaks()
+    clocks = r["clocks"]
+    kms = r["kernel_ms_per_launch"]
+    if best == "mf":
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks["sm_mhz"] or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 1432.0
+        peak = sms * EX2_PER_CLK_SM / 2.0 * mhz * 1e6 / 1e9          # Gpair/s: 2 SFU exponentials per pair
+        achieved = n * n / (kms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
+                "traffic": None, "peak_basis": f"{sms} SMs x {EX2_PER_CLK_SM:g} MUFU.EX2/clk/SM / 2 per pair x "
+                                               f"{mhz:.0f} MHz (median SM clock in the timed region)"}
+    else:
+        bytes_per = 4.0 * n * n
+        achieved = bytes_per / (kms * 1e-3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_basis": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"precision torus R=1 r=0.4 n={n} k={wl.k} deg={wl.deg}, B=1, RK4 dt={wl.dt}",
+                   "path": best, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "rk4_steps_per_s": world * 1e3 / step_ms,
+        "paths": results,
+        "setup": setup,
+        "roofline": roof,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        "e2e": {"value": world * 4.0 * n * n / (e2e_ms * 1e-3), "unit": "pair-evals/s",
+                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": launches_total,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, q.double().cpu().numpy(), args.cpu_seconds)
+    return line if rank == 0 else None
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * nf.h -- C ABI of the GB300 (sm_103a) library for the RBF neural-field method of
+ * Shaw, Kilpatrick & Avitabile, "Radial Basis Function Techniques for Neural Field
+ * Models on Surfaces".
+ *
+ * The problem (§2, Eq. (2.1)): du/dt = -u + g + int_D w(x, y) f(u(y)) dmu(y) on a
+ * node set Xi with a triangulation {E_j}, discretised as the fully discrete
+ * collocation scheme of §2.2, Eq. (2.9):
+ *     alpha_i' = -alpha_i + sum_j w(x_i, x_j) mu_j f(alpha_j) + gamma_i(t),
+ * whose weights mu_j come from RBF quadrature (§3.2 Eq. (3.5), §3.3 Eq. (3.6)).
+ *
+ * Conventions, for every entry point:
+ *  - Return value: nf_status.  NF_OK on success; on failure a thread-local message is
+ *    available from nf_last_error().  The library never aborts, traps or exits.
+ *  - Array arguments are DEVICE pointers (e.g. torch CUDA tensor data pointers),
+ *    contiguous, row-major, owned by the caller; outputs are allocated by the caller.
+ *    Arguments documented as "host" are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *    work is ordered on that stream.  Calls return once the work is enqueued, except
+ *    where a call documents that it synchronises the stream.
+ *  - The library owns only what lives inside an nf_operator handle (packed node
+ *    arrays, dense operator planes, partial-sum workspace, CUDA graphs) and frees it
+ *    in nf_operator_destroy.  Temporary setup workspace is stream-ordered
+ *    (cudaMallocAsync) and released before the call returns its work.
+ *  - Asynchronous device faults surface as NF_ERR_CUDA at the next call.
+ */
+#ifndef NF_H
+#define NF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NF_API __attribute__((visibility("default")))
+#else
+#define NF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NF_OK = 0,
+    NF_ERR_ARG = 1,          /* invalid argument (null pointer, size, alignment, rule of §3.1) */
+    NF_ERR_SINGULAR = 2,     /* an element's interpolation system is singular (§3.1) */
+    NF_ERR_NONFINITE = 3,    /* non-finite input or result detected */
+    NF_ERR_TIMEOUT = 4,      /* a bounded device wait gave up; the kernel returned early */
+    NF_ERR_NOMEM = 5,        /* device allocation failed */
+    NF_ERR_CUDA = 6,         /* CUDA runtime / launch error */
+    NF_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+} nf_status;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+NF_API const char *nf_last_error(void);
+
+/* ABI version, (major << 16) | minor. */
+NF_API int nf_version(void);
+
+/* ------------------------------------------------------------------------------
+ * §3.1 stencils.  For each element E_e (a triangle of the caller's triangulation),
+ * S(E_e) = the k nodes nearest to the centre of E_e.  The centre is the centroid
+ * ((a + b) + c) / 3; distance is Euclidean in R^dim (§4: "standard Euclidean
+ * distance ... for stencil selection").  Ties are broken by node index, so the
+ * result is unique: row e lists node indices in ascending (distance^2, index).
+ *
+ *   nodes     n x dim   FP64   node coordinates, dim in {2, 3}
+ *   tris      m x 3     int32  element vertex indices (0-based, < n)
+ *   k                          stencil size, 1 <= k <= min(n, 128)
+ *   stencils  m x k     int32  output
+ * Errors: NF_ERR_ARG (sizes, k), NF_ERR_CUDA.  Distances are evaluated in FP64
+ * without contraction, so indices agree bit-for-bit with a plain FP64 evaluation.
+ * ---------------------------------------------------------------------------- */
+NF_API nf_status nf_build_stencils(const double *nodes, int64_t n, int dim,
+                            const int32_t *tris, int64_t m, int k,
+                            int32_t *stencils, void *stream);
+
+/* ------------------------------------------------------------------------------
+ * §3.2 Eq. (3.5) (flat, dim = 2) and §3.3 Eq. (3.6) (closed surfaces, dim = 3):
+ * RBF quadrature weights mu (written q here).  Per element: polyharmonic spline
+ * r^3 (§3.1 Eq. (3.3), ell = 3) plus polynomials of total degree <= deg, the saddle
+ * system of Eq. (3.4) with the analytic integrals of each basis function over the
+ * element as right-hand side; node weight = sum of the element weights of every
+ * stencil containing the node.  On surfaces the stencil is first mapped to the
+ * element's plane by the central projection through the projection point p_E
+ * (three cutting planes, §3.3) and each weight is multiplied by the Jacobian of
+ * mu_E at the projected node (the area factor of Eq. (3.6)).
+ *
+ *   nodes     n x dim   FP64   node coordinates
+ *   normals   n x 3     FP64   outward unit node normals (dim 3); NULL when dim = 2
+ *   tris      m x 3     int32  triangulation (closed and edge-manifold when dim = 3)
+ *   stencils  m x k     int32  from nf_build_stencils
+ *   deg                        appended polynomial degree, 0..4, with
+ *                              (deg+1)(deg+2)/2 <= k (unisolvency, §3.1)
+ *   q         n         FP64   output weights
+ *   bad_element  host int64*   set to the first singular element, or -1 (may be NULL)
+ * Synchronises `stream` (it must report per-element failures).
+ * Errors: NF_ERR_ARG, NF_ERR_SINGULAR (q undefined), NF_ERR_NOMEM, NF_ERR_CUDA.
+ * ---------------------------------------------------------------------------- */
+NF_API nf_status nf_quad_weights(const double *nodes, const double *normals, int64_t n, int dim,
+                          const int32_t *tris, int64_t m, const int32_t *stencils, int k,
+                          int deg, double *q, int64_t *bad_element, void *stream);
+
+/* ------------------------------------------------------------------------------
+ * Kernel and operator.
+ * Lateral-inhibition ("Mexican hat") kernel, §5 Eq. (5.1) in unnormalised form:
+ *     w(r) = A1 exp(-r^2 / s1^2) - A2 exp(-r^2 / s2^2),   r = |x_i - x_j| (Euclidean,
+ * chord distance on surfaces).  Firing rate §4 Eq. (4.4):
+ *     f(u) = 1 / (1 + exp(-beta (u - theta))), per-trajectory beta, theta.
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+    float A1, s1, A2, s2;
+} nf_kernel;
+
+typedef enum {
+    NF_MATRIX_FREE = 0,   /* pair sum evaluated on the fly every stage (FP32) */
+    NF_DENSE_FP32 = 1,    /* W diag(q) precomputed once, FP32, streamed every stage */
+    NF_DENSE_BF16X2 = 2   /* W diag(q) / s_i stored as bf16 hi + bf16 lo, FP32 accumulate */
+} nf_path;
+
+typedef struct nf_operator nf_operator;
+
+/* Create the operator I = W diag(q) f(.) of Eq. (2.9) on n nodes.
+ *   x   n x 3  FP32  node coordinates (z = 0 for flat domains)
+ *   q   n      FP32  quadrature weights mu_j
+ *   path             nf_path; dense paths allocate n x n (FP32: 4 n^2 bytes; BF16X2:
+ *                    4 n^2 bytes + 4 n) inside the handle and build it on `stream`.
+ *   op  host         receives the handle.
+ * x and q are copied into the handle; the caller may free them afterwards.
+ * Errors: NF_ERR_ARG, NF_ERR_NOMEM, NF_ERR_CUDA. */
+NF_API nf_status nf_operator_create(const float *x, const float *q, int64_t n, nf_kernel kp,
+                             int path, void *stream, nf_operator **op);
+
+NF_API nf_status nf_operator_destroy(nf_operator *op);
+
+/* Synchronise `stream` and report device-side failures recorded on the operator
+ * (NF_ERR_TIMEOUT when a bounded wait in a kernel gave up).  Clears nothing. */
+NF_API nf_status nf_operator_check(nf_operator *op, void *stream);
+
+/* Measurement helpers.  With profiling enabled, the captured RK4 step records CUDA
+ * events immediately before and after each stage's nonlocal-sum launches (the
+ * dominant kernels); nf_operator_kernel_ms waits for the most recent step and returns
+ * the four stage durations in milliseconds (host float[4]). */
+NF_API nf_status nf_operator_profile(nf_operator *op, int enable);
+NF_API nf_status nf_operator_kernel_ms(nf_operator *op, float *ms);
+
+/* Nonlocal sum of Eq. (2.9) for B trajectories:
+ *     I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]).
+ *   u      B x n  FP32   states (trajectory-major)
+ *   beta, theta   B FP32 device arrays
+ *   I      B x n  FP32   output
+ * Errors: NF_ERR_ARG, NF_ERR_CUDA. */
+NF_API nf_status nf_nonlocal_apply(nf_operator *op, const float *u, int B, const float *beta,
+                            const float *theta, float *I, void *stream);
+
+/* Forcing gamma(t) of Eq. (2.9).
+ *  NF_FORCE_NONE: gamma = 0.
+ *  NF_FORCE_MMS_EIGEN: the manufactured-solution technique of §4 Eq. (4.5) with two
+ *    eigenfunctions of the integral operator, W Y1 = lam1 Y1, W Y2 = lam2 Y2, W 1 = lam0:
+ *      z = c + a(t) (Y1 + Y2),  a(t) = a0 cos t,  u* = theta + ln(z / (1 - z)) / beta,
+ *      gamma = d(u*)/dt + u* - [lam0 c + a(t) (lam1 Y1 + lam2 Y2)],
+ *    so that f(u*) = z solves the continuous problem exactly.  Y1, Y2: n FP32 device. */
+enum { NF_FORCE_NONE = 0, NF_FORCE_MMS_EIGEN = 1 };
+typedef struct {
+    int kind;
+    const float *Y1;
+    const float *Y2;
+    double c, a0, lam0, lam1, lam2;
+} nf_forcing;
+
+/* Funk-Hecke eigenvalues lam_l, l = 0, 1, 2, of the kernel w on the unit sphere
+ * (int_{S^2} w(|x - y|) Y_l(y) dS(y) = lam_l Y_l(x)), in closed form; host output
+ * lam[3].  For the manufactured forcing on the sphere (Y1 = z/2, Y2 = x y). */
+NF_API nf_status nf_mms_sphere_eigs(nf_kernel kp, double *lam);
+
+/* Classical RK4 on Eq. (2.9), nsteps steps of size dt from t0, in place:
+ *     k_s = -U_s + I(U_s) + gamma(t_s),   u <- u + dt/6 (k1 + 2 k2 + 2 k3 + k4).
+ *   u      B x n FP32  in/out
+ *   beta, theta  B FP32 device
+ *   g      host pointer to nf_forcing, or NULL
+ *   ckpt   ((nsteps / C) + 1) x B x n FP32 device, or NULL: receives u at steps
+ *          0, C, 2C, ... (checkpoints for nf_adjoint)
+ * The step sequence is captured once in a CUDA graph and replayed.
+ * Errors: NF_ERR_ARG, NF_ERR_CUDA. */
+NF_API nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt, int nsteps,
+                         const float *beta, const float *theta, const nf_forcing *g,
+                         float *ckpt, int C, void *stream);
+
+/* Discrete adjoint of nf_rk4_advance for a terminal loss L(u_N):
+ *   lambda_T  B x n FP32   dL/du_N
+ *   ckpt      checkpoints written by nf_rk4_advance with the same arguments
+ *   grad_u0   B x n FP32   output dL/du_0
+ *   grad_kernel B x 4 FP32 output dL/d(A1, s1, A2, s2), per trajectory
+ * Stages are recomputed segment by segment from the checkpoints.  The transposed pair
+ * sum uses the symmetry of the radial kernel (W^T = W).
+ * Errors: NF_ERR_ARG, NF_ERR_UNSUPPORTED (dense operators), NF_ERR_CUDA. */
+NF_API nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B, double t0, double dt,
+                     int nsteps, const float *beta, const float *theta, const nf_forcing *g,
+                     const float *lambda_T, float *grad_u0, float *grad_kernel, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NF_H */

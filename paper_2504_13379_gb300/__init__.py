@@ -1,0 +1,266 @@
+"""GB300 (sm_103a) implementation of the RBF neural-field hot path of Shaw,
+Kilpatrick & Avitabile, "Radial Basis Function Techniques for Neural Field Models on
+Surfaces".
+
+This module is a thin ctypes binding over the C-ABI library ``libnf.so``
+(declared in ``include/nf.h``).  It only marshals torch CUDA tensors (pointers,
+sizes, the current stream) into those calls; every step of the computation runs in
+the library's CUDA kernels.  If the library is missing or cannot be loaded, every
+entry point raises -- there is no CPU fallback.
+
+Entry points (same names as the C ABI):
+
+* :func:`nf_build_stencils`  §3.1 stencils S(E)
+* :func:`nf_quad_weights`    §3.2 Eq. (3.5) / §3.3 Eq. (3.6) quadrature weights
+* :class:`Operator`          W diag(q) of Eq. (2.9): ``nf_operator_create``
+* :func:`nf_nonlocal_apply`  I = sum_j w(x_i, x_j) q_j f(u_j)
+* :func:`nf_rk4_advance`     RK4 on Eq. (2.9)
+* :func:`nf_adjoint`         discrete adjoint of the RK4 map
+* :func:`nf_mms_sphere_eigs` Funk-Hecke eigenvalues for manufactured forcing
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "NFError", "lib", "build", "nf_build_stencils", "nf_quad_weights", "Operator", "nf_nonlocal_apply",
+    "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
+    "DENSE_BF16X2", "STATUS",
+]
+
+MATRIX_FREE, DENSE_FP32, DENSE_BF16X2 = 0, 1, 2
+STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINITE", 4: "NF_ERR_TIMEOUT",
+          5: "NF_ERR_NOMEM", 6: "NF_ERR_CUDA", 7: "NF_ERR_UNSUPPORTED"}
+
+# exported symbols declared in include/nf.h
+EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights", "nf_operator_create",
+           "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
+           "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms"]
+
+
+class NFError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{self.name}: {message}")
+
+
+class _Kernel(C.Structure):
+    _fields_ = [("A1", C.c_float), ("s1", C.c_float), ("A2", C.c_float), ("s2", C.c_float)]
+
+
+class _Forcing(C.Structure):
+    _fields_ = [("kind", C.c_int), ("Y1", C.c_void_p), ("Y2", C.c_void_p), ("c", C.c_double),
+                ("a0", C.c_double), ("lam0", C.c_double), ("lam1", C.c_double), ("lam2", C.c_double)]
+
+
+_lib = None
+_vp = C.c_void_p
+_i64 = C.c_int64
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def lib(path: str | None = None):
+    """Load ``libnf.so`` (building it if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not found at {path}")
+    L = C.CDLL(path)
+    L.nf_last_error.restype = C.c_char_p
+    L.nf_version.restype = C.c_int
+    for name in EXPORTS[2:]:
+        getattr(L, name).restype = C.c_int
+    L.nf_build_stencils.argtypes = [_vp, _i64, C.c_int, _vp, _i64, C.c_int, _vp, _vp]
+    L.nf_quad_weights.argtypes = [_vp, _vp, _i64, C.c_int, _vp, _i64, _vp, C.c_int, C.c_int, _vp,
+                                  C.POINTER(C.c_int64), _vp]
+    L.nf_operator_create.argtypes = [_vp, _vp, _i64, _Kernel, C.c_int, _vp, C.POINTER(_vp)]
+    L.nf_operator_destroy.argtypes = [_vp]
+    L.nf_operator_check.argtypes = [_vp, _vp]
+    L.nf_operator_profile.argtypes = [_vp, C.c_int]
+    L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
+    L.nf_nonlocal_apply.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]
+    L.nf_mms_sphere_eigs.argtypes = [_Kernel, C.POINTER(C.c_double)]
+    L.nf_rk4_advance.argtypes = [_vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp,
+                                 C.POINTER(_Forcing), _vp, C.c_int, _vp]
+    L.nf_adjoint.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp,
+                             C.POINTER(_Forcing), _vp, _vp, _vp, _vp]
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != 0:
+        raise NFError(st, lib().nf_last_error().decode(errors="replace"))
+
+
+def _stream(t: torch.Tensor | None = None):
+    dev = t.device if t is not None else None
+    return C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _dptr(t: torch.Tensor, dtype: torch.dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _kernel(kp) -> _Kernel:
+    A1, s1, A2, s2 = (float(v) for v in kp)
+    return _Kernel(A1, s1, A2, s2)
+
+
+# ------------------------------------------------------------------------ §3.1-3.3
+
+def nf_build_stencils(nodes: torch.Tensor, tris: torch.Tensor, k: int) -> torch.Tensor:
+    """k nearest nodes (ascending (d^2, index)) to each element centroid.
+    nodes: n x dim float64 CUDA, tris: m x 3 int32 CUDA -> m x k int32."""
+    n, dim = nodes.shape
+    m = tris.shape[0]
+    out = torch.empty((m, k), dtype=torch.int32, device=nodes.device)
+    _check(lib().nf_build_stencils(_dptr(nodes, torch.float64, "nodes"), n, dim, _dptr(tris, torch.int32, "tris"),
+                                   m, int(k), _dptr(out, torch.int32, "stencils"), _stream(nodes)))
+    return out
+
+
+def nf_quad_weights(nodes: torch.Tensor, tris: torch.Tensor, stencils: torch.Tensor, deg: int,
+                    normals: torch.Tensor | None = None) -> torch.Tensor:
+    """RBF-QF node weights (float64, n)."""
+    n, dim = nodes.shape
+    m, k = stencils.shape
+    q = torch.empty(n, dtype=torch.float64, device=nodes.device)
+    bad = C.c_int64(-1)
+    nptr = _dptr(normals, torch.float64, "normals") if normals is not None else None
+    _check(lib().nf_quad_weights(_dptr(nodes, torch.float64, "nodes"), nptr, n, dim, _dptr(tris, torch.int32, "tris"),
+                                 m, _dptr(stencils, torch.int32, "stencils"), k, int(deg),
+                                 _dptr(q, torch.float64, "q"), C.byref(bad), _stream(nodes)))
+    return q
+
+
+# ------------------------------------------------------------------------ operator
+
+class Forcing:
+    """Forcing descriptor: kind 0 (none) or 1 (manufactured, two eigenfunctions)."""
+
+    def __init__(self, kind=0, Y1=None, Y2=None, c=0.0, a0=0.0, lam=(0.0, 0.0, 0.0)):
+        self.kind, self.Y1, self.Y2, self.c, self.a0, self.lam = kind, Y1, Y2, c, a0, tuple(lam)
+
+    def _struct(self):
+        y1 = _dptr(self.Y1, torch.float32, "Y1").value if self.Y1 is not None else None
+        y2 = _dptr(self.Y2, torch.float32, "Y2").value if self.Y2 is not None else None
+        return _Forcing(int(self.kind), y1, y2, float(self.c), float(self.a0), *(float(v) for v in self.lam))
+
+
+class Operator:
+    """Owning handle for ``nf_operator`` (W diag(q) on n nodes, one of three paths)."""
+
+    def __init__(self, x: torch.Tensor, q: torch.Tensor, kernel, path: int = MATRIX_FREE):
+        self.n = int(x.shape[0])
+        self.kernel = tuple(float(v) for v in kernel)
+        self.path = int(path)
+        self.device = x.device
+        h = C.c_void_p()
+        _check(lib().nf_operator_create(_dptr(x, torch.float32, "x"), _dptr(q, torch.float32, "q"), self.n,
+                                        _kernel(kernel), self.path, _stream(x), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("operator destroyed")
+        return self._h
+
+    def profile(self, enable: bool = True):
+        """Record events around each stage's nonlocal kernels in captured RK4 steps."""
+        _check(lib().nf_operator_profile(self.handle, int(enable)))
+
+    def kernel_ms(self):
+        """Durations (ms) of the four stages' nonlocal kernels in the last RK4 step."""
+        out = (C.c_float * 4)()
+        _check(lib().nf_operator_kernel_ms(self.handle, out))
+        return list(out)
+
+    def check(self):
+        _check(lib().nf_operator_check(self.handle, _stream()))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            torch.cuda.synchronize(self.device)
+            lib().nf_operator_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _per_traj(v, B, device):
+    if isinstance(v, torch.Tensor):
+        return v.to(device=device, dtype=torch.float32).contiguous().expand(B).contiguous()
+    return torch.full((B,), float(v), dtype=torch.float32, device=device)
+
+
+def nf_nonlocal_apply(op: Operator, u: torch.Tensor, beta, theta, out: torch.Tensor | None = None) -> torch.Tensor:
+    """I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]); u: B x n float32 CUDA."""
+    u2 = u if u.dim() == 2 else u.view(1, -1)
+    B = u2.shape[0]
+    be, th = _per_traj(beta, B, u.device), _per_traj(theta, B, u.device)
+    I = out if out is not None else torch.empty_like(u2)
+    _check(lib().nf_nonlocal_apply(op.handle, _dptr(u2, torch.float32, "u"), B, _dptr(be, torch.float32, "beta"),
+                                   _dptr(th, torch.float32, "theta"), _dptr(I, torch.float32, "I"), _stream(u)))
+    return I if u.dim() == 2 else I.view(-1)
+
+
+def nf_rk4_advance(op: Operator, u: torch.Tensor, t0: float, dt: float, nsteps: int, beta, theta,
+                   forcing: Forcing | None = None, ckpt: torch.Tensor | None = None, C_every: int = 1):
+    """Advance u (B x n float32 CUDA, in place) by nsteps RK4 steps."""
+    u2 = u if u.dim() == 2 else u.view(1, -1)
+    B = u2.shape[0]
+    be, th = _per_traj(beta, B, u.device), _per_traj(theta, B, u.device)
+    f = C.byref(forcing._struct()) if forcing is not None else None
+    cp = _dptr(ckpt, torch.float32, "ckpt") if ckpt is not None else None
+    _check(lib().nf_rk4_advance(op.handle, _dptr(u2, torch.float32, "u"), B, float(t0), float(dt), int(nsteps),
+                                _dptr(be, torch.float32, "beta"), _dptr(th, torch.float32, "theta"), f, cp,
+                                int(C_every), _stream(u)))
+    # keep the per-trajectory arrays alive until the queued work has consumed them
+    op._keep = (be, th, forcing)
+    return u
+
+
+def nf_adjoint(op: Operator, ckpt: torch.Tensor, C_every: int, t0: float, dt: float, nsteps: int, beta, theta,
+               lambda_T: torch.Tensor, forcing: Forcing | None = None):
+    """Discrete RK4 adjoint: returns (dL/du0 (B x n), dL/d(A1,s1,A2,s2) (B x 4))."""
+    lam = lambda_T if lambda_T.dim() == 2 else lambda_T.view(1, -1)
+    B, n = lam.shape
+    be, th = _per_traj(beta, B, lam.device), _per_traj(theta, B, lam.device)
+    gu = torch.empty_like(lam)
+    gk = torch.empty((B, 4), dtype=torch.float32, device=lam.device)
+    f = C.byref(forcing._struct()) if forcing is not None else None
+    _check(lib().nf_adjoint(op.handle, _dptr(ckpt, torch.float32, "ckpt"), int(C_every), B, float(t0), float(dt),
+                            int(nsteps), _dptr(be, torch.float32, "beta"), _dptr(th, torch.float32, "theta"), f,
+                            _dptr(lam, torch.float32, "lambda_T"), _dptr(gu, torch.float32, "grad_u0"),
+                            _dptr(gk, torch.float32, "grad_kernel"), _stream(lam)))
+    op._keep = (be, th, forcing)
+    return gu, gk
+
+
+def nf_mms_sphere_eigs(kernel):
+    lam = (C.c_double * 3)()
+    _check(lib().nf_mms_sphere_eigs(_kernel(kernel), lam))
+    return tuple(lam)

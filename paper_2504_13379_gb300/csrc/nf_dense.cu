@@ -1,0 +1,237 @@
+// nf_dense.cu -- precomputed operator W diag(q) of Eq. (2.9) and its streaming
+// matrix-vector product.
+//
+// Build (once per operator): WQ[i, j] = w(|x_i - x_j|) q_j, row-major, leading
+// dimension n_pad (padded columns are zero because q is zero there).
+//   NF_DENSE_FP32:   FP32 plane.
+//   NF_DENSE_BF16X2: s_i = 2^ceil(log2 max_j |WQ_ij|) (a power of two, so dividing by
+//                    it is exact); hi = bf16_rn(WQ/s_i), lo = bf16_rn(WQ/s_i - hi).
+//                    hi + lo carries ~16 significant bits; I_i = s_i sum_j (hi+lo) F_j.
+// Apply (every stage): HBM-bound stream of 4 bytes per entry for either plane type.
+// Work items (32-row block, column split) write partial sums like the matrix-free
+// kernel, so the same stage kernel finishes the RK4 step.
+#include "nf_internal.cuh"
+
+#include <algorithm>
+
+namespace nfi {
+
+// ---------------------------------------------------------------- build
+__device__ __forceinline__ float mexhat(float r2, float A1, float is1, float A2, float is2) {
+    return A1 * expf(-r2 * is1) - A2 * expf(-r2 * is2);
+}
+
+// one block per row i; FP32 plane
+__global__ void dense_build_fp32_kernel(const float4 *__restrict__ x4, const float *__restrict__ q, int64_t n,
+                                        int64_t n_pad, float A1, float is1, float A2, float is2,
+                                        float *__restrict__ W) {
+    const int64_t i = blockIdx.x;
+    const float4 xi = x4[i];
+    float *row = W + i * n_pad;
+    for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x) {
+        const float4 xj = x4[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        row[j] = mexhat(r2, A1, is1, A2, is2) * q[j];
+    }
+}
+
+// one block per row: row scale s_i (power of two), then hi / lo planes
+__global__ void dense_build_bf16x2_kernel(const float4 *__restrict__ x4, const float *__restrict__ q, int64_t n,
+                                          int64_t n_pad, float A1, float is1, float A2, float is2,
+                                          uint16_t *__restrict__ Whi, uint16_t *__restrict__ Wlo,
+                                          float *__restrict__ rs) {
+    __shared__ float red[32];
+    const int64_t i = blockIdx.x;
+    const float4 xi = x4[i];
+    float mx = 0.f;
+    for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x) {
+        const float4 xj = x4[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        mx = fmaxf(mx, fabsf(mexhat(r2, A1, is1, A2, is2) * q[j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    mx = red[0];
+    // s = 2^e with mx <= s (frexp: mx = m 2^e, m in [0.5, 1))
+    int e = 0;
+    float s = 1.f;
+    if (mx > 0.f) {
+        (void)frexpf(mx, &e);
+        s = ldexpf(1.f, e);
+    }
+    const float inv = 1.f / s;  // exact: power of two
+    if (threadIdx.x == 0) rs[i] = s;
+    for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x) {
+        const float4 xj = x4[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float v = mexhat(r2, A1, is1, A2, is2) * q[j] * inv;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        Whi[i * n_pad + j] = __bfloat16_as_ushort(hi);
+        Wlo[i * n_pad + j] = __bfloat16_as_ushort(lo);
+    }
+}
+
+nf_status launch_dense_build(nf_operator *op, cudaStream_t s) {
+    const nf_kernel &k = op->kp;
+    const float is1 = 1.f / (k.s1 * k.s1), is2 = 1.f / (k.s2 * k.s2);
+    if (op->path == NF_DENSE_FP32) {
+        dense_build_fp32_kernel<<<(unsigned)op->n_pad, 256, 0, s>>>(op->x4, op->q, op->n, op->n_pad, k.A1, is1, k.A2,
+                                                               is2, op->W32);
+    } else {
+        dense_build_bf16x2_kernel<<<(unsigned)op->n_pad, 256, 0, s>>>(op->x4, op->q, op->n, op->n_pad, k.A1, is1,
+                                                                 k.A2, is2, op->Whi, op->Wlo, op->rs);
+    }
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+// ---------------------------------------------------------------- GEMV
+constexpr int DG_THREADS = 256;
+constexpr int DG_WARPS = DG_THREADS / 32;
+constexpr int DG_R = 4;                        // rows per warp
+constexpr int DG_ROWS = DG_WARPS * DG_R;       // rows per block
+constexpr int DG_TILE = 1024;                  // columns per inner tile
+static_assert(kNodePad % DG_TILE == 0, "tile must divide the node padding");
+
+__device__ __forceinline__ float4 ld_stream_f4(const float *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// FP32 plane.  Lane l of a warp covers columns tile + 4l + 128u, u = 0..7.
+__global__ void __launch_bounds__(DG_THREADS)
+gemv_fp32_kernel(const float *__restrict__ W, const float *__restrict__ F, int64_t n_pad, int B, int b,
+                 int64_t jchunk, float *__restrict__ partial) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = blockIdx.y;
+    const int64_t row0 = ((int64_t)blockIdx.x * DG_WARPS + warp) * DG_R;
+    const int64_t j0 = (int64_t)split * jchunk, j1 = min(n_pad, j0 + jchunk);
+    const float *Fb = F + (int64_t)b * n_pad;
+    float acc[DG_R] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t t = j0; t < j1; t += DG_TILE) {
+#pragma unroll
+        for (int uh = 0; uh < 8; uh += 4) {
+            float4 w[DG_R][4];
+#pragma unroll
+            for (int r = 0; r < DG_R; ++r)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    w[r][u] = ld_stream_f4(W + (row0 + r) * n_pad + t + 128 * (uh + u) + 4 * lane);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 f = __ldg(reinterpret_cast<const float4 *>(Fb + t + 128 * (uh + u) + 4 * lane));
+#pragma unroll
+                for (int r = 0; r < DG_R; ++r) {
+                    acc[r] = fmaf(w[r][u].x, f.x, acc[r]);
+                    acc[r] = fmaf(w[r][u].y, f.y, acc[r]);
+                    acc[r] = fmaf(w[r][u].z, f.z, acc[r]);
+                    acc[r] = fmaf(w[r][u].w, f.w, acc[r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < DG_R; ++r) {
+        const float v = warp_sum(acc[r]);
+        if (lane == 0) partial[((int64_t)split * B + b) * n_pad + row0 + r] = v;
+    }
+}
+
+// BF16 hi + lo planes.  Lane l covers columns tile + 8l + 256u, u = 0..3.
+__global__ void __launch_bounds__(DG_THREADS)
+gemv_bf16x2_kernel(const uint16_t *__restrict__ Whi, const uint16_t *__restrict__ Wlo, const float *__restrict__ F,
+                   int64_t n_pad, int B, int b, int64_t jchunk, float *__restrict__ partial) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = blockIdx.y;
+    const int64_t row0 = ((int64_t)blockIdx.x * DG_WARPS + warp) * DG_R;
+    const int64_t j0 = (int64_t)split * jchunk, j1 = min(n_pad, j0 + jchunk);
+    const float *Fb = F + (int64_t)b * n_pad;
+    float acc[DG_R] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t t = j0; t < j1; t += DG_TILE) {
+#pragma unroll
+        for (int uh = 0; uh < 4; uh += 2) {
+            uint4 h[DG_R][2], l[DG_R][2];
+#pragma unroll
+            for (int r = 0; r < DG_R; ++r)
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t off = (row0 + r) * n_pad + t + 256 * (uh + u) + 8 * lane;
+                    h[r][u] = ld_stream_u4(Whi + off);
+                    l[r][u] = ld_stream_u4(Wlo + off);
+                }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float *fp = Fb + t + 256 * (uh + u) + 8 * lane;
+                const float4 f0 = __ldg(reinterpret_cast<const float4 *>(fp));
+                const float4 f1 = __ldg(reinterpret_cast<const float4 *>(fp + 4));
+                const float fv[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+                for (int r = 0; r < DG_R; ++r) {
+                    const uint32_t hw[4] = {h[r][u].x, h[r][u].y, h[r][u].z, h[r][u].w};
+                    const uint32_t lw[4] = {l[r][u].x, l[r][u].y, l[r][u].z, l[r][u].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float h0 = __uint_as_float(hw[q] << 16), h1 = __uint_as_float(hw[q] & 0xffff0000u);
+                        const float l0 = __uint_as_float(lw[q] << 16), l1 = __uint_as_float(lw[q] & 0xffff0000u);
+                        acc[r] = fmaf(h0 + l0, fv[2 * q], acc[r]);
+                        acc[r] = fmaf(h1 + l1, fv[2 * q + 1], acc[r]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < DG_R; ++r) {
+        const float v = warp_sum(acc[r]);
+        if (lane == 0) partial[((int64_t)split * B + b) * n_pad + row0 + r] = v;
+    }
+}
+
+SplitPlan dense_plan(nf_operator *op) {
+    int res = 0;
+    if (op->path == NF_DENSE_FP32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, gemv_fp32_kernel, DG_THREADS, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, gemv_bf16x2_kernel, DG_THREADS, 0);
+    return plan_splits(op->n_pad, DG_ROWS, DG_TILE, std::max(res, 1));
+}
+
+nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
+    const SplitPlan pl = dense_plan(op);
+    dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits);
+    for (int b = 0; b < B; ++b) {
+        if (op->path == NF_DENSE_FP32)
+            gemv_fp32_kernel<<<grid, DG_THREADS, 0, s>>>(op->W32, op->g, op->n_pad, B, b, pl.jchunk, op->partial);
+        else
+            gemv_bf16x2_kernel<<<grid, DG_THREADS, 0, s>>>(op->Whi, op->Wlo, op->g, op->n_pad, B, b, pl.jchunk,
+                                                           op->partial);
+        NF_CUDA_TRY(cudaGetLastError());
+    }
+    *splits_out = pl.splits;
+    return NF_OK;
+}
+
+}  // namespace nfi

@@ -1,0 +1,198 @@
+// nf_internal.cuh -- internal declarations shared by the library's CUDA sources.
+// Not part of the C ABI (that is include/nf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/nf.h"
+
+namespace nfi {
+
+// ------------------------------------------------------------------ error plumbing
+nf_status fail(nf_status st, const char *fmt, ...);
+nf_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+void clear_error();
+
+#define NF_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess) return nfi::cuda_fail(_e, #expr, __FILE__, __LINE__);   \
+    } while (0)
+
+#define NF_TRY(expr)                                                                   \
+    do {                                                                               \
+        nf_status _s = (expr);                                                         \
+        if (_s != NF_OK) return _s;                                                    \
+    } while (0)
+
+#define NF_ARG(cond, ...)                                                              \
+    do {                                                                               \
+        if (!(cond)) return nfi::fail(NF_ERR_ARG, __VA_ARGS__);                        \
+    } while (0)
+
+// device-side error codes written to an int flag (0 = ok)
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2, DEV_NONFINITE = 3, DEV_BOUNDS = 4 };
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t v, int64_t m) { return (v + m - 1) / m; }
+
+int num_sms();
+int device_id();
+
+// ------------------------------------------------------------------ PTX helpers
+// Bounded waits: a wait that does not complete within the limit reports a timeout
+// through the error flag instead of spinning forever.
+constexpr long long kSpinLimit = 1ll << 22;  // try_wait polls (~1 s at ~0.25 us per poll)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Returns false if the barrier phase did not complete within kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (long long it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA unit), completion signalled on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 2^x on the SFU (MUFU.EX2), flush-to-zero: results below 2^-126 become 0.
+__device__ __forceinline__ float ex2_sfu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void set_dev_error(int *flag, int code) {
+    if (flag) atomicCAS(flag, 0, code);
+}
+
+__device__ __forceinline__ float bf16_bits_to_float(uint32_t h) { return __uint_as_float(h << 16); }
+
+}  // namespace nfi
+
+// ---------------------------------------------------------------------- operator
+// Node data are padded to n_pad (a multiple of kNodePad) with q = 0, so padded
+// columns contribute nothing and every tile is full.
+constexpr int64_t kNodePad = 1024;
+
+struct nf_graph_cache;
+
+struct nf_operator {
+    int64_t n = 0, n_pad = 0;
+    nf_kernel kp{};
+    int path = 0;
+    int device = 0;
+    float4 *x4 = nullptr;    // n_pad: (x, y, z, 0)
+    float *q = nullptr;      // n_pad, zero padded
+    // dense planes (row-major, leading dimension ld = n_pad)
+    float *W32 = nullptr;        // W diag(q), FP32
+    uint16_t *Whi = nullptr;     // bf16 bits of (W diag(q))_ij / s_i, high part
+    uint16_t *Wlo = nullptr;     // bf16 bits of the residual
+    float *rs = nullptr;         // s_i, powers of two
+    // workspace owned by the handle
+    float *partial = nullptr;    // [split][B][n_pad]
+    size_t partial_cap = 0;
+    float *g = nullptr;          // [B][n_pad]: q_j f(U_j) (matrix-free) or f(U_j) (dense)
+    float *U = nullptr;          // [B][n]: current stage input
+    float *ks = nullptr;         // [B][n]: RK4 slope accumulator
+    size_t state_cap = 0;        // elements of U / ks
+    size_t g_cap = 0;
+    long long *step_ctr = nullptr;  // device step counter for graph replay
+    unsigned *done_ctr = nullptr;   // last-block-done counter
+    int *err = nullptr;             // device error flag
+    double *t0_dev = nullptr;       // start time of the current nf_rk4_advance call
+    nf_graph_cache *graphs = nullptr;
+    // live kernel timing: events recorded around each stage's nonlocal launches
+    bool profile = false;
+    cudaEvent_t prof_ev[8] = {};
+};
+
+namespace nfi {
+
+// ---------------------------------------------------------------- launch plans
+struct SplitPlan {
+    int rows_per_block;   // rows of I per block
+    int64_t row_blocks;
+    int splits;           // j-range splits (blockIdx.y)
+    int64_t jchunk;       // columns per split, a multiple of the tile width
+};
+SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm);
+
+nf_status ensure_workspace(nf_operator *op, int B, int splits);
+
+// matrix-free / dense nonlocal launches (g must hold q f(U) / f(U) for B trajectories)
+nf_status mf_init_attrs();
+nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out);
+nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_out);
+nf_status launch_dense_build(nf_operator *op, cudaStream_t s);
+
+// elementwise kernels
+nf_status launch_prep_g(nf_operator *op, const float *u, int B, const float *beta, const float *theta,
+                        bool copy_to_U, cudaStream_t s);
+nf_status launch_reduce_I(nf_operator *op, int B, int splits, float *I, cudaStream_t s);
+
+struct StageParams {
+    float *u;              // B x n in/out
+    const float *beta, *theta;
+    nf_forcing forcing;
+    double dt;             // t0 is read from the operator's device clock
+    int stage;             // 1..4
+    float *ckpt;
+    int C;
+    int splits;
+};
+nf_status launch_stage(nf_operator *op, int B, const StageParams &p, cudaStream_t s);
+nf_status launch_set_clock(nf_operator *op, double t0, cudaStream_t s);
+
+// nonlocal sum of the current g into partial (path dispatch)
+nf_status launch_nonlocal_partial(nf_operator *op, int B, cudaStream_t s, int *splits_out);
+
+void destroy_graphs(nf_operator *op);
+
+}  // namespace nfi

@@ -1,0 +1,433 @@
+// nf_mf.cu -- matrix-free nonlocal sum (§2.2, Eq. (2.9)) and the fused RK4 stage
+// kernel.
+//
+// Pair kernel.  I[b, i] = sum_j w(|x_i - x_j|) g[b, j], g = q o f(U) (FP32), with the
+// Mexican-hat kernel w(r) = A1 exp(-r^2/s1^2) - A2 exp(-r^2/s2^2).  Work is split
+// into items (row block, column split): each warp owns R rows (coordinates in
+// registers); its lanes stride over the columns of the split; column tiles of
+// MF_TJ nodes (x, y, z and the NB trajectories' g values) are staged into shared
+// memory by the TMA bulk-copy unit, double buffered on mbarriers.  Per pair:
+// 3 FADD + FMUL + 2 FFMA (r^2), 2 FMUL (exponent scaling), 2 MUFU.EX2, and 2 FFMA
+// (NB = 1: separate e1 and e2 accumulators) or FMUL + FFMA + NB FFMA (NB > 1).
+// Each warp reduces its rows with shuffles and writes one partial sum per
+// (split, trajectory, row); the stage kernel (or the reduce kernel) adds the
+// splits in a fixed order, so results are deterministic.
+#include "nf_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace nfi {
+
+constexpr int MF_THREADS = 256;
+constexpr int MF_WARPS = MF_THREADS / 32;
+constexpr int MF_TJ = 512;  // columns per shared-memory tile; divides kNodePad
+static_assert(kNodePad % MF_TJ == 0, "tile must divide the node padding");
+
+template <int NB>
+struct MfSmem {
+    float4 xs[2][MF_TJ];
+    float gs[2][NB][MF_TJ];
+    uint64_t bar[2];
+};
+
+template <int NB, int R>
+__global__ void __launch_bounds__(MF_THREADS)
+mf_pair_kernel(const float4 *__restrict__ x4, const float *__restrict__ g, int64_t n_pad, int B, int b_base,
+               int64_t jchunk, float c1, float c2, float A1, float A2, float *__restrict__ partial,
+               int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MfSmem<NB> &sm = *reinterpret_cast<MfSmem<NB> *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int split = blockIdx.y;
+    const int b0 = b_base + blockIdx.z * NB;
+    const int64_t j0 = (int64_t)split * jchunk;
+    const int64_t j1 = min(n_pad, j0 + jchunk);
+    const int ntiles = (int)((j1 - j0) / MF_TJ);
+    const int64_t row0 = ((int64_t)blockIdx.x * MF_WARPS + warp) * R;
+    constexpr uint32_t kTileBytes = MF_TJ * 16 + NB * MF_TJ * 4;
+
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int t) {
+        const int buf = t & 1;
+        const int64_t jt = j0 + (int64_t)t * MF_TJ;
+        mbar_arrive_expect_tx(&sm.bar[buf], kTileBytes);
+        bulk_g2s(sm.xs[buf], x4 + jt, MF_TJ * 16, &sm.bar[buf]);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) bulk_g2s(sm.gs[buf][b], g + (int64_t)(b0 + b) * n_pad + jt, MF_TJ * 4, &sm.bar[buf]);
+    };
+    if (tid == 0) {
+        if (ntiles > 0) issue(0);
+        if (ntiles > 1) issue(1);
+    }
+
+    float xi[R], yi[R], zi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float4 p = x4[row0 + r];
+        xi[r] = p.x;
+        yi[r] = p.y;
+        zi[r] = p.z;
+    }
+    constexpr int NA = (NB == 1) ? 2 : NB;  // NB == 1: separate e1 / e2 accumulators
+    float acc[R][NA];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[r][a] = 0.f;
+
+    bool timed_out = false;
+    for (int t = 0; t < ntiles; ++t) {
+        const int buf = t & 1;
+        const bool ok = mbar_wait_bounded(&sm.bar[buf], (uint32_t)((t >> 1) & 1));
+        // Uniform decision; this barrier also certifies that every warp has finished
+        // tile t-1, whose buffer the next issue overwrites.
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        if (tid == 0 && t >= 1 && t + 1 < ntiles) issue(t + 1);
+        const float4 *xs = sm.xs[buf];
+#pragma unroll 4
+        for (int jj = lane; jj < MF_TJ; jj += 32) {
+            const float4 xj = xs[jj];
+            float gb[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) gb[b] = sm.gs[buf][b][jj];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float dx = xi[r] - xj.x, dy = yi[r] - xj.y, dz = zi[r] - xj.z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float e1 = ex2_sfu(r2 * c1);
+                const float e2 = ex2_sfu(r2 * c2);
+                if constexpr (NB == 1) {
+                    acc[r][0] = fmaf(e1, gb[0], acc[r][0]);
+                    acc[r][1] = fmaf(e2, gb[0], acc[r][1]);
+                } else {
+                    const float w = fmaf(A1, e1, -A2 * e2);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) acc[r][b] = fmaf(w, gb[b], acc[r][b]);
+                }
+            }
+        }
+    }
+    if (timed_out) {
+        if (tid == 0) set_dev_error(err, DEV_TIMEOUT);
+        // let any copy still in flight land before the block's shared memory is released
+        if (tid == 0)
+            for (int b = 0; b < 2; ++b) (void)mbar_wait_bounded(&sm.bar[b], 0), (void)mbar_wait_bounded(&sm.bar[b], 1);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            float v = (NB == 1) ? (A1 * acc[r][0] - A2 * acc[r][1]) : acc[r][b];
+            v = warp_sum(v);
+            if (lane == 0) partial[((int64_t)split * B + (b0 + b)) * n_pad + row0 + r] = v;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// split planner: (row blocks x column splits) items of equal cost; pick the number
+// of splits that best fills whole waves of resident blocks.
+SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm) {
+    SplitPlan p{};
+    p.rows_per_block = rows_per_block;
+    p.row_blocks = n_pad / rows_per_block;
+    const int64_t tiles = n_pad / tile_cols;
+    const int64_t slots = (int64_t)num_sms() * std::max(1, resident_blocks_per_sm);
+    double best = -1.0;
+    int best_s = 1;
+    const int64_t smax = std::min<int64_t>(tiles, 64);
+    for (int64_t s = 1; s <= smax; ++s) {
+        const int64_t per = ceil_div(tiles, s);
+        const int64_t s_eff = ceil_div(tiles, per);
+        if (s_eff != s) continue;
+        const int64_t items = p.row_blocks * s_eff;
+        const int64_t waves = ceil_div(items, slots);
+        double eff = (double)items / (double)(waves * slots);
+        // each extra split costs a little (prologue, partial traffic): prefer fewer
+        eff -= 0.002 * (double)s;
+        if (eff > best + 1e-9) {
+            best = eff;
+            best_s = (int)s;
+        }
+        if (items >= 16 * slots) break;  // enough waves that the tail is negligible
+    }
+    p.splits = best_s;
+    p.jchunk = ceil_div(tiles, best_s) * tile_cols;
+    return p;
+}
+
+template <int NB, int R>
+static cudaError_t set_mf_attr() {
+    return cudaFuncSetAttribute(mf_pair_kernel<NB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(MfSmem<NB>));
+}
+
+// Opt every pair-kernel instance into its shared-memory size (outside any capture).
+nf_status mf_init_attrs() {
+    NF_CUDA_TRY((set_mf_attr<1, 2>()));
+    NF_CUDA_TRY((set_mf_attr<2, 2>()));
+    NF_CUDA_TRY((set_mf_attr<4, 2>()));
+    NF_CUDA_TRY((set_mf_attr<8, 2>()));
+    NF_CUDA_TRY((set_mf_attr<1, 4>()));
+    NF_CUDA_TRY((set_mf_attr<2, 4>()));
+    NF_CUDA_TRY((set_mf_attr<4, 4>()));
+    NF_CUDA_TRY((set_mf_attr<8, 4>()));
+    return NF_OK;
+}
+
+template <int NB, int R>
+static nf_status launch_mf_group(nf_operator *op, int B, int b_base, int groups, const SplitPlan &pl,
+                                 cudaStream_t s) {
+    const size_t smem = sizeof(MfSmem<NB>);
+    const float L2E = 1.4426950408889634f;
+    const nf_kernel &k = op->kp;
+    const float c1 = -L2E / (k.s1 * k.s1), c2 = -L2E / (k.s2 * k.s2);
+    dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, (unsigned)groups);
+    mf_pair_kernel<NB, R><<<grid, MF_THREADS, smem, s>>>(op->x4, op->g, op->n_pad, B, b_base, pl.jchunk, c1, c2,
+                                                         k.A1, k.A2, op->partial, op->err);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+template <int NB, int R>
+static int mf_resident() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mf_pair_kernel<NB, R>, MF_THREADS, sizeof(MfSmem<NB>));
+    return std::max(nb, 1);
+}
+
+// Rows per warp: 4 for large problems, 2 for small ones (more blocks to fill the GPU).
+static int mf_rows_per_warp(int64_t n_pad) { return n_pad >= 16384 ? 4 : 2; }
+
+SplitPlan mf_plan(nf_operator *op) {
+    const int R = mf_rows_per_warp(op->n_pad);
+    const int res = (R == 4) ? mf_resident<1, 4>() : mf_resident<1, 2>();
+    return plan_splits(op->n_pad, MF_WARPS * R, MF_TJ, res);
+}
+
+nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
+    const SplitPlan pl = mf_plan(op);
+    const int R = mf_rows_per_warp(op->n_pad);
+    int b = 0;
+    auto run = [&](int nb) -> nf_status {
+        const int groups = (B - b) / nb;
+        if (groups <= 0) return NF_OK;
+        nf_status st = NF_OK;
+        if (R == 4) {
+            switch (nb) {
+                case 8: st = launch_mf_group<8, 4>(op, B, b, groups, pl, s); break;
+                case 4: st = launch_mf_group<4, 4>(op, B, b, groups, pl, s); break;
+                case 2: st = launch_mf_group<2, 4>(op, B, b, groups, pl, s); break;
+                default: st = launch_mf_group<1, 4>(op, B, b, groups, pl, s); break;
+            }
+        } else {
+            switch (nb) {
+                case 8: st = launch_mf_group<8, 2>(op, B, b, groups, pl, s); break;
+                case 4: st = launch_mf_group<4, 2>(op, B, b, groups, pl, s); break;
+                case 2: st = launch_mf_group<2, 2>(op, B, b, groups, pl, s); break;
+                default: st = launch_mf_group<1, 2>(op, B, b, groups, pl, s); break;
+            }
+        }
+        b += groups * nb;
+        return st;
+    };
+    NF_TRY(run(8));
+    NF_TRY(run(4));
+    NF_TRY(run(2));
+    NF_TRY(run(1));
+    *splits_out = pl.splits;
+    return NF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Elementwise kernels.
+
+__device__ __forceinline__ float firing_rate(float u, float beta, float theta) {
+    return 1.0f / (1.0f + expf(-beta * (u - theta)));
+}
+
+// g[b, j] = q_j f_b(u[b, j]) (q == nullptr: f alone);  optionally U = u.
+__global__ void prep_g_kernel(const float *__restrict__ u, int64_t n, int64_t n_pad, int B,
+                              const float *__restrict__ q, const float *__restrict__ beta,
+                              const float *__restrict__ theta, float *__restrict__ g, float *__restrict__ U) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * n) return;
+    const int b = (int)(idx / n);
+    const int64_t j = idx - (int64_t)b * n;
+    const float uv = u[idx];
+    const float f = firing_rate(uv, beta[b], theta[b]);
+    g[(int64_t)b * n_pad + j] = q ? q[j] * f : f;
+    if (U) U[idx] = uv;
+}
+
+nf_status launch_prep_g(nf_operator *op, const float *u, int B, const float *beta, const float *theta,
+                        bool copy_to_U, cudaStream_t s) {
+    const int64_t tot = (int64_t)B * op->n;
+    const int T = 256;
+    const bool mf = (op->path == NF_MATRIX_FREE);
+    prep_g_kernel<<<(unsigned)ceil_div(tot, T), T, 0, s>>>(u, op->n, op->n_pad, B, mf ? op->q : nullptr, beta,
+                                                          theta, op->g, copy_to_U ? op->U : nullptr);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+__global__ void reduce_I_kernel(const float *__restrict__ partial, int splits, int64_t n, int64_t n_pad, int B,
+                                const float *__restrict__ rs, float *__restrict__ I) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * n) return;
+    const int b = (int)(idx / n);
+    const int64_t i = idx - (int64_t)b * n;
+    float acc = 0.f;
+    for (int sp = 0; sp < splits; ++sp) acc += partial[((int64_t)sp * B + b) * n_pad + i];
+    I[idx] = rs ? acc * rs[i] : acc;
+}
+
+nf_status launch_reduce_I(nf_operator *op, int B, int splits, float *I, cudaStream_t s) {
+    const int64_t tot = (int64_t)B * op->n;
+    const int T = 256;
+    const float *rs = (op->path == NF_DENSE_BF16X2) ? op->rs : nullptr;
+    reduce_I_kernel<<<(unsigned)ceil_div(tot, T), T, 0, s>>>(op->partial, splits, op->n, op->n_pad, B, rs, I);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Fused RK4 stage: I = sum of splits; k_s = -U_s + I + gamma(t_s); RK4 bookkeeping;
+// next stage input and its g.  On the last stage the last block advances the
+// device step counter, so one captured step can be replayed.
+struct StageKArgs {
+    const float *partial;
+    int splits;
+    int64_t n, n_pad;
+    int B;
+    float *u, *U, *ks, *g;
+    const float *q;     // matrix-free: g = q f; dense: g = f (q lives in W)
+    const float *rs;    // BF16X2 row scale, or null
+    const float *beta, *theta;
+    nf_forcing F;
+    const double *t0;
+    double dt;
+    int stage;
+    long long *step_ctr;
+    unsigned *done_ctr;
+    float *ckpt;
+    int C;
+};
+
+__device__ __forceinline__ double forcing_value(const nf_forcing &F, int64_t i, double t, float beta,
+                                                float theta) {
+    if (F.kind != NF_FORCE_MMS_EIGEN) return 0.0;
+    const double Y1 = F.Y1[i], Y2 = F.Y2[i];
+    const double Y = Y1 + Y2;
+    const double a = F.a0 * cos(t), da = -F.a0 * sin(t);
+    const double z = F.c + a * Y;
+    const double us = (double)theta + log(z / (1.0 - z)) / (double)beta;
+    const double dus = da * Y / ((double)beta * z * (1.0 - z));
+    return dus + us - (F.lam0 * F.c + a * (F.lam1 * Y1 + F.lam2 * Y2));
+}
+
+__global__ void rk4_stage_kernel(StageKArgs a) {
+    const long long step = *a.step_ctr;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < (int64_t)a.B * a.n) {
+        const int b = (int)(idx / a.n);
+        const int64_t i = idx - (int64_t)b * a.n;
+        float I = 0.f;
+        for (int sp = 0; sp < a.splits; ++sp) I += a.partial[((int64_t)sp * a.B + b) * a.n_pad + i];
+        if (a.rs) I *= a.rs[i];
+        const double cs = (a.stage == 1) ? 0.0 : (a.stage == 4 ? 1.0 : 0.5);
+        const double ts = *a.t0 + (double)step * a.dt + cs * a.dt;
+        const float bb = a.beta[b], th = a.theta[b];
+        const float gam = (float)forcing_value(a.F, i, ts, bb, th);
+        const float Uv = a.U[idx], uv = a.u[idx];
+        const float k = (-Uv + I) + gam;
+        const float dt = (float)a.dt;
+        float Un;
+        if (a.stage == 1) {
+            a.ks[idx] = k;
+            Un = fmaf(0.5f * dt, k, uv);
+        } else if (a.stage == 2) {
+            a.ks[idx] = fmaf(2.f, k, a.ks[idx]);
+            Un = fmaf(0.5f * dt, k, uv);
+        } else if (a.stage == 3) {
+            a.ks[idx] = fmaf(2.f, k, a.ks[idx]);
+            Un = fmaf(dt, k, uv);
+        } else {
+            const float unew = fmaf(dt / 6.f, a.ks[idx] + k, uv);
+            a.u[idx] = unew;
+            Un = unew;
+            if (a.ckpt && ((step + 1) % a.C) == 0)
+                a.ckpt[(int64_t)((step + 1) / a.C) * a.B * a.n + idx] = unew;
+        }
+        a.U[idx] = Un;
+        const float f = firing_rate(Un, bb, th);
+        a.g[(int64_t)b * a.n_pad + i] = a.q ? a.q[i] * f : f;
+    }
+    if (a.stage == 4) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(a.done_ctr, 1u);
+            if (prev == gridDim.x - 1) {
+                *a.done_ctr = 0u;
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.step_ctr), 1ull);
+                __threadfence();
+            }
+        }
+    }
+}
+
+// Start a new nf_rk4_advance call: clock t0 and step counter 0.
+__global__ void set_clock_kernel(double *t0_dev, long long *step_ctr, double t0) {
+    *t0_dev = t0;
+    *step_ctr = 0;
+}
+
+nf_status launch_set_clock(nf_operator *op, double t0, cudaStream_t s) {
+    set_clock_kernel<<<1, 1, 0, s>>>(op->t0_dev, op->step_ctr, t0);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+nf_status launch_stage(nf_operator *op, int B, const StageParams &p, cudaStream_t s) {
+    StageKArgs a{};
+    a.partial = op->partial;
+    a.splits = p.splits;
+    a.n = op->n;
+    a.n_pad = op->n_pad;
+    a.B = B;
+    a.u = p.u;
+    a.U = op->U;
+    a.ks = op->ks;
+    a.g = op->g;
+    a.q = (op->path == NF_MATRIX_FREE) ? op->q : nullptr;
+    a.rs = (op->path == NF_DENSE_BF16X2) ? op->rs : nullptr;
+    a.beta = p.beta;
+    a.theta = p.theta;
+    a.F = p.forcing;
+    a.t0 = op->t0_dev;
+    a.dt = p.dt;
+    a.stage = p.stage;
+    a.step_ctr = op->step_ctr;
+    a.done_ctr = op->done_ctr;
+    a.ckpt = p.ckpt;
+    a.C = p.C;
+    const int64_t tot = (int64_t)B * op->n;
+    const int T = 256;
+    rk4_stage_kernel<<<(unsigned)ceil_div(tot, T), T, 0, s>>>(a);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+}  // namespace nfi

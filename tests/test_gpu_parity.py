@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Bars: stencil indices bit-exact; quadrature weights within 1e-12 relative
+(max-norm); FP32 nonlocal sums and trajectories within 1e-5 relative L2 per
+trajectory.  The oracle always receives the FP32-rounded values the GPU sees.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import nodesets
+import oracle
+from nodesets import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+Q_REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def nf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2504_13379_gb300 as nf
+    nf.lib()
+    return nf
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel_l2(got, want):
+    got, want = np.atleast_2d(got), np.atleast_2d(want)
+    return max(np.linalg.norm(g - w) / np.linalg.norm(w) for g, w in zip(got, want))
+
+
+# ------------------------------------------------------------------ §3.1 stencils
+
+@pytest.mark.parametrize("case", ["square", "sphere", "torus", "ties2d", "ties3d"])
+def test_stencils_bit_exact(nf, case):
+    if case == "square":
+        ns, k = nodesets.square_halton(1500), 24
+        X = ns.coords()
+    elif case == "sphere":
+        ns, k = nodesets.sphere_fibonacci(3000, seed=4), 32
+        X = ns.nodes
+    elif case == "torus":
+        ns, k = nodesets.torus_lattice(6000, seed=5), 48
+        X = ns.nodes
+    else:  # quantised coordinates: many exact distance ties
+        rng = np.random.default_rng(7)
+        d = 2 if case == "ties2d" else 3
+        X = np.round(rng.uniform(0, 1, size=(2000, d)) * 16) / 16
+        tris = rng.integers(0, 2000, size=(3000, 3)).astype(np.int32)
+        ns = nodesets.NodeSet(X, tris, None, d)
+        k = 40
+    got = nf.nf_build_stencils(dev(X, torch.float64), dev(ns.tris, torch.int32), k).cpu().numpy()
+    want = oracle.knn(X, ns.tris, k)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_stencils_k_equals_n(nf):
+    rng = np.random.default_rng(3)
+    X = rng.uniform(size=(40, 2))
+    tris = rng.integers(0, 40, size=(7, 3)).astype(np.int32)
+    got = nf.nf_build_stencils(dev(X, torch.float64), dev(tris, torch.int32), 40).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.knn(X, tris, 40))
+
+
+# ------------------------------------------------------------------ §3.2-3.3 weights
+
+def _weights_pair(nf, ns, k, deg):
+    X = ns.coords()
+    st = oracle.knn(X, ns.tris, k)
+    want = oracle.quad_weights(X, ns.tris, st, deg, normals=ns.normals if ns.dim == 3 else None)
+    normals = dev(ns.normals, torch.float64) if ns.dim == 3 else None
+    got = nf.nf_quad_weights(dev(X, torch.float64), dev(ns.tris, torch.int32), dev(st, torch.int32), deg,
+                             normals=normals).cpu().numpy()
+    return got, want
+
+
+@pytest.mark.parametrize("case", ["flat", "sphere", "torus", "ellipsoid", "regular"])
+def test_quad_weights_match_oracle(nf, case):
+    if case == "flat":
+        ns, k, deg = nodesets.square_halton(1500), 24, 2
+    elif case == "sphere":
+        ns, k, deg = nodesets.sphere_fibonacci(4000, seed=1), 32, 3
+    elif case == "torus":
+        ns, k, deg = nodesets.torus_lattice(8000, seed=2), 48, 4
+    elif case == "ellipsoid":
+        ns, k, deg = nodesets.ellipsoid_fibonacci(5000, seed=3), 32, 3
+    else:
+        ns, k, deg = nodesets.square_regular(24), 21, 3
+    got, want = _weights_pair(nf, ns, k, deg)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < Q_REL, err
+
+
+def test_quad_weights_singular_stencil_reported(nf):
+    """A stencil whose nodes are collinear cannot carry the degree-1 polynomial
+    moments (§3.1 unisolvency): the call reports NF_ERR_SINGULAR."""
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [3.0, 0.0], [0.5, 1.0]])
+    tris = np.array([[0, 1, 4]], dtype=np.int32)
+    st = np.array([[0, 1, 2, 3]], dtype=np.int32)  # collinear stencil
+    with pytest.raises(nf.NFError) as ei:
+        nf.nf_quad_weights(dev(X, torch.float64), dev(tris, torch.int32), dev(st, torch.int32), 1)
+    assert ei.value.name == "NF_ERR_SINGULAR"
+
+
+# ------------------------------------------------------------------ §2.2 nonlocal sum
+
+def _op(nf, X, q, kernel, path):
+    return nf.Operator(dev(X, torch.float32), dev(q, torch.float32), kernel, path)
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("n,B", [(3001, 1), (2500, 3), (1100, 7), (5, 2), (1, 1)])
+def test_nonlocal_apply_matches_oracle(nf, path, n, B):
+    rng = np.random.default_rng(n + B)
+    X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
+    u = rng.normal(0.3, 0.4, size=(B, n)).astype(np.float32)
+    beta = rng.uniform(10, 40, B).astype(np.float32)
+    theta = rng.uniform(0.1, 0.3, B).astype(np.float32)
+    kern = (1.0, 0.3, 0.5, 0.6)
+    op = _op(nf, X, q, kern, path)
+    got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), dev(beta, torch.float32), dev(theta, torch.float32))
+    op.check()
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), f32(beta), f32(theta))
+    assert rel_l2(got.cpu().numpy(), want) < REL_L2
+
+
+def test_nonlocal_apply_paper_kernel_torus_sampled_full_size(nf):
+    """Full precision-workload size (n = 100,000 torus nodes), the launch
+    configuration the benchmark times; the oracle evaluates 384 sampled rows."""
+    wl = W.precision()
+    X = wl.ns.nodes.astype(np.float32)
+    rng = np.random.default_rng(11)
+    q = (wl.ns.area / wl.n * rng.uniform(0.8, 1.2, wl.n)).astype(np.float32)
+    u = wl.u0.astype(np.float32)
+    rows = np.sort(rng.choice(wl.n, 384, replace=False))
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(wl.kernel), f32(wl.beta), f32(wl.theta), rows=rows)
+    for path in (0, 2, 1):
+        op = _op(nf, X, q, wl.kernel, path)
+        got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), float(wl.beta[0]), float(wl.theta[0]))
+        op.check()
+        assert rel_l2(got.cpu().numpy()[:, rows], want) < REL_L2, path
+        op.close()
+        del op
+        torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------ RK4 trajectories
+
+def _rk4_pair(nf, X, q, u0, kernel, beta, theta, dt, nsteps, path, forcing=None, extra=None):
+    op = _op(nf, X, q, kernel, path)
+    u = dev(u0, torch.float32)
+    F = None
+    Fo = None
+    if forcing is not None:
+        lam = nf.nf_mms_sphere_eigs(kernel)
+        F = nf.Forcing(1, dev(extra["Y1"], torch.float32), dev(extra["Y2"], torch.float32), forcing["c"],
+                       forcing["a0"], lam)
+        Fo = oracle.mms_sphere_forcing(f32(kernel), forcing["c"], forcing["a0"])
+    nf.nf_rk4_advance(op, u, 0.0, dt, nsteps, dev(beta, torch.float32), dev(theta, torch.float32), forcing=F)
+    op.check()
+    want = oracle.rk4(f32(X), f32(q), f32(u0), f32(kernel), f32(beta), f32(theta), 0.0, dt, nsteps, forcing=Fo)
+    return u.cpu().numpy(), want
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_rk4_flat_workload_full(nf, path):
+    """The flat unit-square workload end to end: oracle stencils and weights, then
+    100 RK4 steps (t = 0..5) on the GPU vs the FP64 oracle."""
+    wl = W.flat()
+    X2 = wl.ns.coords()
+    st = oracle.knn(X2, wl.ns.tris, wl.k)
+    q = oracle.quad_weights(X2, wl.ns.tris, st, wl.deg)
+    X = wl.ns.nodes.astype(np.float32)
+    got, want = _rk4_pair(nf, X, q.astype(np.float32), wl.u0.astype(np.float32), wl.kernel,
+                          wl.beta.astype(np.float32), wl.theta.astype(np.float32), wl.dt, wl.nsteps, path)
+    assert rel_l2(got, want) < REL_L2
+
+
+def test_rk4_sphere_manufactured_forcing(nf):
+    wl = W.sphere(3000)
+    st = oracle.knn(wl.ns.nodes, wl.ns.tris, wl.k)
+    q = oracle.quad_weights(wl.ns.nodes, wl.ns.tris, st, wl.deg, normals=wl.ns.normals)
+    X = wl.ns.nodes.astype(np.float32)
+    extra = {"Y1": f32(0.5 * X[:, 2]), "Y2": f32(X[:, 0]) * f32(X[:, 1])}
+    got, want = _rk4_pair(nf, X, q.astype(np.float32), wl.u0.astype(np.float32), wl.kernel,
+                          wl.beta.astype(np.float32), wl.theta.astype(np.float32), wl.dt, 40, 0,
+                          forcing=wl.forcing, extra=extra)
+    assert rel_l2(got, want) < REL_L2
+
+
+def test_rk4_batched_trajectories(nf):
+    rng = np.random.default_rng(5)
+    ns = nodesets.ellipsoid_fibonacci(2000, seed=9)
+    q = np.full(ns.n, 3.0 / ns.n, dtype=np.float32)
+    u0, beta, theta = nodesets.random_bumps(ns, 6, 17, (1.0, 0.8, 0.6))
+    X = ns.nodes.astype(np.float32)
+    got, want = _rk4_pair(nf, X, q, u0.astype(np.float32), W.KERNEL, beta.astype(np.float32),
+                          theta.astype(np.float32), 0.05, 20, 0)
+    assert rel_l2(got, want) < REL_L2
+
+
+def test_rk4_linear_decay_full_size(nf):
+    """Property at the full precision-workload size: with w = 0, RK4 multiplies u by
+    (1 - dt + dt^2/2 - dt^3/6 + dt^4/24) per step."""
+    wl = W.precision()
+    X = wl.ns.nodes.astype(np.float32)
+    q = np.full(wl.n, wl.ns.area / wl.n, dtype=np.float32)
+    op = _op(nf, X, q, (0.0, 0.1, 0.0, 0.2), 0)
+    u = dev(wl.u0, torch.float32)
+    u0 = u.clone()
+    dt, N = wl.dt, 4
+    nf.nf_rk4_advance(op, u, 0.0, dt, N, 50.0, 0.2)
+    op.check()
+    g = 1 - dt + dt ** 2 / 2 - dt ** 3 / 6 + dt ** 4 / 24
+    want = u0.double().cpu().numpy() * g ** N
+    assert rel_l2(u.cpu().numpy(), want) < 1e-6
+
+
+def test_rk4_checkpoints(nf):
+    rng = np.random.default_rng(2)
+    n = 700
+    X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    q = np.full(n, 1.0 / n, dtype=np.float32)
+    u0 = rng.normal(0.2, 0.3, size=(2, n)).astype(np.float32)
+    op = _op(nf, X, q, (1.0, 0.3, 0.5, 0.6), 0)
+    u = dev(u0, torch.float32)
+    ck = torch.zeros((4, 2, n), dtype=torch.float32, device="cuda")
+    nf.nf_rk4_advance(op, u, 0.0, 0.05, 9, 20.0, 0.2, ckpt=ck, C_every=3)
+    op.check()
+    ck = ck.cpu().numpy()
+    np.testing.assert_array_equal(ck[0], u0)
+    np.testing.assert_array_equal(ck[3], u.cpu().numpy())
+    for c in (1, 2):
+        want = oracle.rk4(f32(X), f32(q), f32(u0), (1.0, 0.3, 0.5, 0.6), 20.0, np.float32(0.2), 0.0, 0.05, 3 * c)
+        assert rel_l2(ck[c], want) < REL_L2
