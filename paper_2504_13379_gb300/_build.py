@@ -54,7 +54,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
 
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
+        # FP64 setup (stencils, RBF-QF solves) rounds every operation separately, like a
+        # plain IEEE evaluation without fused multiply-add.
+        per_file = ["-fmad=false"] if os.path.basename(src) == "nf_setup.cu" else []
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *per_file, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

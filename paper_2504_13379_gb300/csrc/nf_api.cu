@@ -164,7 +164,7 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
     for (int stage = 1; stage <= 4 && st == NF_OK; ++stage) {
         int splits = 1;
         if (op->profile) {
-            cudaError_t pe = cudaEventRecord(op->prof_ev[2 * (stage - 1)], cs);
+            cudaError_t pe = cudaEventRecordWithFlags(op->prof_ev[2 * (stage - 1)], cs, cudaEventRecordExternal);
             if (pe != cudaSuccess) {
                 st = cuda_fail(pe, "cudaEventRecord", __FILE__, __LINE__);
                 break;
@@ -173,7 +173,7 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
         st = launch_nonlocal_partial(op, B, cs, &splits);
         if (st != NF_OK) break;
         if (op->profile) {
-            cudaError_t pe = cudaEventRecord(op->prof_ev[2 * (stage - 1) + 1], cs);
+            cudaError_t pe = cudaEventRecordWithFlags(op->prof_ev[2 * (stage - 1) + 1], cs, cudaEventRecordExternal);
             if (pe != cudaSuccess) {
                 st = cuda_fail(pe, "cudaEventRecord", __FILE__, __LINE__);
                 break;

@@ -1,0 +1,66 @@
+"""GPU adjoint (nf_adjoint) against the FP64 oracle adjoint, which is itself pinned
+to central finite differences in the CPU suite."""
+import numpy as np
+import pytest
+import torch
+
+import nodesets
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2504_13379_gb300 as nf
+    nf.lib()
+    return nf
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("n,B,nsteps,C", [(900, 1, 12, 5), (1500, 2, 10, 10), (2100, 1, 7, 3)])
+def test_adjoint_matches_oracle(nf, n, B, nsteps, C):
+    ns = nodesets.torus_lattice(n if n % 2 == 0 else n + 1, seed=n)
+    n = ns.n
+    X = ns.nodes.astype(np.float32)
+    q = np.full(n, ns.area / n, dtype=np.float32)
+    u0 = np.stack([nodesets.spiral_bumps_u0(ns, count=3 + b) for b in range(B)]).astype(np.float32)
+    kern = (1.0, 0.1, 0.5, 0.2)
+    beta = np.array([20.0, 12.0][:B], dtype=np.float32)
+    theta = np.array([0.2, 0.25][:B], dtype=np.float32)
+    dt = 0.02
+    rng = np.random.default_rng(n)
+    target = (u0 * 0.9 + 0.05 * rng.normal(size=u0.shape)).astype(np.float32)
+    op = nf.Operator(dev(X), dev(q), kern, 0)
+    u = dev(u0)
+    ck = torch.zeros((nsteps // C + 1, B, n), dtype=torch.float32, device="cuda")
+    nf.nf_rk4_advance(op, u, 0.0, dt, nsteps, dev(beta), dev(theta), ckpt=ck, C_every=C)
+    lamT = 2.0 * (u - dev(target))
+    gu, gk = nf.nf_adjoint(op, ck, C, 0.0, dt, nsteps, dev(beta), dev(theta), lamT)
+    op.check()
+    uN = oracle.rk4(f32(X), f32(q), f32(u0), f32(kern), f32(beta), f32(theta), 0.0, dt, nsteps)
+    gu_o, gk_o = oracle.adjoint(f32(X), f32(q), f32(u0), f32(kern), f32(beta), f32(theta), 0.0, dt, nsteps,
+                                2.0 * (uN - f32(target)))
+    gu = gu.cpu().numpy()
+    gk = gk.cpu().numpy()
+    for b in range(B):
+        assert np.linalg.norm(gu[b] - gu_o[b]) / np.linalg.norm(gu_o[b]) < 1e-5
+        np.testing.assert_allclose(gk[b], gk_o[b], rtol=1e-4, atol=1e-6 * np.abs(gk_o[b]).max())
+
+
+def test_adjoint_rejects_dense_operator(nf):
+    X = np.random.default_rng(0).uniform(size=(64, 3)).astype(np.float32)
+    op = nf.Operator(dev(X), dev(np.full(64, 1 / 64)), (1.0, 0.3, 0.5, 0.6), 1)
+    ck = torch.zeros((2, 1, 64), device="cuda")
+    with pytest.raises(nf.NFError) as ei:
+        nf.nf_adjoint(op, ck, 1, 0.0, 0.1, 1, 20.0, 0.2, torch.zeros((1, 64), device="cuda"))
+    assert ei.value.name == "NF_ERR_UNSUPPORTED"
