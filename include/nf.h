@@ -152,6 +152,24 @@ NF_API nf_status nf_operator_kernel_ms(nf_operator *op, float *ms);
 NF_API nf_status nf_nonlocal_apply(nf_operator *op, const float *u, int B, const float *beta,
                             const float *theta, float *I, void *stream);
 
+/* Allocation-free nonlocal sum for one trajectory (the paper has no counterpart: this
+ * is a deployment convenience).  For callers that cannot allocate device memory when
+ * they need the sum -- e.g. inside a host framework that owns all allocations, or a
+ * fixed-budget loop where a cudaMalloc would synchronise the device -- it computes
+ *     I[i] = sum_j w(|x_i - x_j|) q_j f(u[j])      (same kernels as the matrix-free path)
+ * without an operator handle and without allocating: its working memory is a fixed
+ * file-scope device array of about 2.6 MB, held by every GPU that loads the library
+ * until the process exits.
+ *   x  n x 3 FP32, q n FP32, u n FP32, I n FP32 (output): caller-owned device memory.
+ *   n  1 .. 32768 (larger n returns NF_ERR_ARG: the scratch size is fixed).
+ * The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share the
+ * array: each call rewrites what it reads, but calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  Returns after enqueuing on `stream`.
+ * Errors: NF_ERR_ARG, NF_ERR_CUDA. */
+NF_API nf_status nf_nonlocal_apply_noalloc(const float *x, const float *q, int64_t n, nf_kernel kp,
+                                           const float *u, float beta, float theta, float *I, void *stream);
+
 /* Forcing gamma(t) of Eq. (2.9).
  *  NF_FORCE_NONE: gamma = 0.
  *  NF_FORCE_MMS_EIGEN: the manufactured-solution technique of §4 Eq. (4.5) with two

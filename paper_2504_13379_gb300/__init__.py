@@ -40,7 +40,8 @@ STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINIT
 # exported symbols declared in include/nf.h
 EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights", "nf_operator_create",
            "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
-           "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms"]
+           "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms",
+           "nf_nonlocal_apply_noalloc"]
 
 
 class NFError(RuntimeError):
@@ -90,6 +91,7 @@ def lib(path: str | None = None):
     L.nf_operator_profile.argtypes = [_vp, C.c_int]
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
     L.nf_nonlocal_apply.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]
+    L.nf_nonlocal_apply_noalloc.argtypes = [_vp, _vp, _i64, _Kernel, _vp, C.c_float, C.c_float, _vp, _vp]
     L.nf_mms_sphere_eigs.argtypes = [_Kernel, C.POINTER(C.c_double)]
     L.nf_rk4_advance.argtypes = [_vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp,
                                  C.POINTER(_Forcing), _vp, C.c_int, _vp]
@@ -225,6 +227,18 @@ def nf_nonlocal_apply(op: Operator, u: torch.Tensor, beta, theta, out: torch.Ten
     _check(lib().nf_nonlocal_apply(op.handle, _dptr(u2, torch.float32, "u"), B, _dptr(be, torch.float32, "beta"),
                                    _dptr(th, torch.float32, "theta"), _dptr(I, torch.float32, "I"), _stream(u)))
     return I if u.dim() == 2 else I.view(-1)
+
+
+def nf_nonlocal_apply_noalloc(x: torch.Tensor, q: torch.Tensor, u: torch.Tensor, kernel, beta: float, theta: float,
+                              out: torch.Tensor) -> torch.Tensor:
+    """Single-trajectory nonlocal sum that allocates nothing (neither here nor in the
+    library): for callers that cannot allocate device memory at call time.  ``out``
+    must be preallocated (n float32).  n <= 32768; calls that overlap on the GPU race."""
+    n = int(x.shape[0])
+    _check(lib().nf_nonlocal_apply_noalloc(_dptr(x, torch.float32, "x"), _dptr(q, torch.float32, "q"), n,
+                                           _kernel(kernel), _dptr(u, torch.float32, "u"), float(beta), float(theta),
+                                           _dptr(out, torch.float32, "I"), _stream(x)))
+    return out
 
 
 def nf_rk4_advance(op: Operator, u: torch.Tensor, t0: float, dt: float, nsteps: int, beta, theta,

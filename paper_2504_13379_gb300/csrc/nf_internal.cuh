@@ -169,6 +169,8 @@ nf_status ensure_workspace(nf_operator *op, int B, int splits);
 // matrix-free / dense nonlocal launches (g must hold q f(U) / f(U) for B trajectories)
 nf_status mf_init_attrs();
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out);
+nf_status launch_mf_pair_single(const float4 *x4, const float *g, int64_t n_pad, const nf_kernel &k, int max_splits,
+                                float *partial, int *err, cudaStream_t s, int *splits_out);
 nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_out);
 nf_status launch_dense_build(nf_operator *op, cudaStream_t s);
 

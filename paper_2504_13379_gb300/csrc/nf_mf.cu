@@ -250,6 +250,32 @@ nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out
     return NF_OK;
 }
 
+// Single-trajectory pair sums into caller-provided buffers (x4, g padded to n_pad,
+// partial [splits][n_pad]); the split count is capped at max_splits.
+nf_status launch_mf_pair_single(const float4 *x4, const float *g, int64_t n_pad, const nf_kernel &k, int max_splits,
+                                float *partial, int *err, cudaStream_t s, int *splits_out) {
+    const int R = mf_rows_per_warp(n_pad);
+    SplitPlan pl = plan_splits(n_pad, MF_WARPS * R, MF_TJ, R == 4 ? mf_resident<1, 4>() : mf_resident<1, 2>());
+    if (pl.splits > max_splits) {
+        const int64_t tiles = n_pad / MF_TJ;
+        const int64_t per = ceil_div(tiles, max_splits);
+        pl.jchunk = per * MF_TJ;
+        pl.splits = (int)ceil_div(tiles, per);
+    }
+    const float L2E = 1.4426950408889634f;
+    const float c1 = -L2E / (k.s1 * k.s1), c2 = -L2E / (k.s2 * k.s2);
+    dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, 1);
+    if (R == 4)
+        mf_pair_kernel<1, 4><<<grid, MF_THREADS, sizeof(MfSmem<1>), s>>>(x4, g, n_pad, 1, 0, pl.jchunk, c1, c2, k.A1,
+                                                                      k.A2, partial, err);
+    else
+        mf_pair_kernel<1, 2><<<grid, MF_THREADS, sizeof(MfSmem<1>), s>>>(x4, g, n_pad, 1, 0, pl.jchunk, c1, c2, k.A1,
+                                                                      k.A2, partial, err);
+    NF_CUDA_TRY(cudaGetLastError());
+    *splits_out = pl.splits;
+    return NF_OK;
+}
+
 // ----------------------------------------------------------------------------
 // Elementwise kernels.
 
