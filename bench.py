@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--n", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched tensor-core section")
     return ap.parse_args()
 
 
@@ -175,6 +176,110 @@ def cpu_baseline(wl, q, seconds):
     dt = time.perf_counter() - t
     return {"value": rows * wl.n / dt, "unit": "pair-evals/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"one nonlocal stage on {rows} random rows x {wl.n} columns (FP64, {dt:.1f} s)"}
+
+
+def run_batched(args, dev, steps):
+    """Batched workload: 448 trajectories on four node sets.  Tensor-core path (grouped
+    tcgen05 GEMM, bf16 x 3) against the plain FP32 matrix-free comparator."""
+    import torch
+
+    import paper_2504_13379_gb300 as nf
+    from nodesets import workloads as W
+
+    stream = torch.cuda.current_stream(dev)
+    wls = W.batched()
+    qs, xs = [], []
+    t0 = time.perf_counter()
+    for wl in wls:
+        nodes = torch.as_tensor(wl.ns.nodes, device=dev)
+        tris = torch.as_tensor(wl.ns.tris, device=dev)
+        st = nf.nf_build_stencils(nodes, tris, wl.k)
+        q = nf.nf_quad_weights(nodes, tris, st, wl.deg, normals=torch.as_tensor(wl.ns.normals, device=dev))
+        qs.append(q.to(torch.float32).contiguous())
+        xs.append(torch.as_tensor(wl.ns.nodes.astype(np.float32), device=dev))
+    torch.cuda.synchronize(dev)
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    pairs_per_stage = float(sum(wl.B * wl.n * wl.n for wl in wls))
+    w_bytes = float(sum(4 * wl.n * wl.n for wl in wls))
+    flops = float(sum(3 * 2 * wl.B * wl.n * wl.n for wl in wls))
+    u0 = torch.cat([torch.as_tensor(wl.u0.astype(np.float32), device=dev).reshape(-1) for wl in wls])
+    beta = torch.cat([torch.as_tensor(wl.beta.astype(np.float32), device=dev) for wl in wls])
+    theta = torch.cat([torch.as_tensor(wl.theta.astype(np.float32), device=dev) for wl in wls])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "sphere 40000 x 256 traj + ellipsoids (1:0.8:0.6) 8000/15000/30000 x 64 traj, k=32 deg=3",
+           "setup_ms": setup_ms, "pair_evals_per_stage": pairs_per_stage}
+
+    def timed(step_fn, nsteps, kernel_ms_fn=None):
+        for _ in range(3):
+            step_fn()
+        torch.cuda.synchronize(dev)
+        tot, kern = 0.0, 0.0
+        for _ in range(nsteps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step_fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+            if kernel_ms_fn:
+                kern += sum(kernel_ms_fn())
+        return tot / nsteps, (kern / (4 * nsteps) if kernel_ms_fn else None)
+
+    # ---- tensor-core path
+    t0 = time.perf_counter()
+    ops = [nf.Operator(x, q, wl.kernel, nf.DENSE_BF16X2) for x, q, wl in zip(xs, qs, wls)]
+    grp = nf.GroupedOperator(ops, [wl.B for wl in wls])
+    torch.cuda.synchronize(dev)
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    grp.profile(True)
+    u = u0.clone()
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    ms, kms = timed(lambda: nf.nf_rk4_advance(grp, u, 0.0, 0.05, 1, beta, theta), steps, grp.kernel_ms)
+    clocks = sampler.stop()
+    grp.check()
+    pk = peaks()
+    hbm = w_bytes / (kms * 1e-3) / 1e9
+    tfl = flops / (kms * 1e-3) / 1e12
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    tc_peak = pk.get("bf16_tflops_sustained", 1700.0)
+    out["tc_bf16x3"] = {
+        "ms_per_step": ms, "rk4_steps_per_s": 1e3 / ms, "pair_evals_per_s": 4 * pairs_per_stage / (ms * 1e-3),
+        "kernel_ms_per_launch": kms, "build_ms": build_ms, "clocks": clocks,
+        "roofline": {"bound": "hbm" if hbm / hbm_peak >= tfl / tc_peak else "tensor",
+                     "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak},
+                     "tensor": {"achieved": tfl, "peak": tc_peak, "unit": "TFLOP/s", "frac": tfl / tc_peak,
+                                "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (kernel inside a long step)"}},
+        "gpu_launches_per_step": 4}
+    grp.close()
+    for op in ops:
+        op.close()
+    del grp, ops
+    torch.cuda.empty_cache()
+    # ---- plain FP32 comparator: matrix-free pair kernel, B_g trajectories per node set
+    mops = [nf.Operator(x, q, wl.kernel, nf.MATRIX_FREE) for x, q, wl in zip(xs, qs, wls)]
+    blocks = []
+    off, toff = 0, 0
+    for wl in wls:
+        blocks.append((u0[off:off + wl.B * wl.n].view(wl.B, wl.n).clone(), beta[toff:toff + wl.B].contiguous(),
+                       theta[toff:toff + wl.B].contiguous()))
+        off += wl.B * wl.n
+        toff += wl.B
+
+    def mf_step():
+        for op, (ub, be, th) in zip(mops, blocks):
+            nf.nf_rk4_advance(op, ub, 0.0, 0.05, 1, be, th)
+
+    cmp_steps = max(1, min(steps, 5))
+    ms_mf, _ = timed(mf_step, cmp_steps)
+    out["mf_fp32"] = {"ms_per_step": ms_mf, "rk4_steps_per_s": 1e3 / ms_mf,
+                      "pair_evals_per_s": 4 * pairs_per_stage / (ms_mf * 1e-3), "steps_timed": cmp_steps}
+    out["tc_speedup_vs_plain_fp32"] = ms_mf / ms
+    for op in mops:
+        op.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -312,6 +417,9 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches_total,
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args, dev, args.steps)
+        line["gpu_launches"] += 4 * args.steps  # tensor-core path: one grouped GEMM per stage
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, q.double().cpu().numpy(), args.cpu_seconds)
     return line if rank == 0 else None

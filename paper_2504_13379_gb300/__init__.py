@@ -41,7 +41,7 @@ STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINIT
 EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights", "nf_operator_create",
            "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
            "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms",
-           "nf_nonlocal_apply_noalloc"]
+           "nf_nonlocal_apply_noalloc", "nf_operator_group"]
 
 
 class NFError(RuntimeError):
@@ -87,6 +87,7 @@ def lib(path: str | None = None):
                                   C.POINTER(C.c_int64), _vp]
     L.nf_operator_create.argtypes = [_vp, _vp, _i64, _Kernel, C.c_int, _vp, C.POINTER(_vp)]
     L.nf_operator_destroy.argtypes = [_vp]
+    L.nf_operator_group.argtypes = [C.POINTER(_vp), C.POINTER(C.c_int), C.c_int, _vp, C.POINTER(_vp)]
     L.nf_operator_check.argtypes = [_vp, _vp]
     L.nf_operator_profile.argtypes = [_vp, C.c_int]
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
@@ -212,6 +213,35 @@ class Operator:
             pass
 
 
+class GroupedOperator(Operator):
+    """Owning handle for a grouped operator (``nf_operator_group``): several
+    DENSE_BF16X2 operators advanced together by the tcgen05 tensor-core GEMM.  States
+    are the concatenation over members of their B_g x n_g blocks; the members must stay
+    alive while the group is used."""
+
+    def __init__(self, members, B_per_op):
+        self.members = list(members)
+        self.B_per_op = [int(b) for b in B_per_op]
+        self.n = sum(m.n * b for m, b in zip(self.members, self.B_per_op))
+        self.B = sum(self.B_per_op)
+        self.path = 3
+        self.device = self.members[0].device
+        self.kernel = self.members[0].kernel
+        arr = (C.c_void_p * len(self.members))(*[m.handle.value for m in self.members])
+        bs = (C.c_int * len(self.members))(*self.B_per_op)
+        h = C.c_void_p()
+        _check(lib().nf_operator_group(arr, bs, len(self.members), _stream(), C.byref(h)))
+        self._h = h
+
+    def split(self, flat: torch.Tensor):
+        """View a concatenated state as the list of per-member (B_g x n_g) blocks."""
+        out, off = [], 0
+        for m, b in zip(self.members, self.B_per_op):
+            out.append(flat[off:off + b * m.n].view(b, m.n))
+            off += b * m.n
+        return out
+
+
 def _per_traj(v, B, device):
     if isinstance(v, torch.Tensor):
         return v.to(device=device, dtype=torch.float32).contiguous().expand(B).contiguous()
@@ -219,9 +249,13 @@ def _per_traj(v, B, device):
 
 
 def nf_nonlocal_apply(op: Operator, u: torch.Tensor, beta, theta, out: torch.Tensor | None = None) -> torch.Tensor:
-    """I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]); u: B x n float32 CUDA."""
-    u2 = u if u.dim() == 2 else u.view(1, -1)
-    B = u2.shape[0]
+    """I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]); u: B x n float32 CUDA (for a
+    grouped operator: the flat concatenation of the members' B_g x n_g blocks)."""
+    if isinstance(op, GroupedOperator):
+        u2, B = u.reshape(-1), op.B
+    else:
+        u2 = u if u.dim() == 2 else u.view(1, -1)
+        B = u2.shape[0]
     be, th = _per_traj(beta, B, u.device), _per_traj(theta, B, u.device)
     I = out if out is not None else torch.empty_like(u2)
     _check(lib().nf_nonlocal_apply(op.handle, _dptr(u2, torch.float32, "u"), B, _dptr(be, torch.float32, "beta"),
@@ -243,9 +277,13 @@ def nf_nonlocal_apply_noalloc(x: torch.Tensor, q: torch.Tensor, u: torch.Tensor,
 
 def nf_rk4_advance(op: Operator, u: torch.Tensor, t0: float, dt: float, nsteps: int, beta, theta,
                    forcing: Forcing | None = None, ckpt: torch.Tensor | None = None, C_every: int = 1):
-    """Advance u (B x n float32 CUDA, in place) by nsteps RK4 steps."""
-    u2 = u if u.dim() == 2 else u.view(1, -1)
-    B = u2.shape[0]
+    """Advance u (B x n float32 CUDA, in place) by nsteps RK4 steps (grouped operator:
+    u is the flat concatenation of the members' B_g x n_g blocks)."""
+    if isinstance(op, GroupedOperator):
+        u2, B = u.reshape(-1), op.B
+    else:
+        u2 = u if u.dim() == 2 else u.view(1, -1)
+        B = u2.shape[0]
     be, th = _per_traj(beta, B, u.device), _per_traj(theta, B, u.device)
     f = C.byref(forcing._struct()) if forcing is not None else None
     cp = _dptr(ckpt, torch.float32, "ckpt") if ckpt is not None else None

@@ -170,6 +170,15 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
                 break;
             }
         }
+        if (op->path == NF_GROUPED) {
+            // stage s reads the F buffer written by stage s-1: odd stages read buffer 0
+            st = tc_launch(op, (stage - 1) & 1, 1, nullptr, u, beta, theta, dt, stage, ckpt, C, cs);
+            if (st == NF_OK && op->profile) {
+                cudaError_t pe = cudaEventRecordWithFlags(op->prof_ev[2 * (stage - 1) + 1], cs, cudaEventRecordExternal);
+                if (pe != cudaSuccess) st = cuda_fail(pe, "cudaEventRecord", __FILE__, __LINE__);
+            }
+            continue;
+        }
         st = launch_nonlocal_partial(op, B, cs, &splits);
         if (st != NF_OK) break;
         if (op->profile) {
@@ -297,6 +306,7 @@ nf_status nf_operator_create(const float *x, const float *q, int64_t n, nf_kerne
 nf_status nf_operator_destroy(nf_operator *op) {
     if (!op) return NF_OK;
     destroy_graphs(op);
+    destroy_group(op);
     for (cudaEvent_t &ev : op->prof_ev)
         if (ev) cudaEventDestroy(ev);
     cudaFree(op->x4);
@@ -332,6 +342,12 @@ nf_status nf_nonlocal_apply(nf_operator *op, const float *u, int B, const float 
     NF_ARG(u && beta && theta && I, "u, beta, theta and I must be non-NULL");
     NF_ARG(B >= 1 && B <= 65535, "B = %d out of range", B);
     cudaStream_t s = as_stream(stream);
+    if (op->path == NF_GROUPED) {
+        NF_ARG(B == group_traj_total(op), "grouped operator: B = %d must equal the group's %d trajectories", B,
+               group_traj_total(op));
+        NF_TRY(tc_prep(op, u, beta, theta, false, 0, s));
+        return tc_launch(op, 0, 0, I, nullptr, beta, theta, 0.0, 0, nullptr, 1, s);
+    }
     NF_TRY(ensure_workspace(op, B, path_splits(op)));
     NF_TRY(launch_prep_g(op, u, B, beta, theta, false, s));
     int splits = 1;
@@ -352,6 +368,20 @@ nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt,
     const nf_forcing *F = nullptr;
     NF_TRY(check_forcing(g, &F));
     cudaStream_t s = as_stream(stream);
+    if (op->path == NF_GROUPED) {
+        NF_ARG(B == group_traj_total(op), "grouped operator: B = %d must equal the group's %d trajectories", B,
+               group_traj_total(op));
+        if (F->kind != NF_FORCE_NONE) return fail(NF_ERR_UNSUPPORTED, "grouped operators take no forcing");
+        const int64_t tot = group_state_total(op);
+        if (ckpt) NF_CUDA_TRY(cudaMemcpyAsync(ckpt, u, sizeof(float) * tot, cudaMemcpyDeviceToDevice, s));
+        if (nsteps == 0) return NF_OK;
+        cudaGraphExec_t exec = nullptr;
+        NF_TRY(rk4_step_graph(op, u, B, dt, beta, theta, *F, ckpt, ckpt ? C : 1, &exec));
+        NF_TRY(tc_prep(op, u, beta, theta, true, 0, s));
+        NF_TRY(launch_set_clock(op, t0, s));
+        for (int st = 0; st < nsteps; ++st) NF_CUDA_TRY(cudaGraphLaunch(exec, s));
+        return NF_OK;
+    }
     if (ckpt) NF_CUDA_TRY(cudaMemcpyAsync(ckpt, u, sizeof(float) * B * op->n, cudaMemcpyDeviceToDevice, s));
     if (nsteps == 0) return NF_OK;
     NF_TRY(ensure_workspace(op, B, path_splits(op)));

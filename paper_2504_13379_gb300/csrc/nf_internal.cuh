@@ -122,6 +122,10 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t h) { return __uint_
 constexpr int64_t kNodePad = 1024;
 
 struct nf_graph_cache;
+struct nf_group_state;
+
+// internal path id of a grouped operator (several bf16 hi+lo operators, tensor-core GEMM)
+constexpr int NF_GROUPED = 3;
 
 struct nf_operator {
     int64_t n = 0, n_pad = 0;
@@ -148,6 +152,7 @@ struct nf_operator {
     int *err = nullptr;             // device error flag
     double *t0_dev = nullptr;       // start time of the current nf_rk4_advance call
     nf_graph_cache *graphs = nullptr;
+    nf_group_state *group = nullptr;   // grouped operators only (members are not owned)
     // live kernel timing: events recorded around each stage's nonlocal launches
     bool profile = false;
     cudaEvent_t prof_ev[8] = {};
@@ -196,5 +201,14 @@ nf_status launch_set_clock(nf_operator *op, double t0, cudaStream_t s);
 nf_status launch_nonlocal_partial(nf_operator *op, int B, cudaStream_t s, int *splits_out);
 
 void destroy_graphs(nf_operator *op);
+
+// grouped tensor-core path (nf_tc.cu)
+void destroy_group(nf_operator *op);
+int group_traj_total(const nf_operator *op);
+int64_t group_state_total(const nf_operator *op);
+nf_status tc_prep(nf_operator *op, const float *u, const float *beta, const float *theta, bool copy_U, int buffer,
+                  cudaStream_t s);
+nf_status tc_launch(nf_operator *op, int parity, int mode, float *I, float *u, const float *beta, const float *theta,
+                    double dt, int stage, float *ckpt, int C, cudaStream_t s);
 
 }  // namespace nfi

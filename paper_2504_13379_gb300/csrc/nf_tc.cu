@@ -1,0 +1,614 @@
+// nf_tc.cu -- batched path: several node sets ("groups"), each with B_g trajectories,
+// advanced together with a grouped, persistent tcgen05 GEMM per RK4 stage.
+//
+// For group g with n_g nodes: D[i, b] = sum_j (Whi_ij Fhi_bj + Whi_ij Flo_bj + Wlo_ij Fhi_bj)
+// (the bf16 x 3 split; the Wlo Flo term, ~2^-18 relative, is dropped), accumulated in FP32
+// in tensor memory; I[b, i] = s_i D[i, b] with the operator's power-of-two row scales.  The
+// epilogue of the GEMM is the RK4 stage of Eq. (2.9): k_s = -U_s + I_s, the tableau update,
+// the next stage input and its firing rates f(U) split again into bf16 hi + lo, written
+// K-major for the next stage's B operand (ping-pong buffers).
+//
+// One CTA per SM, persistent over the (group, 128-row tile) list, 320 threads:
+//   warp 0      TMA producer: W hi/lo tiles (128 x 32) and F hi/lo tiles (N x 32),
+//               64-byte swizzle, into a 4-stage shared-memory ring
+//   warp 1      MMA issuer: tcgen05.mma kind::f16 (bf16 in, FP32 accumulate), M = 128,
+//               N = B_g (rounded to 16), K = 16 per instruction, 3 products per K step;
+//               owns the tensor-memory allocation (2 x 256 columns, double buffered)
+//   warps 2..9  epilogue: two warps per TMEM lane quarter (one TMEM lane = one row i),
+//               128 columns each; they drain the accumulator after every K chunk of 256
+//               and add it into FP32 registers, then run the fused RK4 stage and the
+//               next-stage bf16 split
+// Chunking K matters for accuracy: the tensor core's FP32 accumulation truncates when
+// aligning addends, an error that grows with the number of K steps summed in tensor
+// memory; 256-wide chunks added with round-to-nearest FP32 adds keep the long sums
+// (K up to 40,000 here) at the accuracy of the bf16 x 3 representation.
+// Every wait on an mbarrier is bounded; on timeout the kernel records NF_ERR_TIMEOUT,
+// stops issuing work, frees its tensor memory and returns.
+#include "nf_internal.cuh"
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+#include <cstring>
+#include <vector>
+
+namespace nfi {
+
+constexpr int TC_M = 128;
+constexpr int TC_BK = 32;           // K elements per stage: 64-byte rows
+constexpr int TC_NMAX = 256;
+constexpr int TC_STAGES = 4;
+constexpr int TC_MAXG = 4;
+constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int TC_CHUNK = 8;        // K blocks (256 elements) accumulated in tensor memory per chunk
+constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;            // 8 KB per plane
+constexpr uint32_t TC_B_BYTES = TC_NMAX * TC_BK * 2;         // 16 KB per plane (max N)
+constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
+
+struct TcGroup {
+    int n, B, n_mma, mtiles;
+    int64_t ldF;          // leading dimension (elements) of the F planes, [b][ldF]
+    int64_t state_off;    // offset of the group's B x n block in the concatenated state
+    int traj_off;         // offset of the group's trajectories in beta / theta
+    const float *rs;
+    uint16_t *Fhi_out, *Flo_out;
+};
+
+struct TcParams {
+    CUtensorMap tmA_hi[TC_MAXG], tmA_lo[TC_MAXG], tmB_hi[TC_MAXG], tmB_lo[TC_MAXG];
+    TcGroup grp[TC_MAXG];
+    int ngroups;
+    int tile_start[TC_MAXG + 1];
+    int mode;             // 0: write I, 1: RK4 stage
+    float *I;             // mode 0 output (concatenated B_g x n_g blocks)
+    float *u, *U, *ks;
+    const float *beta, *theta;
+    const double *t0;
+    double dt;
+    int stage;
+    long long *step_ctr;
+    unsigned *done_ctr;
+    float *ckpt;
+    int C;
+    int64_t state_total;
+    int *err;
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// K-major operand, 64-byte swizzle: 8-row x 64-byte atoms stacked every 512 bytes.
+__device__ __forceinline__ uint64_t sdesc_sw64(const void *p) {
+    const uint64_t a = smem_u32(p);
+    return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int tile_group(const TcParams &p, int t) {
+    int g = 0;
+    while (g + 1 < p.ngroups && t >= p.tile_start[g + 1]) ++g;
+    return g;
+}
+
+__device__ __forceinline__ float tc_firing(float u, float beta, float theta) {
+    return 1.0f / (1.0f + expf(-beta * (u - theta)));
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_constant__ TcParams p) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], acce[2];
+    __shared__ uint32_t tmem_base_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = p.tile_start[p.ngroups];
+    const long long step = *p.step_ctr;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 256);
+        }
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(2 * TC_NMAX));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    auto sA_hi = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES; };
+    auto sA_lo = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES + TC_A_BYTES; };
+    auto sB_hi = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES + 2 * TC_A_BYTES; };
+    auto sB_lo = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES + 2 * TC_A_BYTES + TC_B_BYTES; };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int g = tile_group(p, t);
+                const TcGroup &G = p.grp[g];
+                const int mt = t - p.tile_start[g];
+                const int nk = (G.n + TC_BK - 1) / TC_BK;
+                const uint32_t bytes = 2 * TC_A_BYTES + 2u * (uint32_t)G.n_mma * TC_BK * 2u;
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = (int)(it % TC_STAGES);
+                    const uint32_t ph = (it / TC_STAGES) & 1u;
+                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    tma_load_2d(sA_hi(s), &p.tmA_hi[g], kb * TC_BK, mt * TC_M, &full[s]);
+                    tma_load_2d(sA_lo(s), &p.tmA_lo[g], kb * TC_BK, mt * TC_M, &full[s]);
+                    tma_load_2d(sB_hi(s), &p.tmB_hi[g], kb * TC_BK, 0, &full[s]);
+                    tma_load_2d(sB_lo(s), &p.tmB_lo[g], kb * TC_BK, 0, &full[s]);
+                }
+            }
+            if (!ok) set_dev_error(p.err, DEV_TIMEOUT);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, ci = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int g = tile_group(p, t);
+                const TcGroup &G = p.grp[g];
+                const int nk = (G.n + TC_BK - 1) / TC_BK;
+                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(G.n_mma >> 3) << 17) |
+                                       ((uint32_t)(TC_M >> 4) << 24);
+                // K is accumulated in tensor memory one chunk at a time; the epilogue adds
+                // the chunks in FP32 registers (round to nearest)
+                for (int kc = 0; kc < nk && ok; kc += TC_CHUNK, ++ci) {
+                    const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
+                    if (!mbar_wait_bounded(&acce[ab], aph ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + ab * TC_NMAX;
+                    const int kend = min(nk, kc + TC_CHUNK);
+                    for (int kb = kc; kb < kend; ++kb, ++it) {
+                        const int s = (int)(it % TC_STAGES);
+                        const uint32_t ph = (it / TC_STAGES) & 1u;
+                        if (!mbar_wait_bounded(&full[s], ph)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ahi = sdesc_sw64(sA_hi(s)), alo = sdesc_sw64(sA_lo(s));
+                        const uint64_t bhi = sdesc_sw64(sB_hi(s)), blo = sdesc_sw64(sB_lo(s));
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k) {
+                            const uint64_t off = (uint64_t)((k * 32) >> 4);
+                            umma_bf16(d, ahi + off, bhi + off, idesc, ((kb - kc) | k) ? 1u : 0u);
+                            umma_bf16(d, ahi + off, blo + off, idesc, 1u);
+                            umma_bf16(d, alo + off, bhi + off, idesc, 1u);
+                        }
+                        umma_commit(&empty[s]);  // the slot is free once these MMAs have read it
+                    }
+                    if (!ok) break;
+                    umma_commit(&accf[ab]);      // chunk accumulator ready for the epilogue
+                }
+            }
+            if (!ok) set_dev_error(p.err, DEV_TIMEOUT);
+        }
+    } else {
+        // ------------------------------------------------------------- epilogue
+        // Two warps per TMEM lane quarter (warp & 3 selects the quarter a warp may
+        // access); each owns 128 of the up-to-256 accumulator columns.
+        const int q4 = warp & 3;
+        const int col0 = ((warp - 2) >> 2) * 128;
+        const int row_in_tile = 32 * q4 + lane;
+        uint32_t ci = 0;
+        const float dtf = (float)p.dt;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int g = tile_group(p, t);
+            const TcGroup &G = p.grp[g];
+            const int mt = t - p.tile_start[g];
+            const int nk = (G.n + TC_BK - 1) / TC_BK;
+            float acc[128];
+#pragma unroll
+            for (int c = 0; c < 128; ++c) acc[c] = 0.f;
+            for (int kc = 0; kc < nk; kc += TC_CHUNK, ++ci) {
+                const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
+                if (!mbar_wait_bounded(&accf[ab], aph)) {
+                    if (lane == 0) set_dev_error(p.err, DEV_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (col0 + 32 * c < G.n_mma) {  // warp-uniform
+                        uint32_t r[32];
+                        tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + ab * TC_NMAX + (uint32_t)(col0 + 32 * c), r);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[32 * c + j] += __uint_as_float(r[j]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acce[ab]);
+            }
+            if (!ok) break;
+            const int i = mt * TC_M + row_in_tile;
+            if (i >= G.n) continue;
+            const float si = G.rs[i];
+#pragma unroll
+            for (int c = 0; c < 128; ++c) {
+                const int b = col0 + c;
+                {
+                    if (b >= G.B) continue;
+                    const float I = si * acc[c];
+                    const int64_t idx = G.state_off + (int64_t)b * G.n + i;
+                    if (p.mode == 0) {
+                        p.I[idx] = I;
+                        continue;
+                    }
+                    const int tb = G.traj_off + b;
+                    const float bb = p.beta[tb], th = p.theta[tb];
+                    const float Uv = p.U[idx], uv = p.u[idx];
+                    const float k = -Uv + I;
+                    float Un;
+                    if (p.stage == 1) {
+                        p.ks[idx] = k;
+                        Un = fmaf(0.5f * dtf, k, uv);
+                    } else if (p.stage == 2) {
+                        p.ks[idx] = fmaf(2.f, k, p.ks[idx]);
+                        Un = fmaf(0.5f * dtf, k, uv);
+                    } else if (p.stage == 3) {
+                        p.ks[idx] = fmaf(2.f, k, p.ks[idx]);
+                        Un = fmaf(dtf, k, uv);
+                    } else {
+                        const float unew = fmaf(dtf / 6.f, p.ks[idx] + k, uv);
+                        p.u[idx] = unew;
+                        Un = unew;
+                        if (p.ckpt && ((step + 1) % p.C) == 0)
+                            p.ckpt[(int64_t)((step + 1) / p.C) * p.state_total + idx] = unew;
+                    }
+                    p.U[idx] = Un;
+                    const float f = tc_firing(Un, bb, th);
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+                    G.Fhi_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(hi);
+                    G.Flo_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(lo);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_NMAX));
+    }
+    if (p.mode == 1 && p.stage == 4 && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(p.done_ctr, 1u);
+        if (prev == gridDim.x - 1) {
+            *p.done_ctr = 0u;
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.step_ctr), 1ull);
+            __threadfence();
+        }
+    }
+}
+
+// F planes for all groups from u: hi/lo split of f(u); optionally U = u.
+struct TcPrepGroup {
+    int n, B;
+    int64_t ldF, state_off;
+    int traj_off;
+    uint16_t *Fhi, *Flo;
+};
+struct TcPrepArgs {
+    TcPrepGroup grp[TC_MAXG];
+    int ngroups;
+    const float *u;
+    float *U;
+    const float *beta, *theta;
+    int64_t total;
+};
+
+__global__ void tc_prep_kernel(TcPrepArgs a) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.total) return;
+    int g = 0;
+    while (g + 1 < a.ngroups && idx >= a.grp[g + 1].state_off) ++g;
+    const TcPrepGroup &G = a.grp[g];
+    const int64_t loc = idx - G.state_off;
+    const int b = (int)(loc / G.n);
+    const int64_t i = loc - (int64_t)b * G.n;
+    const float uv = a.u[idx];
+    const int tb = G.traj_off + b;
+    const float f = tc_firing(uv, a.beta[tb], a.theta[tb]);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+    G.Fhi[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(hi);
+    G.Flo[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(lo);
+    if (a.U) a.U[idx] = uv;
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static nf_status encode_fn(EncodeTiledFn *out) {
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        NF_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q));
+        if (!ptr || q != cudaDriverEntryPointSuccess) return fail(NF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    *out = fn;
+    return NF_OK;
+}
+
+// 2-D bf16 map over a row-major [rows][ld] plane, extent (cols x rows), box (TC_BK x box_rows).
+static nf_status make_map(CUtensorMap *m, const void *base, int64_t cols, int64_t rows, int64_t ld, int box_rows) {
+    EncodeTiledFn enc = nullptr;
+    NF_TRY(encode_fn(&enc));
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return NF_OK;
+}
+
+}  // namespace nfi
+
+// Group state lives in the grouped operator handle.
+struct nf_group_state {
+    int count = 0;
+    nf_operator *members[nfi::TC_MAXG] = {};
+    int B[nfi::TC_MAXG] = {};
+    int order[nfi::TC_MAXG] = {};          // groups in launch order (largest N first)
+    uint16_t *F[nfi::TC_MAXG][2][2] = {};  // [group][buffer][hi/lo]
+    int64_t state_total = 0;
+    int traj_total = 0;
+    nfi::TcParams params[2];               // [0]: reads F buffer 0, writes 1; [1]: reads 1, writes 0
+};
+
+namespace nfi {
+
+static nf_status build_group_params(nf_operator *op) {
+    nf_group_state *gs = op->group;
+    for (int par = 0; par < 2; ++par) {
+        TcParams &P = gs->params[par];
+        memset(&P, 0, sizeof(P));
+        P.ngroups = gs->count;
+        int tiles = 0;
+        int64_t soff = 0;
+        int toff = 0;
+        // state offsets follow the caller's member order; launch order is by N
+        int64_t state_off[TC_MAXG], traj_off[TC_MAXG];
+        for (int m = 0; m < gs->count; ++m) {
+            state_off[m] = soff;
+            traj_off[m] = toff;
+            soff += (int64_t)gs->B[m] * gs->members[m]->n;
+            toff += gs->B[m];
+        }
+        for (int k = 0; k < gs->count; ++k) {
+            const int m = gs->order[k];
+            nf_operator *mo = gs->members[m];
+            TcGroup &G = P.grp[k];
+            G.n = (int)mo->n;
+            G.B = gs->B[m];
+            G.n_mma = (G.B + 15) / 16 * 16;
+            G.mtiles = (int)ceil_div(mo->n, TC_M);
+            G.ldF = mo->n_pad;
+            G.state_off = state_off[m];
+            G.traj_off = (int)traj_off[m];
+            G.rs = mo->rs;
+            const int in = par, out = 1 - par;
+            G.Fhi_out = gs->F[m][out][0];
+            G.Flo_out = gs->F[m][out][1];
+            NF_TRY(make_map(&P.tmA_hi[k], mo->Whi, mo->n, mo->n, mo->n_pad, TC_M));
+            NF_TRY(make_map(&P.tmA_lo[k], mo->Wlo, mo->n, mo->n, mo->n_pad, TC_M));
+            NF_TRY(make_map(&P.tmB_hi[k], gs->F[m][in][0], mo->n, G.B, mo->n_pad, G.n_mma));
+            NF_TRY(make_map(&P.tmB_lo[k], gs->F[m][in][1], mo->n, G.B, mo->n_pad, G.n_mma));
+            P.tile_start[k] = tiles;
+            tiles += G.mtiles;
+        }
+        P.tile_start[gs->count] = tiles;
+        P.state_total = gs->state_total;
+        P.err = op->err;
+        P.step_ctr = op->step_ctr;
+        P.done_ctr = op->done_ctr;
+        P.t0 = op->t0_dev;
+    }
+    return NF_OK;
+}
+
+void destroy_group(nf_operator *op) {
+    if (!op->group) return;
+    nf_group_state *gs = op->group;
+    for (int m = 0; m < gs->count; ++m)
+        for (int b = 0; b < 2; ++b)
+            for (int h = 0; h < 2; ++h) cudaFree(gs->F[m][b][h]);
+    delete gs;
+    op->group = nullptr;
+}
+
+int group_traj_total(const nf_operator *op) { return op->group ? op->group->traj_total : 0; }
+int64_t group_state_total(const nf_operator *op) { return op->group ? op->group->state_total : 0; }
+
+nf_status tc_prep(nf_operator *op, const float *u, const float *beta, const float *theta, bool copy_U, int buffer,
+                  cudaStream_t s) {
+    nf_group_state *gs = op->group;
+    TcPrepArgs a{};
+    a.ngroups = gs->count;
+    int64_t soff = 0;
+    int toff = 0;
+    for (int m = 0; m < gs->count; ++m) {
+        TcPrepGroup &G = a.grp[m];
+        G.n = (int)gs->members[m]->n;
+        G.B = gs->B[m];
+        G.ldF = gs->members[m]->n_pad;
+        G.state_off = soff;
+        G.traj_off = toff;
+        G.Fhi = gs->F[m][buffer][0];
+        G.Flo = gs->F[m][buffer][1];
+        soff += (int64_t)G.B * G.n;
+        toff += G.B;
+    }
+    a.u = u;
+    a.U = copy_U ? op->U : nullptr;
+    a.beta = beta;
+    a.theta = theta;
+    a.total = soff;
+    tc_prep_kernel<<<(unsigned)ceil_div(a.total, 256), 256, 0, s>>>(a);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+// One grouped GEMM launch.  mode 0 writes I; mode 1 runs RK4 stage `stage`.
+nf_status tc_launch(nf_operator *op, int parity, int mode, float *I, float *u, const float *beta, const float *theta,
+                    double dt, int stage, float *ckpt, int C, cudaStream_t s) {
+    TcParams P = op->group->params[parity];
+    P.mode = mode;
+    P.I = I;
+    P.u = u;
+    P.U = op->U;
+    P.ks = op->ks;
+    P.beta = beta;
+    P.theta = theta;
+    P.dt = dt;
+    P.stage = stage;
+    P.ckpt = ckpt;
+    P.C = C;
+    const int ntiles = P.tile_start[P.ngroups];
+    const int grid = std::min(ntiles, num_sms());
+    tc_grouped_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(P);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+nf_status tc_init_attr() {
+    NF_CUDA_TRY(cudaFuncSetAttribute(tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    return NF_OK;
+}
+
+}  // namespace nfi
+
+using namespace nfi;
+
+extern "C" nf_status nf_operator_group(nf_operator *const *ops, const int *B_per_op, int count, void *stream,
+                                       nf_operator **grouped) {
+    clear_error();
+    NF_ARG(ops && B_per_op && grouped, "ops, B_per_op and grouped must be non-NULL");
+    *grouped = nullptr;
+    NF_ARG(count >= 1 && count <= TC_MAXG, "count = %d must be in 1..%d", count, TC_MAXG);
+    for (int m = 0; m < count; ++m) {
+        NF_ARG(ops[m], "ops[%d] is NULL", m);
+        NF_ARG(ops[m]->path == NF_DENSE_BF16X2, "ops[%d] must use the NF_DENSE_BF16X2 path", m);
+        NF_ARG(B_per_op[m] >= 1 && B_per_op[m] <= TC_NMAX, "B[%d] = %d must be in 1..%d", m, B_per_op[m], TC_NMAX);
+        NF_ARG(ops[m]->n >= TC_BK, "ops[%d] has n = %lld < %d nodes", m, (long long)ops[m]->n, TC_BK);
+    }
+    NF_TRY(tc_init_attr());
+    cudaStream_t s = as_stream(stream);
+    nf_operator *op = new nf_operator();
+    op->path = NF_GROUPED;
+    op->device = device_id();
+    op->kp = ops[0]->kp;
+    nf_group_state *gs = new nf_group_state();
+    op->group = gs;
+    gs->count = count;
+    int64_t total = 0;
+    int traj = 0;
+    for (int m = 0; m < count; ++m) {
+        gs->members[m] = ops[m];
+        gs->B[m] = B_per_op[m];
+        gs->order[m] = m;
+        total += (int64_t)B_per_op[m] * ops[m]->n;
+        traj += B_per_op[m];
+    }
+    std::stable_sort(gs->order, gs->order + count, [&](int a, int b) { return gs->B[a] > gs->B[b]; });
+    gs->state_total = total;
+    gs->traj_total = traj;
+    op->n = total;  // state length of one "trajectory" of the group (the concatenation)
+    op->n_pad = total;
+    auto cleanup = [&](nf_status st) {
+        nf_operator_destroy(op);
+        return st;
+    };
+    for (int m = 0; m < count; ++m)
+        for (int b = 0; b < 2; ++b)
+            for (int h = 0; h < 2; ++h) {
+                const size_t bytes = sizeof(uint16_t) * (size_t)B_per_op[m] * ops[m]->n_pad;
+                cudaError_t e = cudaMalloc(&gs->F[m][b][h], bytes);
+                if (e == cudaSuccess) e = cudaMemsetAsync(gs->F[m][b][h], 0, bytes, s);
+                if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(F)", __FILE__, __LINE__));
+            }
+    cudaError_t e = cudaMalloc(&op->step_ctr, 64);
+    if (e == cudaSuccess) e = cudaMemsetAsync(op->step_ctr, 0, 64, s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(ctr)", __FILE__, __LINE__));
+    op->done_ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(op->step_ctr) + 16);
+    op->err = reinterpret_cast<int *>(reinterpret_cast<char *>(op->step_ctr) + 32);
+    op->t0_dev = reinterpret_cast<double *>(reinterpret_cast<char *>(op->step_ctr) + 40);
+    e = cudaMalloc(&op->U, sizeof(float) * total);
+    if (e == cudaSuccess) e = cudaMalloc(&op->ks, sizeof(float) * total);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(state)", __FILE__, __LINE__));
+    op->state_cap = (size_t)total;
+    nf_status st = build_group_params(op);
+    if (st != NF_OK) return cleanup(st);
+    *grouped = op;
+    return NF_OK;
+}
