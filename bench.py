@@ -370,6 +370,8 @@ def run_ours(args, rank, world, local_rank):
                "pair_evals_per_s": 4.0 * n * n / (step_ms * 1e-3),
                "kernel_ms_per_launch": kern_ms / (4 * args.steps), "build_ms": build_ms,
                "e2e_ms_per_step": e2e_ms, "clocks": clocks}
+        if path == nf.MATRIX_FREE:
+            res["launch_shape"] = op.launch_shape()
         results[pname] = res
         op.close()
         del op

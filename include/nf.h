@@ -156,6 +156,10 @@ NF_API nf_status nf_operator_check(nf_operator *op, void *stream);
  * the four stage durations in milliseconds (host float[4]). */
 NF_API nf_status nf_operator_profile(nf_operator *op, int enable);
 NF_API nf_status nf_operator_kernel_ms(nf_operator *op, float *ms);
+/* Launch shape of the matrix-free pair kernel picked by the operator's autotuner (timed
+ * once per node count at creation): rows per warp, columns per shared-memory tile and
+ * column splits (host ints; -1 for other paths). */
+NF_API nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, int *tile_cols, int *splits);
 
 /* Nonlocal sum of Eq. (2.9) for B trajectories:
  *     I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]).

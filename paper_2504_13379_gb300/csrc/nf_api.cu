@@ -94,17 +94,20 @@ nf_status launch_nonlocal_partial(nf_operator *op, int B, cudaStream_t s, int *s
 }
 
 // ---------------------------------------------------------------- pack kernel
+// x4: coordinates as float4; xyz: coordinates times `scale` (= sqrt(log2 e) / s1) as
+// structure of arrays, so squared scaled distances are exponents of 2 for the SFU.
 __global__ void pack_nodes_kernel(const float *__restrict__ x, const float *__restrict__ q, int64_t n,
-                                  int64_t n_pad, float4 *__restrict__ x4, float *__restrict__ qp) {
+                                  int64_t n_pad, float scale, float4 *__restrict__ x4, float *__restrict__ xyz,
+                                  float *__restrict__ qp) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
-    if (j < n) {
-        x4[j] = make_float4(x[3 * j], x[3 * j + 1], x[3 * j + 2], 0.f);
-        qp[j] = q[j];
-    } else {
-        x4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        qp[j] = 0.f;
-    }
+    const bool in = j < n;
+    const float a = in ? x[3 * j] : 0.f, b = in ? x[3 * j + 1] : 0.f, c = in ? x[3 * j + 2] : 0.f;
+    x4[j] = make_float4(a, b, c, 0.f);
+    xyz[j] = a * scale;
+    xyz[n_pad + j] = b * scale;
+    xyz[2 * n_pad + j] = c * scale;
+    qp[j] = in ? q[j] : 0.f;
 }
 
 // ---------------------------------------------------------------- graph cache
@@ -278,15 +281,21 @@ nf_status nf_operator_create(const float *x, const float *q, int64_t n, nf_kerne
         if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #expr, __FILE__, __LINE__));    \
     } while (0)
     CREATE_TRY(cudaMalloc(&op->x4, op->n_pad * sizeof(float4)));
+    CREATE_TRY(cudaMalloc(&op->xyz, 3 * op->n_pad * sizeof(float)));
     CREATE_TRY(cudaMalloc(&op->q, op->n_pad * sizeof(float)));
     CREATE_TRY(cudaMalloc(&op->step_ctr, 64));
     CREATE_TRY(cudaMemsetAsync(op->step_ctr, 0, 64, s));
     op->done_ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(op->step_ctr) + 16);
     op->err = reinterpret_cast<int *>(reinterpret_cast<char *>(op->step_ctr) + 32);
     op->t0_dev = reinterpret_cast<double *>(reinterpret_cast<char *>(op->step_ctr) + 40);
-    pack_nodes_kernel<<<(unsigned)ceil_div(op->n_pad, 256), 256, 0, s>>>(x, q, n, op->n_pad, op->x4, op->q);
+    const float scale = std::sqrt(1.4426950408889634f) / kp.s1;
+    pack_nodes_kernel<<<(unsigned)ceil_div(op->n_pad, 256), 256, 0, s>>>(x, q, n, op->n_pad, scale, op->x4, op->xyz,
+                                                                         op->q);
     CREATE_TRY(cudaGetLastError());
-    if (path != NF_MATRIX_FREE) {
+    if (path == NF_MATRIX_FREE) {
+        nf_status st = mf_autotune(op, s);
+        if (st != NF_OK) return cleanup(st);
+    } else {
         const size_t entries = (size_t)op->n_pad * (size_t)op->n_pad;
         if (path == NF_DENSE_FP32) {
             CREATE_TRY(cudaMalloc(&op->W32, entries * sizeof(float)));
@@ -310,6 +319,7 @@ nf_status nf_operator_destroy(nf_operator *op) {
     for (cudaEvent_t &ev : op->prof_ev)
         if (ev) cudaEventDestroy(ev);
     cudaFree(op->x4);
+    cudaFree(op->xyz);
     cudaFree(op->q);
     cudaFree(op->W32);
     cudaFree(op->Whi);
@@ -408,6 +418,14 @@ nf_status nf_operator_kernel_ms(nf_operator *op, float *ms) {
     NF_ARG(op->profile && op->prof_ev[0], "profiling is not enabled on this operator");
     NF_CUDA_TRY(cudaEventSynchronize(op->prof_ev[7]));
     for (int st = 0; st < 4; ++st) NF_CUDA_TRY(cudaEventElapsedTime(&ms[st], op->prof_ev[2 * st], op->prof_ev[2 * st + 1]));
+    return NF_OK;
+}
+
+nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, int *tile_cols, int *splits) {
+    clear_error();
+    NF_ARG(op && rows_per_warp && tile_cols && splits, "arguments must be non-NULL");
+    *rows_per_warp = *tile_cols = *splits = -1;
+    if (op->path == NF_MATRIX_FREE) mf_launch_shape(op, rows_per_warp, tile_cols, splits);
     return NF_OK;
 }
 

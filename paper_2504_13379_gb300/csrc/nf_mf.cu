@@ -16,6 +16,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 namespace nfi {
 
@@ -136,6 +138,146 @@ mf_pair_kernel(const float4 *__restrict__ x4, const float *__restrict__ g, int64
 }
 
 // ----------------------------------------------------------------------------
+// Single-trajectory variant on packed FP32 pairs (f32x2: one instruction, two lanes of
+// the FMA pipe).  Column tiles are staged as structure-of-arrays (x, y, z, g), so a
+// lane reads two adjacent columns with one 8-byte load; each row's coordinates are held
+// duplicated in a 64-bit register pair.  Per two pairs: 3 SUB2, MUL2 + 2 FMA2 (r^2),
+// 2 MUL2 (exponent scaling), 4 MUFU.EX2, 2 FMA2 -- 7 issue slots per pair instead of 12,
+// the same FMA-pipe lane count, the same rounding as the scalar kernel.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 f2_sub(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_mul(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_fma(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 f2_pack(float lo, float hi) {
+    u64 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(u64 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 f2_ex2(u64 a) {
+    float lo, hi;
+    f2_unpack(a, lo, hi);
+    return f2_pack(ex2_sfu(lo), ex2_sfu(hi));
+}
+
+template <int TJ>
+struct MfPackedSmem {
+    float xs[2][TJ], ys[2][TJ], zs[2][TJ], gs[2][TJ];
+    uint64_t bar[2];
+};
+
+// xyz: pre-scaled coordinates as structure of arrays [x(n_pad) | y(n_pad) | z(n_pad)],
+// multiplied by sqrt(log2 e) / s1; g_all: B x n_pad firing rates (times q).
+template <int R, int TJ>
+__global__ void __launch_bounds__(MF_THREADS)
+mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, int64_t n_pad, int B,
+                      int b_base, int64_t jchunk, float k2, float A1, float A2, float *__restrict__ partial,
+                      int *__restrict__ err) {
+    __shared__ __align__(128) MfPackedSmem<TJ> sm;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int split = blockIdx.y;
+    const int64_t j0 = (int64_t)split * jchunk;
+    const int64_t j1 = min(n_pad, j0 + jchunk);
+    const int ntiles = (int)((j1 - j0) / TJ);
+    const int64_t row0 = ((int64_t)blockIdx.x * MF_WARPS + warp) * R;
+    constexpr uint32_t kTileBytes = 4 * TJ * 4;
+    const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
+    const int b = b_base + blockIdx.z;
+    const float *g = g_all + (int64_t)b * n_pad;
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int buf = t & 1;
+        const int64_t jt = j0 + (int64_t)t * TJ;
+        mbar_arrive_expect_tx(&sm.bar[buf], kTileBytes);
+        bulk_g2s(sm.xs[buf], X + jt, TJ * 4, &sm.bar[buf]);
+        bulk_g2s(sm.ys[buf], Y + jt, TJ * 4, &sm.bar[buf]);
+        bulk_g2s(sm.zs[buf], Z + jt, TJ * 4, &sm.bar[buf]);
+        bulk_g2s(sm.gs[buf], g + jt, TJ * 4, &sm.bar[buf]);
+    };
+    if (tid == 0) {
+        if (ntiles > 0) issue(0);
+        if (ntiles > 1) issue(1);
+    }
+    u64 xi[R], yi[R], zi[R], a1[R], a2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float x = X[row0 + r], y = Y[row0 + r], z = Z[row0 + r];
+        xi[r] = f2_pack(x, x);
+        yi[r] = f2_pack(y, y);
+        zi[r] = f2_pack(z, z);
+        a1[r] = 0ull;
+        a2[r] = 0ull;
+    }
+    // coordinates arrive pre-scaled by sqrt(log2(e)) / s1, so r2s = r^2 log2(e) / s1^2:
+    // e1 = 2^(-r2s), e2 = 2^(-k2 r2s) with k2 = s1^2 / s2^2
+    const u64 nk2 = f2_pack(-k2, -k2);
+    bool timed_out = false;
+    for (int t = 0; t < ntiles; ++t) {
+        const int buf = t & 1;
+        const bool ok = mbar_wait_bounded(&sm.bar[buf], (uint32_t)((t >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        if (tid == 0 && t >= 1 && t + 1 < ntiles) issue(t + 1);
+        const u64 *xs = reinterpret_cast<const u64 *>(sm.xs[buf]);
+        const u64 *ys = reinterpret_cast<const u64 *>(sm.ys[buf]);
+        const u64 *zs = reinterpret_cast<const u64 *>(sm.zs[buf]);
+        const u64 *gs = reinterpret_cast<const u64 *>(sm.gs[buf]);
+#pragma unroll 2
+        for (int jp = lane; jp < TJ / 2; jp += 32) {
+            const u64 xj = xs[jp], yj = ys[jp], zj = zs[jp], gj = gs[jp];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj), dz = f2_sub(zi[r], zj);
+                const u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                float s0, s1v;
+                f2_unpack(r2s, s0, s1v);
+                const u64 e1 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+                const u64 e2 = f2_ex2(f2_mul(r2s, nk2));
+                a1[r] = f2_fma(e1, gj, a1[r]);
+                a2[r] = f2_fma(e2, gj, a2[r]);
+            }
+        }
+    }
+    if (timed_out) {
+        if (tid == 0) {
+            set_dev_error(err, DEV_TIMEOUT);
+            for (int b = 0; b < 2; ++b) (void)mbar_wait_bounded(&sm.bar[b], 0), (void)mbar_wait_bounded(&sm.bar[b], 1);
+        }
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float p0, p1, q0, q1;
+        f2_unpack(a1[r], p0, p1);
+        f2_unpack(a2[r], q0, q1);
+        float v = A1 * (p0 + p1) - A2 * (q0 + q1);
+        v = warp_sum(v);
+        if (lane == 0) partial[((int64_t)split * B + b) * n_pad + row0 + r] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // split planner: (row blocks x column splits) items of equal cost; pick the number
 // of splits that best fills whole waves of resident blocks.
 SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm) {
@@ -207,36 +349,143 @@ static int mf_resident() {
     return std::max(nb, 1);
 }
 
-// Rows per warp: 4 for large problems, 2 for small ones (more blocks to fill the GPU).
-static int mf_rows_per_warp(int64_t n_pad) { return n_pad >= 16384 ? 4 : 2; }
+// Launch shapes of the packed kernel the autotuner chooses from: rows per warp, tile width.
+struct MfVariant {
+    int R, TJ;
+};
+constexpr MfVariant kMfVariants[] = {{2, 512}, {4, 512}, {4, 1024}, {8, 1024}};
+constexpr int kNumMfVariants = 4;
+
+template <int R, int TJ>
+static int packed_resident() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mf_pair_packed_kernel<R, TJ>, MF_THREADS, 0);
+    return std::max(nb, 1);
+}
+
+static int variant_resident(int v) {
+    switch (v) {
+        case 0: return packed_resident<2, 512>();
+        case 1: return packed_resident<4, 512>();
+        case 2: return packed_resident<4, 1024>();
+        default: return packed_resident<8, 1024>();
+    }
+}
+
+template <int R, int TJ>
+static void launch_packed(nf_operator *op, int B, int b_base, int groups, const SplitPlan &pl, cudaStream_t s) {
+    const nf_kernel &k = op->kp;
+    const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
+    dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, (unsigned)groups);
+    mf_pair_packed_kernel<R, TJ><<<grid, MF_THREADS, 0, s>>>(op->xyz, op->g, op->n_pad, B, b_base, pl.jchunk, k2, k.A1,
+                                                             k.A2, op->partial, op->err);
+}
+
+static nf_status launch_mf_packed(nf_operator *op, int B, int b_base, int groups, const SplitPlan &pl,
+                                  cudaStream_t s) {
+    switch (op->mf_variant) {
+        case 0: launch_packed<2, 512>(op, B, b_base, groups, pl, s); break;
+        case 1: launch_packed<4, 512>(op, B, b_base, groups, pl, s); break;
+        case 2: launch_packed<4, 1024>(op, B, b_base, groups, pl, s); break;
+        default: launch_packed<8, 1024>(op, B, b_base, groups, pl, s); break;
+    }
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+// Default before (or without) autotuning: small node sets want more, smaller blocks.
+static int default_variant(int64_t n_pad) { return n_pad >= 16384 ? 1 : 0; }
+
+static SplitPlan variant_plan(int64_t n_pad, int v) {
+    return plan_splits(n_pad, MF_WARPS * kMfVariants[v].R, kMfVariants[v].TJ, variant_resident(v));
+}
 
 SplitPlan mf_plan(nf_operator *op) {
-    const int R = mf_rows_per_warp(op->n_pad);
-    const int res = (R == 4) ? mf_resident<1, 4>() : mf_resident<1, 2>();
-    return plan_splits(op->n_pad, MF_WARPS * R, MF_TJ, res);
+    if (op->mf_variant < 0) op->mf_variant = default_variant(op->n_pad);
+    return variant_plan(op->n_pad, op->mf_variant);
+}
+
+void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits) {
+    const SplitPlan pl = mf_plan(op);
+    *R = kMfVariants[op->mf_variant].R;
+    *TJ = kMfVariants[op->mf_variant].TJ;
+    *splits = pl.splits;
+}
+
+// Rows per warp of the scalar multi-trajectory kernel (2 or 4 are instantiated).
+static int mf_rows_per_warp(int64_t n_pad) { return n_pad >= 16384 ? 4 : 2; }
+
+// Time every launch shape once on this operator's size and keep the fastest (cached
+// per padded size and device).  Runs outside any stream capture.
+nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int64_t>, int> cache;
+    const auto key = std::make_pair(op->device, op->n_pad);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            op->mf_variant = it->second;
+            return NF_OK;
+        }
+    }
+    int max_splits = 1;
+    for (int v = 0; v < kNumMfVariants; ++v) max_splits = std::max(max_splits, variant_plan(op->n_pad, v).splits);
+    NF_TRY(ensure_workspace(op, 1, max_splits));
+    cudaEvent_t e0, e1;
+    NF_CUDA_TRY(cudaEventCreate(&e0));
+    NF_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = default_variant(op->n_pad);
+    for (int v = 0; v < kNumMfVariants; ++v) {
+        op->mf_variant = v;
+        const SplitPlan pl = variant_plan(op->n_pad, v);
+        NF_TRY(launch_mf_packed(op, 1, 0, 1, pl, s));  // warm-up
+        NF_CUDA_TRY(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 2; ++rep) NF_TRY(launch_mf_packed(op, 1, 0, 1, pl, s));
+        NF_CUDA_TRY(cudaEventRecord(e1, s));
+        NF_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    op->mf_variant = best_v;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best_v;
+    return NF_OK;
 }
 
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
+    // the column splits (and so the partial-sum layout) come from the packed kernel's
+    // plan; the scalar multi-trajectory kernels block rows their own way over the same splits
     const SplitPlan pl = mf_plan(op);
     const int R = mf_rows_per_warp(op->n_pad);
+    SplitPlan spl = pl;
+    spl.rows_per_block = MF_WARPS * R;
+    spl.row_blocks = op->n_pad / spl.rows_per_block;
     int b = 0;
     auto run = [&](int nb) -> nf_status {
         const int groups = (B - b) / nb;
         if (groups <= 0) return NF_OK;
         nf_status st = NF_OK;
-        if (R == 4) {
+        if (nb == 1) {
+            st = launch_mf_packed(op, B, b, groups, pl, s);
+        } else if (R == 4) {
             switch (nb) {
-                case 8: st = launch_mf_group<8, 4>(op, B, b, groups, pl, s); break;
-                case 4: st = launch_mf_group<4, 4>(op, B, b, groups, pl, s); break;
-                case 2: st = launch_mf_group<2, 4>(op, B, b, groups, pl, s); break;
-                default: st = launch_mf_group<1, 4>(op, B, b, groups, pl, s); break;
+                case 8: st = launch_mf_group<8, 4>(op, B, b, groups, spl, s); break;
+                case 4: st = launch_mf_group<4, 4>(op, B, b, groups, spl, s); break;
+                default: st = launch_mf_group<2, 4>(op, B, b, groups, spl, s); break;
             }
         } else {
             switch (nb) {
-                case 8: st = launch_mf_group<8, 2>(op, B, b, groups, pl, s); break;
-                case 4: st = launch_mf_group<4, 2>(op, B, b, groups, pl, s); break;
-                case 2: st = launch_mf_group<2, 2>(op, B, b, groups, pl, s); break;
-                default: st = launch_mf_group<1, 2>(op, B, b, groups, pl, s); break;
+                case 8: st = launch_mf_group<8, 2>(op, B, b, groups, spl, s); break;
+                case 4: st = launch_mf_group<4, 2>(op, B, b, groups, spl, s); break;
+                default: st = launch_mf_group<2, 2>(op, B, b, groups, spl, s); break;
             }
         }
         b += groups * nb;
