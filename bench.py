@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched tensor-core section")
+    ap.add_argument("--batched-scale", type=float, default=1.0,
+                    help="scale the batched node counts (profiling captures use a smaller case)")
     return ap.parse_args()
 
 
@@ -187,7 +189,8 @@ def run_batched(args, dev, steps):
     from nodesets import workloads as W
 
     stream = torch.cuda.current_stream(dev)
-    wls = W.batched()
+    sizes = tuple(int(round(s * args.batched_scale / 2) * 2) for s in (40000, 8000, 15000, 30000))
+    wls = W.batched(sizes=sizes)
     qs, xs = [], []
     t0 = time.perf_counter()
     for wl in wls:
@@ -206,7 +209,8 @@ def run_batched(args, dev, steps):
     beta = torch.cat([torch.as_tensor(wl.beta.astype(np.float32), device=dev) for wl in wls])
     theta = torch.cat([torch.as_tensor(wl.theta.astype(np.float32), device=dev) for wl in wls])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    out = {"workload": "sphere 40000 x 256 traj + ellipsoids (1:0.8:0.6) 8000/15000/30000 x 64 traj, k=32 deg=3",
+    out = {"workload": f"sphere {sizes[0]} x 256 traj + ellipsoids (1:0.8:0.6) {sizes[1]}/{sizes[2]}/{sizes[3]} "
+                       f"x 64 traj, k=32 deg=3",
            "setup_ms": setup_ms, "pair_evals_per_stage": pairs_per_stage}
 
     def timed(step_fn, nsteps, kernel_ms_fn=None):

@@ -42,6 +42,7 @@ constexpr int TC_STAGES = 4;
 constexpr int TC_MAXG = 4;
 constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int TC_CHUNK = 8;        // K blocks (256 elements) accumulated in tensor memory per chunk
+constexpr int TC_EPI_BATCH = 4;    // trajectory columns per batch of epilogue loads
 constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;            // 8 KB per plane
 constexpr uint32_t TC_B_BYTES = TC_NMAX * TC_BK * 2;         // 16 KB per plane (max N)
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
@@ -132,6 +133,7 @@ __device__ __forceinline__ float tc_firing(float u, float beta, float theta) {
     return 1.0f / (1.0f + expf(-beta * (u - theta)));
 }
 
+template <int STAGE>  // 0: write I (nonlocal apply); 1..4: fused RK4 stage
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_constant__ TcParams p) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
@@ -283,44 +285,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
             const int i = mt * TC_M + row_in_tile;
             if (i >= G.n) continue;
             const float si = G.rs[i];
+            const int64_t base = G.state_off + i;
+            // TC_EPI_BATCH trajectory columns at a time: every load of the batch is issued before
+            // any result is used, so global-memory latency overlaps
 #pragma unroll
-            for (int c = 0; c < 128; ++c) {
-                const int b = col0 + c;
-                {
-                    if (b >= G.B) continue;
-                    const float I = si * acc[c];
-                    const int64_t idx = G.state_off + (int64_t)b * G.n + i;
-                    if (p.mode == 0) {
-                        p.I[idx] = I;
-                        continue;
+            for (int c0 = 0; c0 < 128; c0 += TC_EPI_BATCH) {
+                if (col0 + c0 >= G.B) break;
+                if constexpr (STAGE == 0) {
+#pragma unroll
+                    for (int j = 0; j < TC_EPI_BATCH; ++j) {
+                        const int b = col0 + c0 + j;
+                        if (b < G.B) p.I[base + (int64_t)b * G.n] = si * acc[c0 + j];
                     }
-                    const int tb = G.traj_off + b;
-                    const float bb = p.beta[tb], th = p.theta[tb];
-                    const float Uv = p.U[idx], uv = p.u[idx];
-                    const float k = -Uv + I;
-                    float Un;
-                    if (p.stage == 1) {
-                        p.ks[idx] = k;
-                        Un = fmaf(0.5f * dtf, k, uv);
-                    } else if (p.stage == 2) {
-                        p.ks[idx] = fmaf(2.f, k, p.ks[idx]);
-                        Un = fmaf(0.5f * dtf, k, uv);
-                    } else if (p.stage == 3) {
-                        p.ks[idx] = fmaf(2.f, k, p.ks[idx]);
-                        Un = fmaf(dtf, k, uv);
-                    } else {
-                        const float unew = fmaf(dtf / 6.f, p.ks[idx] + k, uv);
-                        p.u[idx] = unew;
-                        Un = unew;
-                        if (p.ckpt && ((step + 1) % p.C) == 0)
-                            p.ckpt[(int64_t)((step + 1) / p.C) * p.state_total + idx] = unew;
+                } else {
+                    float Uv[TC_EPI_BATCH], uv[TC_EPI_BATCH], kv[TC_EPI_BATCH], bb[TC_EPI_BATCH], th[TC_EPI_BATCH];
+#pragma unroll
+                    for (int j = 0; j < TC_EPI_BATCH; ++j) {
+                        const int b = min(col0 + c0 + j, G.B - 1);
+                        const int64_t idx = base + (int64_t)b * G.n;
+                        Uv[j] = p.U[idx];
+                        uv[j] = p.u[idx];
+                        kv[j] = (STAGE > 1) ? p.ks[idx] : 0.f;
+                        bb[j] = __ldg(p.beta + G.traj_off + b);
+                        th[j] = __ldg(p.theta + G.traj_off + b);
                     }
-                    p.U[idx] = Un;
-                    const float f = tc_firing(Un, bb, th);
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-                    G.Fhi_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(hi);
-                    G.Flo_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(lo);
+#pragma unroll
+                    for (int j = 0; j < TC_EPI_BATCH; ++j) {
+                        const int b = col0 + c0 + j;
+                        if (b >= G.B) break;
+                        const int64_t idx = base + (int64_t)b * G.n;
+                        const float k = -Uv[j] + si * acc[c0 + j];
+                        float Un;
+                        if constexpr (STAGE == 1) {
+                            p.ks[idx] = k;
+                            Un = fmaf(0.5f * dtf, k, uv[j]);
+                        } else if constexpr (STAGE == 2) {
+                            p.ks[idx] = fmaf(2.f, k, kv[j]);
+                            Un = fmaf(0.5f * dtf, k, uv[j]);
+                        } else if constexpr (STAGE == 3) {
+                            p.ks[idx] = fmaf(2.f, k, kv[j]);
+                            Un = fmaf(dtf, k, uv[j]);
+                        } else {
+                            Un = fmaf(dtf / 6.f, kv[j] + k, uv[j]);
+                            p.u[idx] = Un;
+                            if (p.ckpt && ((step + 1) % p.C) == 0)
+                                p.ckpt[(int64_t)((step + 1) / p.C) * p.state_total + idx] = Un;
+                        }
+                        p.U[idx] = Un;
+                        const float f = tc_firing(Un, bb[j], th[j]);
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+                        G.Fhi_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(hi);
+                        G.Flo_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(lo);
+                    }
                 }
             }
         }
@@ -331,7 +348,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_NMAX));
     }
-    if (p.mode == 1 && p.stage == 4 && threadIdx.x == 0) {
+    if (STAGE == 4 && threadIdx.x == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(p.done_ctr, 1u);
         if (prev == gridDim.x - 1) {
@@ -536,13 +553,23 @@ nf_status tc_launch(nf_operator *op, int parity, int mode, float *I, float *u, c
     P.C = C;
     const int ntiles = P.tile_start[P.ngroups];
     const int grid = std::min(ntiles, num_sms());
-    tc_grouped_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(P);
+    switch (mode == 0 ? 0 : stage) {
+        case 0: tc_grouped_kernel<0><<<grid, TC_THREADS, TC_SMEM, s>>>(P); break;
+        case 1: tc_grouped_kernel<1><<<grid, TC_THREADS, TC_SMEM, s>>>(P); break;
+        case 2: tc_grouped_kernel<2><<<grid, TC_THREADS, TC_SMEM, s>>>(P); break;
+        case 3: tc_grouped_kernel<3><<<grid, TC_THREADS, TC_SMEM, s>>>(P); break;
+        default: tc_grouped_kernel<4><<<grid, TC_THREADS, TC_SMEM, s>>>(P); break;
+    }
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
 }
 
 nf_status tc_init_attr() {
-    NF_CUDA_TRY(cudaFuncSetAttribute(tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    NF_CUDA_TRY(cudaFuncSetAttribute(tc_grouped_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    NF_CUDA_TRY(cudaFuncSetAttribute(tc_grouped_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    NF_CUDA_TRY(cudaFuncSetAttribute(tc_grouped_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    NF_CUDA_TRY(cudaFuncSetAttribute(tc_grouped_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    NF_CUDA_TRY(cudaFuncSetAttribute(tc_grouped_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     return NF_OK;
 }
 
