@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched tensor-core section")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation section")
     ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="scale the batched node counts (profiling captures use a smaller case)")
     return ap.parse_args()
@@ -112,6 +113,23 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank timings (a timing reduction, not a data path)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """Units processed by all replicas per second, timed by the slowest rank."""
+    return world * float(units_per_rank) / (max_ms * 1e-3)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -286,6 +304,56 @@ def run_batched(args, dev, steps):
     return out
 
 
+def run_adjoint(args, dev):
+    """Differentiation workload: gradient of L = |u(T) - u_target|^2 w.r.t. the kernel
+    parameters and u0 through the discrete RK4 adjoint (checkpoints every C steps)."""
+    import torch
+
+    import paper_2504_13379_gb300 as nf
+    from nodesets import workloads as W
+
+    wl = W.adjoint()
+    n, C, nsteps, dt = wl.n, wl.extra["C"], wl.nsteps, wl.dt
+    nodes = torch.as_tensor(wl.ns.nodes, device=dev)
+    tris = torch.as_tensor(wl.ns.tris, device=dev)
+    st = nf.nf_build_stencils(nodes, tris, wl.k)
+    q = nf.nf_quad_weights(nodes, tris, st, wl.deg, normals=torch.as_tensor(wl.ns.normals, device=dev))
+    x32 = torch.as_tensor(wl.ns.nodes.astype(np.float32), device=dev)
+    q32 = q.to(torch.float32).contiguous()
+    beta, theta = float(wl.beta[0]), float(wl.theta[0])
+    u0 = torch.as_tensor(wl.u0.astype(np.float32), device=dev)
+    target = u0.clone()
+    op_t = nf.Operator(x32, q32, wl.extra["target_kernel"], nf.MATRIX_FREE)
+    nf.nf_rk4_advance(op_t, target, 0.0, dt, nsteps, beta, theta)
+    op_t.close()
+    op = nf.Operator(x32, q32, wl.kernel, nf.MATRIX_FREE)
+    ck = torch.empty((nsteps // C + 1, 1, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def gradient():
+        u = u0.clone()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        nf.nf_rk4_advance(op, u, 0.0, dt, nsteps, beta, theta, ckpt=ck, C_every=C)
+        b.record(stream)
+        gu, gk = nf.nf_adjoint(op, ck, C, 0.0, dt, nsteps, beta, theta, 2.0 * (u - target))
+        c.record(stream)
+        c.synchronize()
+        return a.elapsed_time(b), b.elapsed_time(c), float(((u - target) ** 2).sum()), gk[0].tolist()
+
+    gradient()  # warm-up (graph capture, allocations)
+    fwd_ms, adj_ms, loss, gk = gradient()
+    op.check()
+    op.close()
+    pairs = float(n) * n
+    return {"workload": f"torus R=1 r=0.4 n={n} k={wl.k} deg={wl.deg}, {nsteps} RK4 steps dt={dt}, checkpoints every {C}",
+            "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "gradient_ms": fwd_ms + adj_ms, "loss": loss,
+            "grad_kernel": dict(zip(["A1", "s1", "A2", "s2"], gk)),
+            "adjoint_pair_evals_per_s": pairs * 4 * nsteps * 2 / (adj_ms * 1e-3),
+            "note": "adjoint time includes the forward recomputation of each segment (4 nsteps stages) "
+                    "and 4 nsteps adjoint pair passes"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -385,11 +453,8 @@ def run_ours(args, rank, world, local_rank):
     r = results[best]
     step_ms = r["ms_per_step"]
     e2e_ms = r["e2e_ms_per_step"]
-    if world > 1:
-        t = torch.tensor([step_ms, e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms, e2e_ms = float(t[0]), float(t[1])
-    value = world * 4.0 * n * n / (step_ms * 1e-3)
+    step_ms, e2e_ms = max_over_ranks([step_ms, e2e_ms], world, dev)
+    value = whole_job_rate(4.0 * n * n, world, step_ms)
     pk = peaks()
     clocks = r["clocks"]
     kms = r["kernel_ms_per_launch"]
@@ -426,6 +491,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batched:
         line["batched"] = run_batched(args, dev, args.steps)
         line["gpu_launches"] += 4 * args.steps  # tensor-core path: one grouped GEMM per stage
+    if not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, q.double().cpu().numpy(), args.cpu_seconds)
     return line if rank == 0 else None

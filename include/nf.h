@@ -161,6 +161,13 @@ NF_API nf_status nf_operator_kernel_ms(nf_operator *op, float *ms);
  * column splits (host ints; -1 for other paths). */
 NF_API nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, int *tile_cols, int *splits);
 
+/* Failure-path self-test (no paper counterpart): launches a one-warp kernel whose
+ * mbarrier wait can never complete, with a short poll limit.  The wait gives up, the
+ * kernel records a timeout and returns; the call synchronises `stream` and returns
+ * NF_ERR_TIMEOUT (anything else means the bounded-wait machinery is broken).  The CUDA
+ * context stays usable afterwards. */
+NF_API nf_status nf_selftest_timeout(void *stream);
+
 /* Nonlocal sum of Eq. (2.9) for B trajectories:
  *     I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]).
  *   u      B x n  FP32   states (trajectory-major)

@@ -41,7 +41,7 @@ STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINIT
 EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights", "nf_operator_create",
            "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
            "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms",
-           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape"]
+           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout"]
 
 
 class NFError(RuntimeError):
@@ -92,6 +92,7 @@ def lib(path: str | None = None):
     L.nf_operator_profile.argtypes = [_vp, C.c_int]
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
     L.nf_operator_launch_shape.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nf_selftest_timeout.argtypes = [_vp]
     L.nf_nonlocal_apply.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]
     L.nf_nonlocal_apply_noalloc.argtypes = [_vp, _vp, _i64, _Kernel, _vp, C.c_float, C.c_float, _vp, _vp]
     L.nf_mms_sphere_eigs.argtypes = [_Kernel, C.POINTER(C.c_double)]

@@ -110,6 +110,20 @@ __global__ void pack_nodes_kernel(const float *__restrict__ x, const float *__re
     qp[j] = in ? q[j] : 0.f;
 }
 
+// Failure-path self-test: waits on an mbarrier whose phase nothing completes, with a
+// small poll limit; the wait gives up and records a timeout instead of hanging.
+__global__ void selftest_wait_kernel(int *flag, long long polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    bool done = false;
+    for (long long i = 0; i < polls && !done; ++i) done = mbar_try_wait(&bar, 0);
+    if (!done && threadIdx.x == 0) set_dev_error(flag, DEV_TIMEOUT);
+}
+
 // ---------------------------------------------------------------- graph cache
 }  // namespace nfi
 
@@ -419,6 +433,22 @@ nf_status nf_operator_kernel_ms(nf_operator *op, float *ms) {
     NF_CUDA_TRY(cudaEventSynchronize(op->prof_ev[7]));
     for (int st = 0; st < 4; ++st) NF_CUDA_TRY(cudaEventElapsedTime(&ms[st], op->prof_ev[2 * st], op->prof_ev[2 * st + 1]));
     return NF_OK;
+}
+
+nf_status nf_selftest_timeout(void *stream) {
+    clear_error();
+    cudaStream_t s = as_stream(stream);
+    int *flag = nullptr;
+    NF_CUDA_TRY(cudaMallocAsync(&flag, sizeof(int), s));
+    NF_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    selftest_wait_kernel<<<1, 32, 0, s>>>(flag, 1 << 12);
+    NF_CUDA_TRY(cudaGetLastError());
+    int h = 0;
+    NF_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NF_CUDA_TRY(cudaFreeAsync(flag, s));
+    NF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h == DEV_TIMEOUT) return fail(NF_ERR_TIMEOUT, "bounded wait gave up as expected (self-test)");
+    return fail(NF_ERR_CUDA, "self-test wait did not report a timeout (flag %d)", h);
 }
 
 nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, int *tile_cols, int *splits) {
