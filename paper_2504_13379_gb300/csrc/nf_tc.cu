@@ -8,48 +8,58 @@
 // the next stage input and its firing rates f(U) split again into bf16 hi + lo, written
 // K-major for the next stage's B operand (ping-pong buffers).
 //
-// One CTA per SM, persistent over the (group, 128-row tile) list, 320 threads:
-//   warp 0      TMA producer: W hi/lo tiles (128 x 32) and F hi/lo tiles (N x 32),
-//               64-byte swizzle, into a 4-stage shared-memory ring
-//   warp 1      MMA issuer: tcgen05.mma kind::f16 (bf16 in, FP32 accumulate), M = 128,
-//               N = B_g (rounded to 16), K = 16 per instruction, 3 products per K step;
-//               owns the tensor-memory allocation (2 x 256 columns, double buffered)
-//   warps 2..9  epilogue: two warps per TMEM lane quarter (one TMEM lane = one row i),
-//               128 columns each; they drain the accumulator after every K chunk of 256
-//               and add it into FP32 registers, then run the fused RK4 stage and the
-//               next-stage bf16 split
+// Two-SM tiles.  CTAs run in clusters of two on neighbouring SMs; a pair owns 256 output rows
+// and issues tcgen05.mma.cta_group::2 with M = 256: each CTA stages its own 128 rows of W hi/lo
+// and one half of the F hi/lo tile (N/2 trajectory rows), so a pipeline stage is 32 KB per CTA
+// instead of 48 KB and the ring is 7 stages deep -- about 2.3x the bytes in flight per SM of a
+// one-SM M = 128 tile at N = 256, and half the L2 -> SM traffic for the shared F tile.
+// 320 threads per CTA, one CTA per SM, persistent over a host-balanced list of pair tiles:
+//   warp 0      TMA producer (both CTAs): W hi/lo tiles (128 x 32) and half F tiles
+//               (N/2 x 32), 64-byte swizzle; completion of both CTAs' copies is counted on
+//               the leader CTA's "full" barrier
+//   warp 1      owns the tensor-memory allocation (2 x 256 columns per CTA, double buffered);
+//               in the leader CTA (rank 0) lane 0 issues the MMAs, N = B_g rounded to 16,
+//               K = 16 per instruction, 3 products per K step, and commits to the "empty" and
+//               "accumulator full" barriers of both CTAs (multicast)
+//   warps 2..9  epilogue (both CTAs): two warps per TMEM lane quarter (one TMEM lane = one
+//               row i), 128 columns each; they drain the accumulator after every K chunk of
+//               256, add it into FP32 registers, release the chunk buffer on the leader's
+//               barrier, then run the fused RK4 stage and the next-stage bf16 split
 // Chunking K matters for accuracy: the tensor core's FP32 accumulation truncates when
 // aligning addends, an error that grows with the number of K steps summed in tensor
 // memory; 256-wide chunks added with round-to-nearest FP32 adds keep the long sums
 // (K up to 40,000 here) at the accuracy of the bf16 x 3 representation.
 // Every wait on an mbarrier is bounded; on timeout the kernel records NF_ERR_TIMEOUT,
-// stops issuing work, frees its tensor memory and returns.
+// stops issuing work, lets copies in flight land, frees its tensor memory and returns.
 #include "nf_internal.cuh"
 
 #include <cuda.h>
 
 #include <algorithm>
-#include <mutex>
 #include <cstring>
+#include <mutex>
+#include <numeric>
 #include <vector>
 
 namespace nfi {
 
-constexpr int TC_M = 128;
-constexpr int TC_BK = 32;           // K elements per stage: 64-byte rows
+constexpr int TC_M = 128;          // rows per CTA
+constexpr int TC_PAIR_M = 256;     // rows per cluster pair (MMA M)
+constexpr int TC_BK = 32;          // K elements per stage: 64-byte rows
 constexpr int TC_NMAX = 256;
-constexpr int TC_STAGES = 4;
+constexpr int TC_STAGES = 7;
 constexpr int TC_MAXG = 4;
-constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 TMEM + MMA, warps 2..9 epilogue
+constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_CHUNK = 8;        // K blocks (256 elements) accumulated in tensor memory per chunk
 constexpr int TC_EPI_BATCH = 4;    // trajectory columns per batch of epilogue loads
-constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;            // 8 KB per plane
-constexpr uint32_t TC_B_BYTES = TC_NMAX * TC_BK * 2;         // 16 KB per plane (max N)
-constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;             // 8 KB per plane
+constexpr uint32_t TC_BH_BYTES = (TC_NMAX / 2) * TC_BK * 2;   // 8 KB per plane: half of N = 256
+constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_BH_BYTES;
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
 
 struct TcGroup {
-    int n, B, n_mma, mtiles;
+    int n, B, n_mma, mtiles;  // mtiles: pair tiles of 256 rows
     int64_t ldF;          // leading dimension (elements) of the F planes, [b][ldF]
     int64_t state_off;    // offset of the group's B x n block in the concatenated state
     int traj_off;         // offset of the group's trajectories in beta / theta
@@ -62,6 +72,8 @@ struct TcParams {
     TcGroup grp[TC_MAXG];
     int ngroups;
     int tile_start[TC_MAXG + 1];
+    const int *sched;      // pair tiles in processing order, cluster c owns sched[sched_off[c] ..]
+    const int *sched_off;  // [clusters + 1]
     int mode;             // 0: write I, 1: RK4 stage
     float *I;             // mode 0 output (concatenated B_g x n_g blocks)
     float *u, *U, *ks;
@@ -78,11 +90,30 @@ struct TcParams {
 };
 
 // ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Shared-cluster address of this CTA's shared variable `p` as seen in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_u32(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+// 2-D tiled load into this CTA's shared memory; the transaction bytes are counted on the
+// barrier at shared-cluster address `bar` (the leader CTA's barrier, for both CTAs).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
 
@@ -92,23 +123,43 @@ __device__ __forceinline__ uint64_t sdesc_sw64(const void *p) {
     return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+// Arrive (once) on the barrier at the same shared-memory offset in both CTAs of the pair
+// when all previously issued MMAs of this thread have completed.
+__device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t *bar, uint32_t parity) {
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
@@ -134,85 +185,92 @@ __device__ __forceinline__ float tc_firing(float u, float beta, float theta) {
 }
 
 template <int STAGE>  // 0: write I (nonlocal apply); 1..4: fused RK4 stage
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_constant__ TcParams p) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    tc_grouped_kernel(const __grid_constant__ TcParams p) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], acce[2];
     __shared__ uint32_t tmem_base_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = p.tile_start[p.ngroups];
+    const uint32_t rank = cluster_rank();
+    const int cluster = (int)(blockIdx.x >> 1);
+    const int tbeg = p.sched_off[cluster], tend = p.sched_off[cluster + 1];
     const long long step = *p.step_ctr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&full[s], 1);   // leader: one expect_tx arrival; both CTAs' bytes
+            mbar_init(&empty[s], 1);  // multicast MMA commit
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 256);
+            mbar_init(&accf[b], 1);                   // multicast MMA commit
+            mbar_init(&acce[b], 2 * TC_EPI_WARPS);    // leader: one arrival per epilogue warp of the pair
         }
         mbar_fence_init();
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                      "r"(2 * TC_NMAX));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // barriers of both CTAs initialised before any remote arrival
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
     auto sA_hi = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES; };
     auto sA_lo = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES + TC_A_BYTES; };
     auto sB_hi = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES + 2 * TC_A_BYTES; };
-    auto sB_lo = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES + 2 * TC_A_BYTES + TC_B_BYTES; };
+    auto sB_lo = [&](int s) { return smem + (size_t)s * TC_STAGE_BYTES + 2 * TC_A_BYTES + TC_BH_BYTES; };
+    bool timed_out = false;
 
     if (warp == 0) {
         // ------------------------------------------------------------- TMA producer
         if (lane == 0) {
             uint32_t it = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int ti = tbeg; ti < tend && !timed_out; ++ti) {
+                const int t = p.sched[ti];
                 const int g = tile_group(p, t);
                 const TcGroup &G = p.grp[g];
-                const int mt = t - p.tile_start[g];
+                const int row0 = (t - p.tile_start[g]) * TC_PAIR_M + (int)rank * TC_M;
                 const int nk = (G.n + TC_BK - 1) / TC_BK;
-                const uint32_t bytes = 2 * TC_A_BYTES + 2u * (uint32_t)G.n_mma * TC_BK * 2u;
+                const int nh = G.n_mma >> 1;
+                const uint32_t bytes = 2 * (2 * TC_A_BYTES + 2u * (uint32_t)nh * TC_BK * 2u);
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = (int)(it % TC_STAGES);
                     const uint32_t ph = (it / TC_STAGES) & 1u;
                     if (!mbar_wait_bounded(&empty[s], ph ^ 1u)) {
-                        ok = false;
+                        timed_out = true;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[s], bytes);
-                    tma_load_2d(sA_hi(s), &p.tmA_hi[g], kb * TC_BK, mt * TC_M, &full[s]);
-                    tma_load_2d(sA_lo(s), &p.tmA_lo[g], kb * TC_BK, mt * TC_M, &full[s]);
-                    tma_load_2d(sB_hi(s), &p.tmB_hi[g], kb * TC_BK, 0, &full[s]);
-                    tma_load_2d(sB_lo(s), &p.tmB_lo[g], kb * TC_BK, 0, &full[s]);
+                    if (rank == 0) mbar_arrive_expect_tx(&full[s], bytes);
+                    const uint32_t fb = mapa_u32(&full[s], 0);
+                    tma_load_2d_pair(sA_hi(s), &p.tmA_hi[g], kb * TC_BK, row0, fb);
+                    tma_load_2d_pair(sA_lo(s), &p.tmA_lo[g], kb * TC_BK, row0, fb);
+                    tma_load_2d_pair(sB_hi(s), &p.tmB_hi[g], kb * TC_BK, (int)rank * nh, fb);
+                    tma_load_2d_pair(sB_lo(s), &p.tmB_lo[g], kb * TC_BK, (int)rank * nh, fb);
                 }
             }
-            if (!ok) set_dev_error(p.err, DEV_TIMEOUT);
+            if (timed_out) set_dev_error(p.err, DEV_TIMEOUT);
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        // ------------------------------------------------------------- MMA issuer (leader)
+        if (lane == 0 && rank == 0) {
             uint32_t it = 0, ci = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int ti = tbeg; ti < tend && !timed_out; ++ti) {
+                const int t = p.sched[ti];
                 const int g = tile_group(p, t);
                 const TcGroup &G = p.grp[g];
                 const int nk = (G.n + TC_BK - 1) / TC_BK;
                 const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(G.n_mma >> 3) << 17) |
-                                       ((uint32_t)(TC_M >> 4) << 24);
+                                       ((uint32_t)(TC_PAIR_M >> 4) << 24);
                 // K is accumulated in tensor memory one chunk at a time; the epilogue adds
                 // the chunks in FP32 registers (round to nearest)
-                for (int kc = 0; kc < nk && ok; kc += TC_CHUNK, ++ci) {
+                for (int kc = 0; kc < nk && !timed_out; kc += TC_CHUNK, ++ci) {
                     const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
-                    if (!mbar_wait_bounded(&acce[ab], aph ^ 1u)) {
-                        ok = false;
+                    if (!mbar_wait_cluster_bounded(&acce[ab], aph ^ 1u)) {
+                        timed_out = true;
                         break;
                     }
                     tc_fence_after();
@@ -221,8 +279,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
                     for (int kb = kc; kb < kend; ++kb, ++it) {
                         const int s = (int)(it % TC_STAGES);
                         const uint32_t ph = (it / TC_STAGES) & 1u;
-                        if (!mbar_wait_bounded(&full[s], ph)) {
-                            ok = false;
+                        if (!mbar_wait_cluster_bounded(&full[s], ph)) {
+                            timed_out = true;
                             break;
                         }
                         tc_fence_after();
@@ -231,17 +289,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
 #pragma unroll
                         for (int k = 0; k < TC_BK / 16; ++k) {
                             const uint64_t off = (uint64_t)((k * 32) >> 4);
-                            umma_bf16(d, ahi + off, bhi + off, idesc, ((kb - kc) | k) ? 1u : 0u);
-                            umma_bf16(d, ahi + off, blo + off, idesc, 1u);
-                            umma_bf16(d, alo + off, bhi + off, idesc, 1u);
+                            umma_bf16_pair(d, ahi + off, bhi + off, idesc, ((kb - kc) | k) ? 1u : 0u);
+                            umma_bf16_pair(d, ahi + off, blo + off, idesc, 1u);
+                            umma_bf16_pair(d, alo + off, bhi + off, idesc, 1u);
                         }
-                        umma_commit(&empty[s]);  // the slot is free once these MMAs have read it
+                        umma_commit_pair(&empty[s]);  // the slot is free in both CTAs once read
                     }
-                    if (!ok) break;
-                    umma_commit(&accf[ab]);      // chunk accumulator ready for the epilogue
+                    if (timed_out) break;
+                    umma_commit_pair(&accf[ab]);      // chunk accumulators ready in both CTAs
                 }
             }
-            if (!ok) set_dev_error(p.err, DEV_TIMEOUT);
+            if (timed_out) set_dev_error(p.err, DEV_TIMEOUT);
         }
     } else {
         // ------------------------------------------------------------- epilogue
@@ -249,11 +307,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
         // access); each owns 128 of the up-to-256 accumulator columns.
         const int q4 = warp & 3;
         const int col0 = ((warp - 2) >> 2) * 128;
-        const int row_in_tile = 32 * q4 + lane;
+        const int row_in_tile = (int)rank * TC_M + 32 * q4 + lane;
+        const uint32_t acce_leader[2] = {mapa_u32(&acce[0], 0), mapa_u32(&acce[1], 0)};
         uint32_t ci = 0;
         const float dtf = (float)p.dt;
-        bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int ti = tbeg; ti < tend && !timed_out; ++ti) {
+            const int t = p.sched[ti];
             const int g = tile_group(p, t);
             const TcGroup &G = p.grp[g];
             const int mt = t - p.tile_start[g];
@@ -265,7 +324,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
                 const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
                 if (!mbar_wait_bounded(&accf[ab], aph)) {
                     if (lane == 0) set_dev_error(p.err, DEV_TIMEOUT);
-                    ok = false;
+                    timed_out = true;
                     break;
                 }
                 tc_fence_after();
@@ -279,10 +338,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&acce[ab]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(acce_leader[ab]);
             }
-            if (!ok) break;
-            const int i = mt * TC_M + row_in_tile;
+            if (timed_out) break;
+            const int i = mt * TC_PAIR_M + row_in_tile;
             if (i >= G.n) continue;
             const float si = G.rs[i];
             const int64_t base = G.state_off + i;
@@ -342,11 +402,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_grouped_kernel(const __grid_
             }
         }
     }
+    // After a timeout, copies already issued may still land in shared memory and count on
+    // the leader's barriers: give them time before the pair leaves (bounded, ~1 ms).
+    if (__syncthreads_or(timed_out ? 1 : 0))
+        for (int w = 0; w < 1000; ++w) __nanosleep(1000);
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();  // neither CTA leaves while the pair's MMAs or arrivals may touch it
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_NMAX));
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_NMAX));
     }
     if (STAGE == 4 && threadIdx.x == 0) {
         __threadfence();
@@ -440,6 +504,8 @@ struct nf_group_state {
     uint16_t *F[nfi::TC_MAXG][2][2] = {};  // [group][buffer][hi/lo]
     int64_t state_total = 0;
     int traj_total = 0;
+    int nclusters = 0;                     // CTA pairs per launch
+    int *sched = nullptr;                  // device: [nclusters + 1] offsets, then the tile list
     nfi::TcParams params[2];               // [0]: reads F buffer 0, writes 1; [1]: reads 1, writes 0
 };
 
@@ -469,7 +535,7 @@ static nf_status build_group_params(nf_operator *op) {
             G.n = (int)mo->n;
             G.B = gs->B[m];
             G.n_mma = (G.B + 15) / 16 * 16;
-            G.mtiles = (int)ceil_div(mo->n, TC_M);
+            G.mtiles = (int)ceil_div(mo->n, TC_PAIR_M);
             G.ldF = mo->n_pad;
             G.state_off = state_off[m];
             G.traj_off = (int)traj_off[m];
@@ -479,8 +545,9 @@ static nf_status build_group_params(nf_operator *op) {
             G.Flo_out = gs->F[m][out][1];
             NF_TRY(make_map(&P.tmA_hi[k], mo->Whi, mo->n, mo->n, mo->n_pad, TC_M));
             NF_TRY(make_map(&P.tmA_lo[k], mo->Wlo, mo->n, mo->n, mo->n_pad, TC_M));
-            NF_TRY(make_map(&P.tmB_hi[k], gs->F[m][in][0], mo->n, G.B, mo->n_pad, G.n_mma));
-            NF_TRY(make_map(&P.tmB_lo[k], gs->F[m][in][1], mo->n, G.B, mo->n_pad, G.n_mma));
+            // each CTA of a pair stages half of the N trajectory rows
+            NF_TRY(make_map(&P.tmB_hi[k], gs->F[m][in][0], mo->n, G.B, mo->n_pad, G.n_mma / 2));
+            NF_TRY(make_map(&P.tmB_lo[k], gs->F[m][in][1], mo->n, G.B, mo->n_pad, G.n_mma / 2));
             P.tile_start[k] = tiles;
             tiles += G.mtiles;
         }
@@ -494,9 +561,62 @@ static nf_status build_group_params(nf_operator *op) {
     return NF_OK;
 }
 
+// Longest-processing-time assignment of the pair tiles to the clusters of one launch.  A
+// tile's cost is its number of 32-wide K blocks times the larger of the per-SM MMA time of a
+// block (3 products x 128 x N x 32 FMA at 4096 FMA per clock: 3 N clocks) and the time to
+// stream its 16 KB of W hi/lo per SM at an even share of HBM bandwidth (~760 clocks).
+static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
+    nf_group_state *gs = op->group;
+    const TcParams &P = gs->params[0];
+    const int ntiles = P.tile_start[P.ngroups];
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(num_sms() & ~1), 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = TC_SMEM;
+    int maxc = 0;
+    NF_CUDA_TRY(cudaOccupancyMaxActiveClusters(&maxc, tc_grouped_kernel<1>, &cfg));
+    if (maxc < 1) return fail(NF_ERR_UNSUPPORTED, "no CTA pair of the batched GEMM fits on this device");
+    const int nclust = std::min(ntiles, maxc);
+    std::vector<double> cost(ntiles);
+    for (int k = 0; k < P.ngroups; ++k) {
+        const TcGroup &G = P.grp[k];
+        const double c = (double)ceil_div(G.n, TC_BK) * std::max(3.0 * G.n_mma, 760.0);
+        for (int t = P.tile_start[k]; t < P.tile_start[k + 1]; ++t) cost[t] = c;
+    }
+    std::vector<int> order(ntiles);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(nclust, 0.0);
+    std::vector<std::vector<int>> lists(nclust);
+    for (int t : order) {
+        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[c].push_back(t);
+        load[c] += cost[t];
+    }
+    std::vector<int> host;
+    host.reserve(nclust + 1 + ntiles);
+    int off = 0;
+    for (int c = 0; c < nclust; ++c) {
+        host.push_back(off);
+        off += (int)lists[c].size();
+    }
+    host.push_back(off);
+    for (int c = 0; c < nclust; ++c) host.insert(host.end(), lists[c].begin(), lists[c].end());
+    NF_CUDA_TRY(cudaMalloc(&gs->sched, sizeof(int) * host.size()));
+    NF_CUDA_TRY(cudaMemcpyAsync(gs->sched, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, s));
+    NF_CUDA_TRY(cudaStreamSynchronize(s));
+    gs->nclusters = nclust;
+    for (int par = 0; par < 2; ++par) {
+        gs->params[par].sched_off = gs->sched;
+        gs->params[par].sched = gs->sched + nclust + 1;
+    }
+    return NF_OK;
+}
+
 void destroy_group(nf_operator *op) {
     if (!op->group) return;
     nf_group_state *gs = op->group;
+    cudaFree(gs->sched);
     for (int m = 0; m < gs->count; ++m)
         for (int b = 0; b < 2; ++b)
             for (int h = 0; h < 2; ++h) cudaFree(gs->F[m][b][h]);
@@ -551,8 +671,7 @@ nf_status tc_launch(nf_operator *op, int parity, int mode, float *I, float *u, c
     P.stage = stage;
     P.ckpt = ckpt;
     P.C = C;
-    const int ntiles = P.tile_start[P.ngroups];
-    const int grid = std::min(ntiles, num_sms());
+    const int grid = 2 * op->group->nclusters;
     switch (mode == 0 ? 0 : stage) {
         case 0: tc_grouped_kernel<0><<<grid, TC_THREADS, TC_SMEM, s>>>(P); break;
         case 1: tc_grouped_kernel<1><<<grid, TC_THREADS, TC_SMEM, s>>>(P); break;
@@ -635,6 +754,7 @@ extern "C" nf_status nf_operator_group(nf_operator *const *ops, const int *B_per
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(state)", __FILE__, __LINE__));
     op->state_cap = (size_t)total;
     nf_status st = build_group_params(op);
+    if (st == NF_OK) st = build_schedule(op, s);
     if (st != NF_OK) return cleanup(st);
     *grouped = op;
     return NF_OK;
