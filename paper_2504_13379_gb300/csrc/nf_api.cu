@@ -307,7 +307,8 @@ nf_status nf_operator_create(const float *x, const float *q, int64_t n, nf_kerne
                                                                          op->q);
     CREATE_TRY(cudaGetLastError());
     if (path == NF_MATRIX_FREE) {
-        nf_status st = mf_autotune(op, s);
+        nf_status st = mf_build_row_order(op, s);
+        if (st == NF_OK) st = mf_autotune(op, s);
         if (st != NF_OK) return cleanup(st);
     } else {
         const size_t entries = (size_t)op->n_pad * (size_t)op->n_pad;
@@ -334,6 +335,7 @@ nf_status nf_operator_destroy(nf_operator *op) {
         if (ev) cudaEventDestroy(ev);
     cudaFree(op->x4);
     cudaFree(op->xyz);
+    cudaFree(op->rowperm);
     cudaFree(op->q);
     cudaFree(op->W32);
     cudaFree(op->Whi);

@@ -15,6 +15,7 @@
 #include "nf_internal.cuh"
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -141,9 +142,10 @@ mf_pair_kernel(const float4 *__restrict__ x4, const float *__restrict__ g, int64
 // Single-trajectory variant on packed FP32 pairs (f32x2: one instruction, two lanes of
 // the FMA pipe).  Column tiles are staged as structure-of-arrays (x, y, z, g), so a
 // lane reads two adjacent columns with one 8-byte load; each row's coordinates are held
-// duplicated in a 64-bit register pair.  Per two pairs: 3 SUB2, MUL2 + 2 FMA2 (r^2),
-// 2 MUL2 (exponent scaling), 4 MUFU.EX2, 2 FMA2 -- 7 issue slots per pair instead of 12,
-// the same FMA-pipe lane count, the same rounding as the scalar kernel.
+// duplicated in a 64-bit register pair.  Difference form, per two pairs: 3 SUB2, MUL2 +
+// 2 FMA2 (r^2), MUL2 (second exponent), 4 MUFU.EX2, 2 FMA2 -- the rounding of the scalar
+// kernel.  Expanded form (below): 3 FMA2, MUL2, 4 MUFU.EX2, 2 FMA2, plus 6 per column pair
+// shared by the warp's rows, which leaves the SFU (2 exponentials per pair) as the bound.
 typedef unsigned long long u64;
 __device__ __forceinline__ u64 f2_sub(u64 a, u64 b) {
     u64 d;
@@ -180,20 +182,46 @@ struct MfPackedSmem {
     uint64_t bar[2];
 };
 
+// Rows are taken in a spatially coherent order (rowperm: Morton order of the nodes), so the
+// R rows of a warp usually lie close together.  Such a warp expands the squared distance
+// about the centre c of its rows' bounding box:
+//   r^2 = |x_i - c|^2 + |x_j - c|^2 - 2 (x_i - c).(x_j - c) = n_i + s_ij,
+//   s_ij = n_j - 2 (x_i - c).(x_j - c),
+// and accumulates 2^(-s_ij) and 2^(-k2 s_ij); the row factors 2^(-n_i), 2^(-k2 n_i) are
+// applied once at the end.  Per column pair the centred coordinates and n_j cost 6 lane
+// operations shared by the warp's R rows; per pair the exponent argument is then a chain
+// of 3 FMAs instead of 3 SUB + MUL + 2 FMA.  FP32 rounding of s_ij is relative to
+// n_i + n_j + 2 |x_i - c||x_j - c|, so the form is used only when every row of the warp has
+// n_i <= kMfLocalSpread (scaled units, i.e. |x_i - c| <= s1 / sqrt(log2 e)); for pairs
+// that carry weight this keeps the error at a few ulps of r^2, the same order as the
+// rounding of the stored coordinates.  Warps whose rows are spread out use the difference
+// form.  The choice is warp-uniform and fixed per launch shape, so results stay
+// deterministic.
+//
+// Integer width ratio.  When m = s2^2 / s1^2 is a small integer (M = 2, 3, 4; the paper's
+// lateral-inhibition kernels have sigma_i = 2 sigma_e, i.e. m = 4), the expanded form works
+// in units of s2 -- centred column coordinates times s1/s2 -- and takes e2 = 2^(-s'_ij)
+// from the SFU and e1 = e2^M by squaring on the FMA pipe: one exponential per pair
+// instead of two.  The relative error of e1 grows to about M times that of ex2.approx
+// (a few 1e-7).  M = 0 is the general form.
+constexpr float kMfLocalSpread = 1.0f;
+
 // xyz: pre-scaled coordinates as structure of arrays [x(n_pad) | y(n_pad) | z(n_pad)],
-// multiplied by sqrt(log2 e) / s1; g_all: B x n_pad firing rates (times q).
-template <int R, int TJ>
-__global__ void __launch_bounds__(MF_THREADS)
-mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, int64_t n_pad, int B,
-                      int b_base, int64_t jchunk, float k2, float A1, float A2, float *__restrict__ partial,
-                      int *__restrict__ err) {
+// multiplied by sqrt(log2 e) / s1; g_all: B x n_pad firing rates (times q); rowperm: n_pad
+// node indices, a permutation (padding rows map to themselves).
+template <int R, int TJ, int M>
+__global__ void __launch_bounds__(MF_THREADS, R >= 8 ? 2 : 4)
+mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
+                      int64_t n_pad, int B, int b_base, int64_t jchunk, float k2, float A1, float A2,
+                      float *__restrict__ partial, int *__restrict__ err) {
+    static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
     __shared__ __align__(128) MfPackedSmem<TJ> sm;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int split = blockIdx.y;
     const int64_t j0 = (int64_t)split * jchunk;
     const int64_t j1 = min(n_pad, j0 + jchunk);
     const int ntiles = (int)((j1 - j0) / TJ);
-    const int64_t row0 = ((int64_t)blockIdx.x * MF_WARPS + warp) * R;
+    const int64_t slot0 = ((int64_t)blockIdx.x * MF_WARPS + warp) * R;
     constexpr uint32_t kTileBytes = 4 * TJ * 4;
     const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
     const int b = b_base + blockIdx.z;
@@ -217,10 +245,37 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
         if (ntiles > 0) issue(0);
         if (ntiles > 1) issue(1);
     }
+    // the warp's rows (all lanes hold the same values) and the centre of their bounding box
+    float xr[R], yr[R], zr[R];
+    float lox = 3.4e38f, loy = 3.4e38f, loz = 3.4e38f, hix = -3.4e38f, hiy = -3.4e38f, hiz = -3.4e38f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = __ldg(rowperm + slot0 + r);
+        xr[r] = X[row];
+        yr[r] = Y[row];
+        zr[r] = Z[row];
+        lox = fminf(lox, xr[r]), hix = fmaxf(hix, xr[r]);
+        loy = fminf(loy, yr[r]), hiy = fmaxf(hiy, yr[r]);
+        loz = fminf(loz, zr[r]), hiz = fmaxf(hiz, zr[r]);
+    }
+    const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy), cz = 0.5f * (loz + hiz);
+    float spread = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float dx = xr[r] - cx, dy = yr[r] - cy, dz = zr[r] - cz;
+        spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
+    }
+    const bool local = spread <= kMfLocalSpread;  // warp-uniform
+    // local: xi, yi, zi hold -2 (x_i - c) (times s1/s2 when M > 0); otherwise x_i itself
+    // (both halves of the pair)
+    const float sk = M > 0 ? sqrtf(k2) : 1.f;
+    const float lsc = -2.f * sk;
     u64 xi[R], yi[R], zi[R], a1[R], a2[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const float x = X[row0 + r], y = Y[row0 + r], z = Z[row0 + r];
+        const float x = local ? lsc * (xr[r] - cx) : xr[r];
+        const float y = local ? lsc * (yr[r] - cy) : yr[r];
+        const float z = local ? lsc * (zr[r] - cz) : zr[r];
         xi[r] = f2_pack(x, x);
         yi[r] = f2_pack(y, y);
         zi[r] = f2_pack(z, z);
@@ -230,6 +285,7 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
     // coordinates arrive pre-scaled by sqrt(log2(e)) / s1, so r2s = r^2 log2(e) / s1^2:
     // e1 = 2^(-r2s), e2 = 2^(-k2 r2s) with k2 = s1^2 / s2^2
     const u64 nk2 = f2_pack(-k2, -k2);
+    const u64 cxp = f2_pack(cx, cx), cyp = f2_pack(cy, cy), czp = f2_pack(cz, cz), skp = f2_pack(sk, sk);
     bool timed_out = false;
     for (int t = 0; t < ntiles; ++t) {
         const int buf = t & 1;
@@ -243,19 +299,57 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
         const u64 *ys = reinterpret_cast<const u64 *>(sm.ys[buf]);
         const u64 *zs = reinterpret_cast<const u64 *>(sm.zs[buf]);
         const u64 *gs = reinterpret_cast<const u64 *>(sm.gs[buf]);
+        if (M > 0 && local) {
 #pragma unroll 2
-        for (int jp = lane; jp < TJ / 2; jp += 32) {
-            const u64 xj = xs[jp], yj = ys[jp], zj = zs[jp], gj = gs[jp];
+            for (int jp = lane; jp < TJ / 2; jp += 32) {
+                const u64 xt = f2_mul(f2_sub(xs[jp], cxp), skp), yt = f2_mul(f2_sub(ys[jp], cyp), skp),
+                          zt = f2_mul(f2_sub(zs[jp], czp), skp);
+                const u64 nj = f2_fma(zt, zt, f2_fma(yt, yt, f2_mul(xt, xt)));
+                const u64 gj = gs[jp];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj), dz = f2_sub(zi[r], zj);
-                const u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
-                float s0, s1v;
-                f2_unpack(r2s, s0, s1v);
-                const u64 e1 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
-                const u64 e2 = f2_ex2(f2_mul(r2s, nk2));
-                a1[r] = f2_fma(e1, gj, a1[r]);
-                a2[r] = f2_fma(e2, gj, a2[r]);
+                for (int r = 0; r < R; ++r) {
+                    const u64 sij = f2_fma(xi[r], xt, f2_fma(yi[r], yt, f2_fma(zi[r], zt, nj)));
+                    float s0, s1v;
+                    f2_unpack(sij, s0, s1v);
+                    const u64 e2 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+                    const u64 sq = f2_mul(e2, e2);
+                    const u64 e1 = M == 2 ? sq : (M == 3 ? f2_mul(sq, e2) : f2_mul(sq, sq));
+                    a1[r] = f2_fma(e1, gj, a1[r]);
+                    a2[r] = f2_fma(e2, gj, a2[r]);
+                }
+            }
+        } else if (local) {
+#pragma unroll 2
+            for (int jp = lane; jp < TJ / 2; jp += 32) {
+                const u64 xt = f2_sub(xs[jp], cxp), yt = f2_sub(ys[jp], cyp), zt = f2_sub(zs[jp], czp);
+                const u64 nj = f2_fma(zt, zt, f2_fma(yt, yt, f2_mul(xt, xt)));
+                const u64 gj = gs[jp];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const u64 sij = f2_fma(xi[r], xt, f2_fma(yi[r], yt, f2_fma(zi[r], zt, nj)));
+                    float s0, s1v;
+                    f2_unpack(sij, s0, s1v);
+                    const u64 e1 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+                    const u64 e2 = f2_ex2(f2_mul(sij, nk2));
+                    a1[r] = f2_fma(e1, gj, a1[r]);
+                    a2[r] = f2_fma(e2, gj, a2[r]);
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (int jp = lane; jp < TJ / 2; jp += 32) {
+                const u64 xj = xs[jp], yj = ys[jp], zj = zs[jp], gj = gs[jp];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj), dz = f2_sub(zi[r], zj);
+                    const u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                    float s0, s1v;
+                    f2_unpack(r2s, s0, s1v);
+                    const u64 e1 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+                    const u64 e2 = f2_ex2(f2_mul(r2s, nk2));
+                    a1[r] = f2_fma(e1, gj, a1[r]);
+                    a2[r] = f2_fma(e2, gj, a2[r]);
+                }
             }
         }
     }
@@ -271,9 +365,18 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
         float p0, p1, q0, q1;
         f2_unpack(a1[r], p0, p1);
         f2_unpack(a2[r], q0, q1);
-        float v = A1 * (p0 + p1) - A2 * (q0 + q1);
-        v = warp_sum(v);
-        if (lane == 0) partial[((int64_t)split * B + b) * n_pad + row0 + r] = v;
+        float s1f = A1 * (p0 + p1), s2f = A2 * (q0 + q1);
+        if (local) {  // n_i from the same rounded centred coordinates the loop used
+            float mx, my, mz, unused;
+            f2_unpack(xi[r], mx, unused);
+            f2_unpack(yi[r], my, unused);
+            f2_unpack(zi[r], mz, unused);
+            const float ni = 0.25f * (mx * mx + my * my + mz * mz);  // in units of s2 when M > 0
+            s1f *= exp2f(M > 0 ? -(float)M * ni : -ni);
+            s2f *= exp2f(M > 0 ? -ni : -k2 * ni);
+        }
+        float v = warp_sum(s1f - s2f);
+        if (lane == 0) partial[((int64_t)split * B + b) * n_pad + __ldg(rowperm + slot0 + r)] = v;
     }
 }
 
@@ -356,11 +459,21 @@ struct MfVariant {
 constexpr MfVariant kMfVariants[] = {{2, 512}, {4, 512}, {4, 1024}, {8, 1024}};
 constexpr int kNumMfVariants = 4;
 
+// Integer width ratio m = s2^2 / s1^2 in {2, 3, 4} (to FP32 rounding of the k2 the kernel
+// receives), else 0: selects the one-exponential form of the packed kernel.
+static int mf_width_ratio(const nf_kernel &k) {
+    const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
+    for (int m = 2; m <= 4; ++m)
+        if (std::fabs((double)m * (double)k2 - 1.0) <= 4.0 * (double)FLT_EPSILON) return m;
+    return 0;
+}
+
 template <int R, int TJ>
 static int packed_resident() {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mf_pair_packed_kernel<R, TJ>, MF_THREADS, 0);
-    return std::max(nb, 1);
+    int nb0 = 0, nb4 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, mf_pair_packed_kernel<R, TJ, 0>, MF_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb4, mf_pair_packed_kernel<R, TJ, 4>, MF_THREADS, 0);
+    return std::max(std::min(nb0, nb4), 1);
 }
 
 static int variant_resident(int v) {
@@ -377,8 +490,15 @@ static void launch_packed(nf_operator *op, int B, int b_base, int groups, const 
     const nf_kernel &k = op->kp;
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
     dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, (unsigned)groups);
-    mf_pair_packed_kernel<R, TJ><<<grid, MF_THREADS, 0, s>>>(op->xyz, op->g, op->n_pad, B, b_base, pl.jchunk, k2, k.A1,
-                                                             k.A2, op->partial, op->err);
+#define NF_PACKED_ARGS \
+    op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, pl.jchunk, k2, k.A1, k.A2, op->partial, op->err
+    switch (mf_width_ratio(k)) {
+        case 2: mf_pair_packed_kernel<R, TJ, 2><<<grid, MF_THREADS, 0, s>>>(NF_PACKED_ARGS); break;
+        case 3: mf_pair_packed_kernel<R, TJ, 3><<<grid, MF_THREADS, 0, s>>>(NF_PACKED_ARGS); break;
+        case 4: mf_pair_packed_kernel<R, TJ, 4><<<grid, MF_THREADS, 0, s>>>(NF_PACKED_ARGS); break;
+        default: mf_pair_packed_kernel<R, TJ, 0><<<grid, MF_THREADS, 0, s>>>(NF_PACKED_ARGS); break;
+    }
+#undef NF_PACKED_ARGS
 }
 
 static nf_status launch_mf_packed(nf_operator *op, int B, int b_base, int groups, const SplitPlan &pl,
@@ -523,6 +643,111 @@ nf_status launch_mf_pair_single(const float4 *x4, const float *g, int64_t n_pad,
     NF_CUDA_TRY(cudaGetLastError());
     *splits_out = pl.splits;
     return NF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Row order of the packed pair kernel: nodes sorted by the Morton (Z-order) code of their
+// cell in a 1024^3 grid over the bounding box, ties by index, so that consecutive rows --
+// the R rows of a warp -- are near each other.  Keys (code << 32 | index) are unique; a
+// bitonic network over the next power of two sorts them.  Padding rows keep their place.
+
+// Bounding box of the first n coordinates (one block): box = {lo x, lo y, lo z, hi x, hi y, hi z}.
+__global__ void row_bbox_kernel(const float *__restrict__ xyz, int64_t n, int64_t n_pad, float *__restrict__ box) {
+    __shared__ float red[6][32];
+    float v[6] = {3.4e38f, 3.4e38f, 3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            const float c = xyz[d * n_pad + j];
+            v[d] = fminf(v[d], c);
+            v[3 + d] = fmaxf(v[3 + d], c);
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1)
+        for (int d = 0; d < 3; ++d) {
+            v[d] = fminf(v[d], __shfl_xor_sync(0xffffffffu, v[d], o));
+            v[3 + d] = fmaxf(v[3 + d], __shfl_xor_sync(0xffffffffu, v[3 + d], o));
+        }
+    if (lane == 0)
+        for (int d = 0; d < 6; ++d) red[d][warp] = v[d];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int d = threadIdx.x;
+        float a = red[d][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) a = d < 3 ? fminf(a, red[d][w]) : fmaxf(a, red[d][w]);
+        box[d] = a;
+    }
+}
+
+// 10 bits of v spread to every third bit position.
+__device__ __forceinline__ uint32_t spread_bits3(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void row_key_kernel(const float *__restrict__ xyz, int64_t n, int64_t n_pad, int64_t m,
+                               const float *__restrict__ box, unsigned long long *__restrict__ keys) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    if (j >= n) {
+        keys[j] = ~0ull;
+        return;
+    }
+    uint32_t code = 0;
+    for (int d = 0; d < 3; ++d) {
+        const float ext = box[3 + d] - box[d];
+        const float t = ext > 0.f ? (xyz[d * n_pad + j] - box[d]) / ext : 0.f;
+        const uint32_t c = (uint32_t)fminf(fmaxf(t * 1024.f, 0.f), 1023.f);
+        code |= spread_bits3(c) << d;
+    }
+    keys[j] = ((unsigned long long)code << 32) | (unsigned long long)j;
+}
+
+// One compare-exchange step of the bitonic network (block size kk, partner distance jj).
+__global__ void row_bitonic_kernel(unsigned long long *__restrict__ keys, int64_t m, int64_t jj, int64_t kk) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t l = i ^ jj;
+    if (l <= i) return;
+    const unsigned long long a = keys[i], b = keys[l];
+    const bool ascending = (i & kk) == 0;
+    if ((a > b) == ascending) {
+        keys[i] = b;
+        keys[l] = a;
+    }
+}
+
+__global__ void row_perm_kernel(const unsigned long long *__restrict__ keys, int64_t n, int64_t n_pad,
+                                int *__restrict__ rowperm) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pad) return;
+    rowperm[k] = k < n ? (int)(keys[k] & 0xffffffffull) : (int)k;
+}
+
+nf_status mf_build_row_order(nf_operator *op, cudaStream_t s) {
+    const int64_t n = op->n, n_pad = op->n_pad;
+    int64_t m = 1;
+    while (m < n_pad) m <<= 1;
+    NF_CUDA_TRY(cudaMalloc(&op->rowperm, sizeof(int) * n_pad));
+    unsigned long long *keys = nullptr;
+    float *box = nullptr;
+    NF_CUDA_TRY(cudaMalloc(&keys, sizeof(unsigned long long) * m + 64));
+    box = reinterpret_cast<float *>(keys + m);
+    nf_status st = NF_OK;
+    row_bbox_kernel<<<1, 1024, 0, s>>>(op->xyz, n, n_pad, box);
+    row_key_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(op->xyz, n, n_pad, m, box, keys);
+    for (int64_t kk = 2; kk <= m; kk <<= 1)
+        for (int64_t jj = kk >> 1; jj > 0; jj >>= 1)
+            row_bitonic_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(keys, m, jj, kk);
+    row_perm_kernel<<<(unsigned)ceil_div(n_pad, 256), 256, 0, s>>>(keys, n, n_pad, op->rowperm);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "row order", __FILE__, __LINE__);
+    cudaFree(keys);
+    return st;
 }
 
 // ----------------------------------------------------------------------------

@@ -139,6 +139,28 @@ def test_nonlocal_apply_matches_oracle(nf, path, n, B):
     assert rel_l2(got.cpu().numpy(), want) < REL_L2
 
 
+@pytest.mark.parametrize("s1", [0.02, 0.3, 3.0])
+def test_nonlocal_apply_row_order_forms(nf, s1):
+    """The matrix-free kernel takes rows in Morton order; a warp whose rows lie within
+    s1 / sqrt(log2 e) of their centre expands the squared distance about that centre,
+    any other warp uses coordinate differences.  Nodes in six blobs, listed in random
+    order, with a narrow, a medium and a wide kernel mix both forms; every row must
+    match the oracle."""
+    rng = np.random.default_rng(int(s1 * 100))
+    n = 4099
+    centres = rng.uniform(-5, 5, size=(6, 3))
+    X = (centres[rng.integers(0, 6, n)] + rng.normal(0, 0.5, size=(n, 3))).astype(np.float32)
+    q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
+    u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
+    kern = (1.0, s1, 0.5, 2 * s1)
+    op = _op(nf, X, q, kern, 0)
+    got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), 20.0, 0.2).cpu().numpy()
+    op.check()
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
+    assert rel_l2(got, want) < REL_L2
+    assert np.abs(got - want).max() / np.abs(want).max() < REL_L2
+
+
 def test_nonlocal_apply_paper_kernel_torus_sampled_full_size(nf):
     """Full precision-workload size (n = 100,000 torus nodes), the launch
     configuration the benchmark times; the oracle evaluates 384 sampled rows."""
