@@ -7,6 +7,8 @@
 //   NF_DENSE_BF16X2: s_i = 2^ceil(log2 max_j |WQ_ij|) (a power of two, so dividing by
 //                    it is exact); hi = bf16_rn(WQ/s_i), lo = bf16_rn(WQ/s_i - hi).
 //                    hi + lo carries ~16 significant bits; I_i = s_i sum_j (hi+lo) F_j.
+//                    The two planes use the blocked layout (128 x 32 blocks of 8 KB), the
+//                    tile the batched tensor-core GEMM reads with one sequential copy.
 // Apply (every stage): HBM-bound stream of 4 bytes per entry for either plane type.
 // Work items (32-row block, column split) write partial sums like the matrix-free
 // kernel, so the same stage kernel finishes the RK4 step.
@@ -79,8 +81,9 @@ __global__ void dense_build_bf16x2_kernel(const float4 *__restrict__ x4, const f
         const float v = mexhat(r2, A1, is1, A2, is2) * q[j] * inv;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        Whi[i * n_pad + j] = __bfloat16_as_ushort(hi);
-        Wlo[i * n_pad + j] = __bfloat16_as_ushort(lo);
+        const int64_t o = blocked_offset(i, j, n_pad);
+        Whi[o] = __bfloat16_as_ushort(hi);
+        Wlo[o] = __bfloat16_as_ushort(lo);
     }
 }
 
@@ -178,7 +181,7 @@ gemv_bf16x2_kernel(const uint16_t *__restrict__ Whi, const uint16_t *__restrict_
             for (int r = 0; r < DG_R; ++r)
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int64_t off = (row0 + r) * n_pad + t + 256 * (uh + u) + 8 * lane;
+                    const int64_t off = blocked_offset(row0 + r, t + 256 * (uh + u) + 8 * lane, n_pad);
                     h[r][u] = ld_stream_u4(Whi + off);
                     l[r][u] = ld_stream_u4(Wlo + off);
                 }

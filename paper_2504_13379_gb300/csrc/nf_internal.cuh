@@ -85,6 +85,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Non-suspending poll (test_wait) in a bounded spin, for the single threads that feed the
+// tensor core: try_wait may park the thread for a system-dependent interval, which adds
+// to every producer / consumer hand-off of a copy pipeline.  ~1 s at ~20 ns per poll.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_spin_bounded(uint64_t *bar, uint32_t parity) {
+    for (long long it = 0; it < (kSpinLimit << 4); ++it)
+        if (mbar_test_wait(bar, parity)) return true;
+    return false;
+}
+
 // 1-D bulk copy global -> shared (TMA unit), completion signalled on `bar`.
 // dst, src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -139,8 +160,8 @@ struct nf_operator {
     float *q = nullptr;      // n_pad, zero padded
     // dense planes (row-major, leading dimension ld = n_pad)
     float *W32 = nullptr;        // W diag(q), FP32
-    uint16_t *Whi = nullptr;     // bf16 bits of (W diag(q))_ij / s_i, high part
-    uint16_t *Wlo = nullptr;     // bf16 bits of the residual
+    uint16_t *Whi = nullptr;     // bf16 bits of (W diag(q))_ij / s_i, high part (blocked layout)
+    uint16_t *Wlo = nullptr;     // bf16 bits of the residual (blocked layout)
     float *rs = nullptr;         // s_i, powers of two
     // workspace owned by the handle
     float *partial = nullptr;    // [split][B][n_pad]
@@ -162,6 +183,15 @@ struct nf_operator {
 };
 
 namespace nfi {
+
+// Blocked layout of the bf16 planes: 128-row x 32-column blocks of 8 KB, each stored row by
+// row (64 bytes per row), blocks ordered by row block, then column block.  A tensor-core
+// operand tile (128 rows x 32 K) is one contiguous 8 KB read; a row's 32-column pieces lie
+// 8 KB apart.  n_pad is a multiple of 1024, so the blocks tile the padded matrix exactly.
+constexpr int kBlkRows = 128, kBlkCols = 32;
+__host__ __device__ __forceinline__ int64_t blocked_offset(int64_t i, int64_t j, int64_t n_pad) {
+    return (((i >> 7) * (n_pad >> 5) + (j >> 5)) << 12) + ((i & 127) << 5) + (j & 31);
+}
 
 // ---------------------------------------------------------------- launch plans
 struct SplitPlan {

@@ -52,7 +52,7 @@ constexpr int TC_MAXG = 4;
 constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 TMEM + MMA, warps 2..9 epilogue
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_CHUNK = 8;        // K blocks (256 elements) accumulated in tensor memory per chunk
-constexpr int TC_EPI_BATCH = 4;    // trajectory columns per batch of epilogue loads
+constexpr int TC_EPI_BATCH = 2;    // trajectory columns per batch of epilogue loads
 constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;             // 8 KB per plane
 constexpr uint32_t TC_BH_BYTES = (TC_NMAX / 2) * TC_BK * 2;   // 8 KB per plane: half of N = 256
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_BH_BYTES;
@@ -60,6 +60,7 @@ constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
 
 struct TcGroup {
     int n, B, n_mma, mtiles;  // mtiles: pair tiles of 256 rows
+    int nkb_pad;              // 32-column blocks per row block of the blocked W planes
     int64_t ldF;          // leading dimension (elements) of the F planes, [b][ldF]
     int64_t state_off;    // offset of the group's B x n block in the concatenated state
     int traj_off;         // offset of the group's trajectories in beta / theta
@@ -76,6 +77,7 @@ struct TcParams {
     const int *sched_off;  // [clusters + 1]
     int mode;             // 0: write I, 1: RK4 stage
     float *I;             // mode 0 output (concatenated B_g x n_g blocks)
+    float *Iscr;          // RK4 stages: nonlocal sums awaiting the deferred stage update
     float *u, *U, *ks;
     const float *beta, *theta;
     const double *t0;
@@ -143,23 +145,16 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+// Arrive on a barrier in another CTA of the cluster (shared-cluster address).  Default
+// semantics (release at CTA scope): what must be ordered before it are this warp's tensor
+// memory reads, which tcgen05.fence::before_thread_sync does; a cluster-scope release would
+// also wait for the epilogue's outstanding global stores.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t *bar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
@@ -240,14 +235,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = (int)(it % TC_STAGES);
                     const uint32_t ph = (it / TC_STAGES) & 1u;
-                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u)) {
+                    if (!mbar_spin_bounded(&empty[s], ph ^ 1u)) {
                         timed_out = true;
                         break;
                     }
                     if (rank == 0) mbar_arrive_expect_tx(&full[s], bytes);
                     const uint32_t fb = mapa_u32(&full[s], 0);
-                    tma_load_2d_pair(sA_hi(s), &p.tmA_hi[g], kb * TC_BK, row0, fb);
-                    tma_load_2d_pair(sA_lo(s), &p.tmA_lo[g], kb * TC_BK, row0, fb);
+                    const int wy = ((row0 >> 7) * G.nkb_pad + kb) * TC_M;  // block (row0 / 128, kb)
+                    tma_load_2d_pair(sA_hi(s), &p.tmA_hi[g], 0, wy, fb);
+                    tma_load_2d_pair(sA_lo(s), &p.tmA_lo[g], 0, wy, fb);
                     tma_load_2d_pair(sB_hi(s), &p.tmB_hi[g], kb * TC_BK, (int)rank * nh, fb);
                     tma_load_2d_pair(sB_lo(s), &p.tmB_lo[g], kb * TC_BK, (int)rank * nh, fb);
                 }
@@ -269,7 +265,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 // the chunks in FP32 registers (round to nearest)
                 for (int kc = 0; kc < nk && !timed_out; kc += TC_CHUNK, ++ci) {
                     const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
-                    if (!mbar_wait_cluster_bounded(&acce[ab], aph ^ 1u)) {
+                    if (!mbar_spin_bounded(&acce[ab], aph ^ 1u)) {
                         timed_out = true;
                         break;
                     }
@@ -279,7 +275,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                     for (int kb = kc; kb < kend; ++kb, ++it) {
                         const int s = (int)(it % TC_STAGES);
                         const uint32_t ph = (it / TC_STAGES) & 1u;
-                        if (!mbar_wait_cluster_bounded(&full[s], ph)) {
+                        if (!mbar_spin_bounded(&full[s], ph)) {
                             timed_out = true;
                             break;
                         }
@@ -304,77 +300,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     } else {
         // ------------------------------------------------------------- epilogue
         // Two warps per TMEM lane quarter (warp & 3 selects the quarter a warp may
-        // access); each owns 128 of the up-to-256 accumulator columns.
+        // access); each owns half of the tile's N accumulator columns (at most 128).
         const int q4 = warp & 3;
-        const int col0 = ((warp - 2) >> 2) * 128;
+        const int half = (warp - 2) >> 2;
         const int row_in_tile = (int)rank * TC_M + 32 * q4 + lane;
         const uint32_t acce_leader[2] = {mapa_u32(&acce[0], 0), mapa_u32(&acce[1], 0)};
         uint32_t ci = 0;
         const float dtf = (float)p.dt;
-        for (int ti = tbeg; ti < tend && !timed_out; ++ti) {
-            const int t = p.sched[ti];
-            const int g = tile_group(p, t);
-            const TcGroup &G = p.grp[g];
-            const int mt = t - p.tile_start[g];
-            const int nk = (G.n + TC_BK - 1) / TC_BK;
-            float acc[128];
-#pragma unroll
-            for (int c = 0; c < 128; ++c) acc[c] = 0.f;
-            for (int kc = 0; kc < nk; kc += TC_CHUNK, ++ci) {
-                const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
-                if (!mbar_wait_bounded(&accf[ab], aph)) {
-                    if (lane == 0) set_dev_error(p.err, DEV_TIMEOUT);
-                    timed_out = true;
-                    break;
-                }
-                tc_fence_after();
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (col0 + 32 * c < G.n_mma) {  // warp-uniform
-                        uint32_t r[32];
-                        tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + ab * TC_NMAX + (uint32_t)(col0 + 32 * c), r);
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) acc[32 * c + j] += __uint_as_float(r[j]);
-                    }
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(acce_leader[ab]);
-            }
-            if (timed_out) break;
-            const int i = mt * TC_PAIR_M + row_in_tile;
-            if (i >= G.n) continue;
-            const float si = G.rs[i];
-            const int64_t base = G.state_off + i;
-            // TC_EPI_BATCH trajectory columns at a time: every load of the batch is issued before
-            // any result is used, so global-memory latency overlaps
-#pragma unroll
-            for (int c0 = 0; c0 < 128; c0 += TC_EPI_BATCH) {
-                if (col0 + c0 >= G.B) break;
-                if constexpr (STAGE == 0) {
+        // Deferred RK4 update.  After its last chunk a tile's scaled sums go to the scratch
+        // state Iscr and the warps move on to the next tile; the previous tile's stage update
+        // runs in slices in the gaps between the next tile's chunk drains, so the tensor core
+        // does not wait for its global-memory latency.  Pending job: group pg (< 0: none),
+        // pair tile pmt, next column pnext (warp-uniform).
+        int pg = -1, pmt = 0, pnext = 0;
+        auto rk4_slice = [&](int upto) {
+            if (pg < 0) return;
+            const TcGroup &PG = p.grp[pg];
+            const int pncol = PG.n_mma >> 1, pcol0 = half * pncol;
+            const int end = min(upto, pncol);
+            const int i = pmt * TC_PAIR_M + row_in_tile;
+            if (i < PG.n) {
+                const int64_t base = PG.state_off + i;
+                for (int c0 = pnext; c0 < end && pcol0 + c0 < PG.B; c0 += TC_EPI_BATCH) {
+                    // every load of the batch is issued before any result is used
+                    float Dv[TC_EPI_BATCH], Uv[TC_EPI_BATCH], uv[TC_EPI_BATCH], kv[TC_EPI_BATCH], bb[TC_EPI_BATCH],
+                        th[TC_EPI_BATCH];
 #pragma unroll
                     for (int j = 0; j < TC_EPI_BATCH; ++j) {
-                        const int b = col0 + c0 + j;
-                        if (b < G.B) p.I[base + (int64_t)b * G.n] = si * acc[c0 + j];
-                    }
-                } else {
-                    float Uv[TC_EPI_BATCH], uv[TC_EPI_BATCH], kv[TC_EPI_BATCH], bb[TC_EPI_BATCH], th[TC_EPI_BATCH];
-#pragma unroll
-                    for (int j = 0; j < TC_EPI_BATCH; ++j) {
-                        const int b = min(col0 + c0 + j, G.B - 1);
-                        const int64_t idx = base + (int64_t)b * G.n;
+                        const int b = min(pcol0 + c0 + j, PG.B - 1);
+                        const int64_t idx = base + (int64_t)b * PG.n;
+                        Dv[j] = p.Iscr[idx];
                         Uv[j] = p.U[idx];
                         uv[j] = p.u[idx];
                         kv[j] = (STAGE > 1) ? p.ks[idx] : 0.f;
-                        bb[j] = __ldg(p.beta + G.traj_off + b);
-                        th[j] = __ldg(p.theta + G.traj_off + b);
+                        bb[j] = __ldg(p.beta + PG.traj_off + b);
+                        th[j] = __ldg(p.theta + PG.traj_off + b);
                     }
 #pragma unroll
                     for (int j = 0; j < TC_EPI_BATCH; ++j) {
-                        const int b = col0 + c0 + j;
-                        if (b >= G.B) break;
-                        const int64_t idx = base + (int64_t)b * G.n;
-                        const float k = -Uv[j] + si * acc[c0 + j];
+                        const int b = pcol0 + c0 + j;
+                        if (b >= PG.B) break;
+                        const int64_t idx = base + (int64_t)b * PG.n;
+                        const float k = -Uv[j] + Dv[j];
                         float Un;
                         if constexpr (STAGE == 1) {
                             p.ks[idx] = k;
@@ -395,12 +362,72 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                         const float f = tc_firing(Un, bb[j], th[j]);
                         const __nv_bfloat16 hi = __float2bfloat16_rn(f);
                         const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-                        G.Fhi_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(hi);
-                        G.Flo_out[(int64_t)b * G.ldF + i] = __bfloat16_as_ushort(lo);
+                        PG.Fhi_out[(int64_t)b * PG.ldF + i] = __bfloat16_as_ushort(hi);
+                        PG.Flo_out[(int64_t)b * PG.ldF + i] = __bfloat16_as_ushort(lo);
                     }
                 }
             }
+            pnext = end;
+            if (pnext >= pncol) pg = -1;
+        };
+        for (int ti = tbeg; ti < tend && !timed_out; ++ti) {
+            const int t = p.sched[ti];
+            const int g = tile_group(p, t);
+            const TcGroup &G = p.grp[g];
+            const int mt = t - p.tile_start[g];
+            const int nk = (G.n + TC_BK - 1) / TC_BK;
+            const int ncol = G.n_mma >> 1;
+            const int col0 = half * ncol;
+            // columns of the pending job per chunk of this tile (whole batches)
+            const int nchunks = (nk + TC_CHUNK - 1) / TC_CHUNK;
+            const int pend = pg >= 0 ? (p.grp[pg].n_mma >> 1) - pnext : 0;
+            const int per = ((pend + nchunks - 1) / nchunks + TC_EPI_BATCH - 1) / TC_EPI_BATCH * TC_EPI_BATCH;
+            float acc[128];
+#pragma unroll
+            for (int c = 0; c < 128; ++c) acc[c] = 0.f;
+            for (int kc = 0; kc < nk; kc += TC_CHUNK, ++ci) {
+                const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
+                if (STAGE > 0) rk4_slice(pnext + per);  // while this chunk is on the tensor core
+                if (!mbar_wait_bounded(&accf[ab], aph)) {
+                    if (lane == 0) set_dev_error(p.err, DEV_TIMEOUT);
+                    timed_out = true;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (32 * c < ncol) {  // warp-uniform
+                        uint32_t r[32];
+                        tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + ab * TC_NMAX + (uint32_t)(col0 + 32 * c), r);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[32 * c + j] += __uint_as_float(r[j]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(acce_leader[ab]);
+            }
+            if (timed_out) break;
+            if (STAGE > 0) rk4_slice(1 << 30);  // whatever of the previous tile is left
+            const int i = mt * TC_PAIR_M + row_in_tile;
+            if (i < G.n) {
+                const float si = G.rs[i];
+                float *dst = STAGE == 0 ? p.I : p.Iscr;
+                const int64_t base = G.state_off + i;
+#pragma unroll
+                for (int c = 0; c < 128; ++c) {
+                    const int b = col0 + c;
+                    if (c >= ncol || b >= G.B) break;
+                    dst[base + (int64_t)b * G.n] = si * acc[c];
+                }
+            }
+            if (STAGE > 0) {
+                pg = g;
+                pmt = mt;
+                pnext = 0;
+            }
         }
+        if (STAGE > 0 && !timed_out) rk4_slice(1 << 30);
     }
     // After a timeout, copies already issued may still land in shared memory and count on
     // the leader's barriers: give them time before the pair leaves (bounded, ~1 ms).
@@ -505,6 +532,7 @@ struct nf_group_state {
     int64_t state_total = 0;
     int traj_total = 0;
     int nclusters = 0;                     // CTA pairs per launch
+    float *Iscr = nullptr;                 // state_total: sums awaiting the deferred RK4 update
     int *sched = nullptr;                  // device: [nclusters + 1] offsets, then the tile list
     nfi::TcParams params[2];               // [0]: reads F buffer 0, writes 1; [1]: reads 1, writes 0
 };
@@ -543,8 +571,13 @@ static nf_status build_group_params(nf_operator *op) {
             const int in = par, out = 1 - par;
             G.Fhi_out = gs->F[m][out][0];
             G.Flo_out = gs->F[m][out][1];
-            NF_TRY(make_map(&P.tmA_hi[k], mo->Whi, mo->n, mo->n, mo->n_pad, TC_M));
-            NF_TRY(make_map(&P.tmA_lo[k], mo->Wlo, mo->n, mo->n, mo->n_pad, TC_M));
+            // W planes in the blocked layout: viewed as (n_pad / 128) x (n_pad / 32) blocks of
+            // 128 rows x 32 columns stacked row after row, so block (rb, kb) starts at row
+            // (rb * n_pad / 32 + kb) * 128 of a 32-column matrix
+            const int64_t wrows = mo->n_pad * (mo->n_pad / kBlkCols);
+            NF_TRY(make_map(&P.tmA_hi[k], mo->Whi, kBlkCols, wrows, kBlkCols, TC_M));
+            NF_TRY(make_map(&P.tmA_lo[k], mo->Wlo, kBlkCols, wrows, kBlkCols, TC_M));
+            G.nkb_pad = (int)(mo->n_pad / kBlkCols);
             // each CTA of a pair stages half of the N trajectory rows
             NF_TRY(make_map(&P.tmB_hi[k], gs->F[m][in][0], mo->n, G.B, mo->n_pad, G.n_mma / 2));
             NF_TRY(make_map(&P.tmB_lo[k], gs->F[m][in][1], mo->n, G.B, mo->n_pad, G.n_mma / 2));
@@ -617,6 +650,7 @@ void destroy_group(nf_operator *op) {
     if (!op->group) return;
     nf_group_state *gs = op->group;
     cudaFree(gs->sched);
+    cudaFree(gs->Iscr);
     for (int m = 0; m < gs->count; ++m)
         for (int b = 0; b < 2; ++b)
             for (int h = 0; h < 2; ++h) cudaFree(gs->F[m][b][h]);
@@ -662,6 +696,7 @@ nf_status tc_launch(nf_operator *op, int parity, int mode, float *I, float *u, c
     TcParams P = op->group->params[parity];
     P.mode = mode;
     P.I = I;
+    P.Iscr = op->group->Iscr;
     P.u = u;
     P.U = op->U;
     P.ks = op->ks;
@@ -751,6 +786,7 @@ extern "C" nf_status nf_operator_group(nf_operator *const *ops, const int *B_per
     op->t0_dev = reinterpret_cast<double *>(reinterpret_cast<char *>(op->step_ctr) + 40);
     e = cudaMalloc(&op->U, sizeof(float) * total);
     if (e == cudaSuccess) e = cudaMalloc(&op->ks, sizeof(float) * total);
+    if (e == cudaSuccess) e = cudaMalloc(&gs->Iscr, sizeof(float) * total);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(state)", __FILE__, __LINE__));
     op->state_cap = (size_t)total;
     nf_status st = build_group_params(op);
