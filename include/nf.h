@@ -133,7 +133,7 @@ NF_API nf_status nf_operator_create(const float *x, const float *q, int64_t n, n
 NF_API nf_status nf_operator_destroy(nf_operator *op);
 
 /* Batched tensor-core operator over several node sets (the batching form of Eq. (2.9)):
- * ops[g] (count <= 4) are NF_DENSE_BF16X2 operators with n_g >= 32 nodes, advanced with
+ * ops[g] (count <= 4) are NF_DENSE_BF16X2 operators with n_g >= 64 nodes, advanced with
  * B_per_op[g] (1..256) trajectories each.  Per RK4 stage one persistent tcgen05 GEMM
  * computes, for every group, D = Whi Fhi + Whi Flo + Wlo Fhi (bf16 inputs, FP32 tensor-
  * memory accumulation; F = f(U) split into bf16 hi + lo) and its epilogue performs the
@@ -142,7 +142,8 @@ NF_API nf_status nf_operator_destroy(nf_operator *op);
  * B_g x n_g blocks; beta, theta likewise concatenated; forcing must be NONE; ckpt holds
  * (nsteps / C + 1) copies of the concatenated state.  The members must outlive the group,
  * which does not own them (nf_operator_destroy on the group frees only its own buffers).
- * Errors: NF_ERR_ARG, NF_ERR_NOMEM, NF_ERR_CUDA. */
+ * Errors: NF_ERR_ARG, NF_ERR_NOMEM, NF_ERR_CUDA, NF_ERR_UNSUPPORTED (no two-SM cluster of
+ * the kernel fits on the device). */
 NF_API nf_status nf_operator_group(nf_operator *const *ops, const int *B_per_op, int count, void *stream,
                                    nf_operator **grouped);
 

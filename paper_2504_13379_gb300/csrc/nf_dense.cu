@@ -7,7 +7,7 @@
 //   NF_DENSE_BF16X2: s_i = 2^ceil(log2 max_j |WQ_ij|) (a power of two, so dividing by
 //                    it is exact); hi = bf16_rn(WQ/s_i), lo = bf16_rn(WQ/s_i - hi).
 //                    hi + lo carries ~16 significant bits; I_i = s_i sum_j (hi+lo) F_j.
-//                    The two planes use the blocked layout (128 x 32 blocks of 8 KB), the
+//                    The two planes use the blocked layout (128 x 64 blocks of 16 KB), the
 //                    tile the batched tensor-core GEMM reads with one sequential copy.
 // Apply (every stage): HBM-bound stream of 4 bytes per entry for either plane type.
 // Work items (32-row block, column split) write partial sums like the matrix-free

@@ -184,13 +184,13 @@ struct nf_operator {
 
 namespace nfi {
 
-// Blocked layout of the bf16 planes: 128-row x 32-column blocks of 8 KB, each stored row by
-// row (64 bytes per row), blocks ordered by row block, then column block.  A tensor-core
-// operand tile (128 rows x 32 K) is one contiguous 8 KB read; a row's 32-column pieces lie
-// 8 KB apart.  n_pad is a multiple of 1024, so the blocks tile the padded matrix exactly.
-constexpr int kBlkRows = 128, kBlkCols = 32;
+// Blocked layout of the bf16 planes: 128-row x 64-column blocks of 16 KB, each stored row by
+// row (128 bytes per row), blocks ordered by row block, then column block.  A tensor-core
+// operand tile (128 rows x 64 K) is one contiguous 16 KB read; a row's 64-column pieces lie
+// 16 KB apart.  n_pad is a multiple of 1024, so the blocks tile the padded matrix exactly.
+constexpr int kBlkRows = 128, kBlkCols = 64;
 __host__ __device__ __forceinline__ int64_t blocked_offset(int64_t i, int64_t j, int64_t n_pad) {
-    return (((i >> 7) * (n_pad >> 5) + (j >> 5)) << 12) + ((i & 127) << 5) + (j & 31);
+    return (((i >> 7) * (n_pad >> 6) + (j >> 6)) << 13) + ((i & 127) << 6) + (j & 63);
 }
 
 // ---------------------------------------------------------------- launch plans

@@ -10,21 +10,24 @@
 //
 // Two-SM tiles.  CTAs run in clusters of two on neighbouring SMs; a pair owns 256 output rows
 // and issues tcgen05.mma.cta_group::2 with M = 256: each CTA stages its own 128 rows of W hi/lo
-// and one half of the F hi/lo tile (N/2 trajectory rows), so a pipeline stage is 32 KB per CTA
-// instead of 48 KB and the ring is 7 stages deep -- about 2.3x the bytes in flight per SM of a
-// one-SM M = 128 tile at N = 256, and half the L2 -> SM traffic for the shared F tile.
+// and one half of the F hi/lo tile (N/2 trajectory rows), which halves the L2 -> SM traffic
+// for the shared F tile.  A pipeline stage covers K = 64 (128-byte rows, 128-byte swizzle):
+// 32 KB of W and up to 32 KB of F per CTA, three stages deep.  Large stages matter more than
+// deep rings here: each stage costs a fixed producer / consumer hand-off, and one SM streams
+// about 100 GB/s with 64 KB stages against about 45 GB/s with 16 KB stages.
 // 320 threads per CTA, one CTA per SM, persistent over a host-balanced list of pair tiles:
-//   warp 0      TMA producer (both CTAs): W hi/lo tiles (128 x 32) and half F tiles
-//               (N/2 x 32), 64-byte swizzle; completion of both CTAs' copies is counted on
-//               the leader CTA's "full" barrier
+//   warp 0      TMA producer (both CTAs): W hi/lo tiles (128 x 64, one contiguous block of the
+//               blocked layout each) and half F tiles (N/2 x 64); completion of both CTAs'
+//               copies is counted on the leader CTA's "full" barrier
 //   warp 1      owns the tensor-memory allocation (2 x 256 columns per CTA, double buffered);
 //               in the leader CTA (rank 0) lane 0 issues the MMAs, N = B_g rounded to 16,
 //               K = 16 per instruction, 3 products per K step, and commits to the "empty" and
 //               "accumulator full" barriers of both CTAs (multicast)
 //   warps 2..9  epilogue (both CTAs): two warps per TMEM lane quarter (one TMEM lane = one
-//               row i), 128 columns each; they drain the accumulator after every K chunk of
-//               256, add it into FP32 registers, release the chunk buffer on the leader's
-//               barrier, then run the fused RK4 stage and the next-stage bf16 split
+//               row i), N/2 columns each; they drain the accumulator after every K chunk of
+//               256, add it into FP32 registers and release the chunk buffer on the leader's
+//               barrier; the fused RK4 stage update and next-stage bf16 split of a tile run
+//               deferred, in slices between the next tile's chunk drains
 // Chunking K matters for accuracy: the tensor core's FP32 accumulation truncates when
 // aligning addends, an error that grows with the number of K steps summed in tensor
 // memory; 256-wide chunks added with round-to-nearest FP32 adds keep the long sums
@@ -45,16 +48,16 @@ namespace nfi {
 
 constexpr int TC_M = 128;          // rows per CTA
 constexpr int TC_PAIR_M = 256;     // rows per cluster pair (MMA M)
-constexpr int TC_BK = 32;          // K elements per stage: 64-byte rows
+constexpr int TC_BK = 64;          // K elements per stage: 128-byte rows
 constexpr int TC_NMAX = 256;
-constexpr int TC_STAGES = 7;
+constexpr int TC_STAGES = 3;
 constexpr int TC_MAXG = 4;
 constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 TMEM + MMA, warps 2..9 epilogue
 constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_CHUNK = 8;        // K blocks (256 elements) accumulated in tensor memory per chunk
+constexpr int TC_CHUNK = 4;        // K blocks (256 elements) accumulated in tensor memory per chunk
 constexpr int TC_EPI_BATCH = 2;    // trajectory columns per batch of epilogue loads
-constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;             // 8 KB per plane
-constexpr uint32_t TC_BH_BYTES = (TC_NMAX / 2) * TC_BK * 2;   // 8 KB per plane: half of N = 256
+constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;             // 16 KB per plane
+constexpr uint32_t TC_BH_BYTES = (TC_NMAX / 2) * TC_BK * 2;   // 16 KB per plane: half of N = 256
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_BH_BYTES;
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
 
@@ -119,10 +122,10 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         : "memory");
 }
 
-// K-major operand, 64-byte swizzle: 8-row x 64-byte atoms stacked every 512 bytes.
-__device__ __forceinline__ uint64_t sdesc_sw64(const void *p) {
+// K-major operand, 128-byte swizzle: 8-row x 128-byte atoms stacked every 1024 bytes.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void *p) {
     const uint64_t a = smem_u32(p);
-    return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+    return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
 __device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -280,8 +283,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint64_t ahi = sdesc_sw64(sA_hi(s)), alo = sdesc_sw64(sA_lo(s));
-                        const uint64_t bhi = sdesc_sw64(sB_hi(s)), blo = sdesc_sw64(sB_lo(s));
+                        const uint64_t ahi = sdesc_sw128(sA_hi(s)), alo = sdesc_sw128(sA_lo(s));
+                        const uint64_t bhi = sdesc_sw128(sB_hi(s)), blo = sdesc_sw128(sB_lo(s));
 #pragma unroll
                         for (int k = 0; k < TC_BK / 16; ++k) {
                             const uint64_t off = (uint64_t)((k * 32) >> 4);
@@ -514,7 +517,7 @@ static nf_status make_map(CUtensorMap *m, const void *base, int64_t cols, int64_
     const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return NF_OK;
@@ -571,9 +574,9 @@ static nf_status build_group_params(nf_operator *op) {
             const int in = par, out = 1 - par;
             G.Fhi_out = gs->F[m][out][0];
             G.Flo_out = gs->F[m][out][1];
-            // W planes in the blocked layout: viewed as (n_pad / 128) x (n_pad / 32) blocks of
-            // 128 rows x 32 columns stacked row after row, so block (rb, kb) starts at row
-            // (rb * n_pad / 32 + kb) * 128 of a 32-column matrix
+            // W planes in the blocked layout: viewed as (n_pad / 128) x (n_pad / 64) blocks of
+            // 128 rows x 64 columns stacked row after row, so block (rb, kb) starts at row
+            // (rb * n_pad / 64 + kb) * 128 of a 64-column matrix
             const int64_t wrows = mo->n_pad * (mo->n_pad / kBlkCols);
             NF_TRY(make_map(&P.tmA_hi[k], mo->Whi, kBlkCols, wrows, kBlkCols, TC_M));
             NF_TRY(make_map(&P.tmA_lo[k], mo->Wlo, kBlkCols, wrows, kBlkCols, TC_M));
@@ -595,7 +598,7 @@ static nf_status build_group_params(nf_operator *op) {
 }
 
 // Longest-processing-time assignment of the pair tiles to the clusters of one launch.  A
-// tile's cost is its number of 32-wide K blocks times the larger of the per-SM MMA time of a
+// tile's cost is its number of 32-wide K steps times the larger of the per-SM MMA time of a
 // block (3 products x 128 x N x 32 FMA at 4096 FMA per clock: 3 N clocks) and the time to
 // stream its 16 KB of W hi/lo per SM at an even share of HBM bandwidth (~760 clocks).
 static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
@@ -613,7 +616,7 @@ static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
     std::vector<double> cost(ntiles);
     for (int k = 0; k < P.ngroups; ++k) {
         const TcGroup &G = P.grp[k];
-        const double c = (double)ceil_div(G.n, TC_BK) * std::max(3.0 * G.n_mma, 760.0);
+        const double c = (double)ceil_div(G.n, 32) * std::max(3.0 * G.n_mma, 760.0);
         for (int t = P.tile_start[k]; t < P.tile_start[k + 1]; ++t) cost[t] = c;
     }
     std::vector<int> order(ntiles);
