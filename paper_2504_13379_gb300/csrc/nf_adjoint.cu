@@ -235,8 +235,7 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     cudaStream_t s = as_stream(stream);
     const int64_t n = op->n, n_pad = op->n_pad;
     const size_t BN = (size_t)B * n;
-    const SplitPlan fpl = mf_plan(op);
-    NF_TRY(ensure_workspace(op, B, fpl.splits));
+    NF_TRY(ensure_workspace(op, B, mf_splits(op, B)));
     const SplitPlan apl = adj_plan(op);
     const int Cseg = std::min(C, std::max(nsteps, 1));
     float *stages = nullptr, *lam = nullptr, *acc = nullptr, *ubuf = nullptr, *part6 = nullptr, *contrib = nullptr;

@@ -155,7 +155,8 @@ struct nf_operator {
     int device = 0;
     float4 *x4 = nullptr;    // n_pad: (x, y, z, 0)
     float *xyz = nullptr;    // 3 x n_pad: coordinates times sqrt(log2 e)/s1, structure of arrays
-    int mf_variant = -1;     // launch shape of the packed pair kernel (autotuned)
+    int mf_variant = -1;     // launch shape of the packed pair kernel
+    int mf_sym_r = 8;        // rows per warp of the symmetric single-trajectory kernel (autotuned)
     int *rowperm = nullptr;  // n_pad: row order of the packed pair kernel (Morton order of the nodes)
     float *q = nullptr;      // n_pad, zero padded
     // dense planes (row-major, leading dimension ld = n_pad)
@@ -207,6 +208,8 @@ nf_status ensure_workspace(nf_operator *op, int B, int splits);
 // matrix-free / dense nonlocal launches (g must hold q f(U) / f(U) for B trajectories)
 nf_status mf_init_attrs();
 nf_status mf_build_row_order(nf_operator *op, cudaStream_t s);
+SplitPlan mf_plan(nf_operator *op);     // column splits of the multi-trajectory matrix-free launches
+int mf_splits(nf_operator *op, int B);  // partial-sum slots of a matrix-free launch over B trajectories
 nf_status mf_autotune(nf_operator *op, cudaStream_t s);
 void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits);
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out);

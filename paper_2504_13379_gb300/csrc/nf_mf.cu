@@ -19,6 +19,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 namespace nfi {
 
@@ -150,6 +151,11 @@ typedef unsigned long long u64;
 __device__ __forceinline__ u64 f2_sub(u64 a, u64 b) {
     u64 d;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_add(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 __device__ __forceinline__ u64 f2_mul(u64 a, u64 b) {
@@ -381,6 +387,279 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
 }
 
 // ----------------------------------------------------------------------------
+// Symmetric single-trajectory kernel.  w(x_i, x_j) = w(x_j, x_i), so every unordered pair
+// is evaluated once and feeds both sums: I_i += w_ij g_j and I_j += w_ij g_i.  Nodes are
+// taken in Morton order (rowperm) and cut into blocks of MS_BLK; one CTA takes a block
+// pair (I <= J): it gathers block J's coordinates and g into shared memory, its warps
+// sweep block I's rows R at a time (the packed forms above: expanded about the warp's
+// centre when its rows are close, coordinate differences otherwise), accumulate the row
+// sums in registers and the column sums per warp in shared memory.  Row sums of pair
+// (I, J) go to partial slot J, column sums to slot I; a diagonal pair (I = I) sweeps all
+// ordered pairs of the block and writes rows only.  Every (slot, node) entry is written
+// exactly once, and the stage kernel adds the n_pad / MS_BLK slots in a fixed order, so
+// results are deterministic.  Per unordered pair (expanded form, M > 0) this costs one
+// exponential and 9 FMA-pipe lane operations for two ordered pairs.
+constexpr int MS_BLK = 1024;
+constexpr int MS_THREADS = 256;
+constexpr int MS_WARPS = MS_THREADS / 32;
+// shared memory (4-byte words): column block x, y, z, g, node (5 MS_BLK); row block node and
+// precomputed row operands mx, my, mz, h1, h2, f1, f2 (8 MS_BLK); per-pass centre and form
+// (MS_BLK: up to MS_BLK / 4 passes x 4); per-warp column sums (MS_WARPS MS_BLK)
+constexpr size_t MS_SMEM = sizeof(float) * ((5 + 8 + 1 + MS_WARPS) * (size_t)MS_BLK);
+
+// Block pair of CTA t over nb blocks, enumerated as (0,0), (0,1), (1,1), (0,2), ...
+__device__ __forceinline__ void sym_pair(int64_t t, int &I, int &J) {
+    int64_t j = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (j * (j + 1) / 2 > t) --j;
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    J = (int)j;
+    I = (int)(t - j * (j + 1) / 2);
+}
+
+// Sum R per-lane values over the warp.  Transposed butterfly: at each of the first log2(R)
+// steps a lane keeps half of its rows and adds its partner's copy of them (R - 1 shuffles
+// in total), then plain xor steps finish.  Every lane returns the total of row `row`.
+template <int R>
+__device__ __forceinline__ float warp_reduce_rows(float (&v)[R], int lane, int &row) {
+    int base = 0;
+    int cnt = R;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        if (cnt > 1) {
+            const int h = cnt >> 1;
+            const bool upper = (lane & off) != 0;
+#pragma unroll
+            for (int k = 0; k < R / 2; ++k) {
+                if (k < h) {
+                    const float send = upper ? v[k] : v[k + h];
+                    const float keep = upper ? v[k + h] : v[k];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+            }
+            if (upper) base += h;
+            cnt = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+        }
+    }
+    row = base;
+    return v[0];
+}
+
+template <int R, int M>
+__global__ void __launch_bounds__(MS_THREADS, 2)
+mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
+              int64_t n_pad, int B, int b_base, float k2, float A1, float A2, float *__restrict__ partial) {
+    static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
+    static_assert(R == 4 || R == 8, "rows per warp");
+    constexpr int NPASS = MS_BLK / R;
+    extern __shared__ __align__(16) float ms_smem[];
+    float *xs = ms_smem, *ys = xs + MS_BLK, *zs = ys + MS_BLK, *gs = zs + MS_BLK;
+    int *cnode = reinterpret_cast<int *>(gs + MS_BLK);
+    int *rnode = cnode + MS_BLK;
+    float *rmx = reinterpret_cast<float *>(rnode + MS_BLK), *rmy = rmx + MS_BLK, *rmz = rmy + MS_BLK;
+    float *rh1 = rmz + MS_BLK, *rh2 = rh1 + MS_BLK, *rf1 = rh2 + MS_BLK, *rf2 = rf1 + MS_BLK;
+    float4 *pc = reinterpret_cast<float4 *>(rf2 + MS_BLK);  // per pass: centre, form (w = 1: expanded)
+    float *colacc = reinterpret_cast<float *>(pc + MS_BLK / 4);  // [MS_WARPS][MS_BLK]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int I, J;
+    sym_pair(blockIdx.x, I, J);
+    const bool diag = I == J;
+    const int b = b_base + blockIdx.z;
+    const float *g = g_all + (int64_t)b * n_pad;
+    const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
+    const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
+    // gather the column block, and the row block's raw data (x, y, z, g in mx, my, mz, h1)
+    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+        const int node = __ldg(rowperm + cbase + k);
+        cnode[k] = node;
+        xs[k] = X[node];
+        ys[k] = Y[node];
+        zs[k] = Z[node];
+        gs[k] = g[node];
+        const int rn = diag ? node : __ldg(rowperm + rbase + k);
+        rnode[k] = rn;
+        rmx[k] = X[rn];
+        rmy[k] = Y[rn];
+        rmz[k] = Z[rn];
+        rh1[k] = g[rn];
+    }
+    for (int k = tid; k < MS_WARPS * MS_BLK; k += MS_THREADS) colacc[k] = 0.f;
+    __syncthreads();
+    const float sk = M > 0 ? sqrtf(k2) : 1.f;
+    // one thread per pass: centre of the pass's R rows, the form, and the row operands:
+    // expanded form -2 (x_i - c) (times s1/s2 when M > 0), else x_i; f1, f2 the row factors
+    // 2^(-n_i) of e1 and e2 (1 in the difference form); h1 = A1 f1 g_i and h2 = -A2 f2 g_i
+    // weight the row's terms in the column sums
+    for (int ps = tid; ps < NPASS; ps += MS_THREADS) {
+        const int r0 = ps * R;
+        float lox = 3.4e38f, loy = 3.4e38f, loz = 3.4e38f, hix = -3.4e38f, hiy = -3.4e38f, hiz = -3.4e38f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            lox = fminf(lox, rmx[r0 + r]), hix = fmaxf(hix, rmx[r0 + r]);
+            loy = fminf(loy, rmy[r0 + r]), hiy = fmaxf(hiy, rmy[r0 + r]);
+            loz = fminf(loz, rmz[r0 + r]), hiz = fmaxf(hiz, rmz[r0 + r]);
+        }
+        const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy), cz = 0.5f * (loz + hiz);
+        float spread = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float dx = rmx[r0 + r] - cx, dy = rmy[r0 + r] - cy, dz = rmz[r0 + r] - cz;
+            spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
+        }
+        const bool local = spread <= kMfLocalSpread;
+        pc[ps] = make_float4(cx, cy, cz, local ? 1.f : 0.f);
+        const float lsc = -2.f * sk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = r0 + r;
+            const float x = local ? lsc * (rmx[k] - cx) : rmx[k];
+            const float y = local ? lsc * (rmy[k] - cy) : rmy[k];
+            const float z = local ? lsc * (rmz[k] - cz) : rmz[k];
+            const float ni = 0.25f * (x * x + y * y + z * z);  // n_i, in units of s2 when M > 0
+            const float f1 = local ? exp2f(M > 0 ? -(float)M * ni : -ni) : 1.f;
+            const float f2 = local ? exp2f(M > 0 ? -ni : -k2 * ni) : 1.f;
+            const float gi = rh1[k];
+            rmx[k] = x;
+            rmy[k] = y;
+            rmz[k] = z;
+            rh1[k] = A1 * f1 * gi;
+            rh2[k] = -A2 * f2 * gi;
+            rf1[k] = A1 * f1;
+            rf2[k] = -A2 * f2;
+        }
+    }
+    __syncthreads();
+    const u64 nk2 = f2_pack(-k2, -k2), skp = f2_pack(sk, sk), k2p = f2_pack(k2, k2);
+    const float4 *xs4 = reinterpret_cast<const float4 *>(xs), *ys4 = reinterpret_cast<const float4 *>(ys);
+    const float4 *zs4 = reinterpret_cast<const float4 *>(zs), *gs4 = reinterpret_cast<const float4 *>(gs);
+    float4 *cw4 = reinterpret_cast<float4 *>(colacc + warp * MS_BLK);
+    float *out_rows = partial + ((int64_t)J * B + b) * n_pad;
+    auto lo2 = [](float4 v) { return f2_pack(v.x, v.y); };
+    auto hi2 = [](float4 v) { return f2_pack(v.z, v.w); };
+    // e1, e2 of two pairs from the exponent argument (expanded s_ij or r^2)
+    auto exps = [&](u64 arg, u64 &e1, u64 &e2) {
+        float s0, s1v;
+        f2_unpack(arg, s0, s1v);
+        if constexpr (M > 0) {
+            e2 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+            const u64 sq = f2_mul(e2, e2);
+            e1 = M == 2 ? sq : (M == 3 ? f2_mul(sq, e2) : f2_mul(sq, sq));
+        } else {
+            e1 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+            e2 = f2_ex2(f2_mul(arg, nk2));
+        }
+    };
+
+    for (int ps = warp; ps < NPASS; ps += MS_WARPS) {
+        const int r0 = ps * R;
+        const float4 c = pc[ps];
+        const bool local = c.w != 0.f;  // warp-uniform
+        u64 xi[R], yi[R], zi[R], h1[R], h2[R], a1[R], a2[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            xi[r] = f2_pack(rmx[r0 + r], rmx[r0 + r]);
+            yi[r] = f2_pack(rmy[r0 + r], rmy[r0 + r]);
+            zi[r] = f2_pack(rmz[r0 + r], rmz[r0 + r]);
+            h1[r] = f2_pack(rh1[r0 + r], rh1[r0 + r]);
+            h2[r] = f2_pack(rh2[r0 + r], rh2[r0 + r]);
+            a1[r] = 0ull;
+            a2[r] = 0ull;
+        }
+        const u64 cxp = f2_pack(c.x, c.x), cyp = f2_pack(c.y, c.y), czp = f2_pack(c.z, c.z);
+        // each lane takes 4 consecutive columns (two f32x2 pairs) per step
+        if (local) {
+#pragma unroll 1
+            for (int q = lane; q < MS_BLK / 4; q += 32) {
+                const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
+                u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
+                u64 yt[2] = {f2_sub(lo2(y4), cyp), f2_sub(hi2(y4), cyp)};
+                u64 zt[2] = {f2_sub(lo2(z4), czp), f2_sub(hi2(z4), czp)};
+                const u64 gj[2] = {lo2(g4), hi2(g4)};
+                u64 nj[2], cacc[2] = {0ull, 0ull};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if constexpr (M > 0) {
+                        xt[h] = f2_mul(xt[h], skp);
+                        yt[h] = f2_mul(yt[h], skp);
+                        zt[h] = f2_mul(zt[h], skp);
+                    }
+                    nj[h] = f2_fma(zt[h], zt[h], f2_fma(yt[h], yt[h], f2_mul(xt[h], xt[h])));
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const u64 sij = f2_fma(xi[r], xt[h], f2_fma(yi[r], yt[h], f2_fma(zi[r], zt[h], nj[h])));
+                        u64 e1, e2;
+                        exps(sij, e1, e2);
+                        a1[r] = f2_fma(e1, gj[h], a1[r]);
+                        a2[r] = f2_fma(e2, gj[h], a2[r]);
+                        cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
+                    }
+                }
+                if (!diag) {
+                    float4 cv = cw4[q];
+                    u64 c0 = f2_add(lo2(cv), cacc[0]), c1 = f2_add(hi2(cv), cacc[1]);
+                    f2_unpack(c0, cv.x, cv.y);
+                    f2_unpack(c1, cv.z, cv.w);
+                    cw4[q] = cv;
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int q = lane; q < MS_BLK / 4; q += 32) {
+                const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
+                const u64 xj[2] = {lo2(x4), hi2(x4)}, yj[2] = {lo2(y4), hi2(y4)}, zj[2] = {lo2(z4), hi2(z4)};
+                const u64 gj[2] = {lo2(g4), hi2(g4)};
+                u64 cacc[2] = {0ull, 0ull};
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const u64 dx = f2_sub(xi[r], xj[h]), dy = f2_sub(yi[r], yj[h]), dz = f2_sub(zi[r], zj[h]);
+                        u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                        if constexpr (M > 0) r2s = f2_mul(r2s, k2p);  // in units of s2
+                        u64 e1, e2;
+                        exps(r2s, e1, e2);
+                        a1[r] = f2_fma(e1, gj[h], a1[r]);
+                        a2[r] = f2_fma(e2, gj[h], a2[r]);
+                        cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
+                    }
+                }
+                if (!diag) {
+                    float4 cv = cw4[q];
+                    u64 c0 = f2_add(lo2(cv), cacc[0]), c1 = f2_add(hi2(cv), cacc[1]);
+                    f2_unpack(c0, cv.x, cv.y);
+                    f2_unpack(c1, cv.z, cv.w);
+                    cw4[q] = cv;
+                }
+            }
+        }
+        float v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float p0, p1, q0, q1;
+            f2_unpack(a1[r], p0, p1);
+            f2_unpack(a2[r], q0, q1);
+            v[r] = rf1[r0 + r] * (p0 + p1) + rf2[r0 + r] * (q0 + q1);
+        }
+        int row;
+        const float tot = warp_reduce_rows<R>(v, lane, row);
+        if ((lane & (32 / R - 1)) == 0) out_rows[rnode[r0 + row]] = tot;
+    }
+    if (diag) return;
+    __syncthreads();
+    float *out_cols = partial + ((int64_t)I * B + b) * n_pad;
+    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < MS_WARPS; ++w) v += colacc[w * MS_BLK + k];
+        out_cols[cnode[k]] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // split planner: (row blocks x column splits) items of equal cost; pick the number
 // of splits that best fills whole waves of resident blocks.
 SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm) {
@@ -419,7 +698,20 @@ static cudaError_t set_mf_attr() {
 }
 
 // Opt every pair-kernel instance into its shared-memory size (outside any capture).
+template <int R, int M>
+static cudaError_t set_sym_attr() {
+    return cudaFuncSetAttribute(mf_sym_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MS_SMEM);
+}
+
 nf_status mf_init_attrs() {
+    NF_CUDA_TRY((set_sym_attr<4, 0>()));
+    NF_CUDA_TRY((set_sym_attr<4, 2>()));
+    NF_CUDA_TRY((set_sym_attr<4, 3>()));
+    NF_CUDA_TRY((set_sym_attr<4, 4>()));
+    NF_CUDA_TRY((set_sym_attr<8, 0>()));
+    NF_CUDA_TRY((set_sym_attr<8, 2>()));
+    NF_CUDA_TRY((set_sym_attr<8, 3>()));
+    NF_CUDA_TRY((set_sym_attr<8, 4>()));
     NF_CUDA_TRY((set_mf_attr<1, 2>()));
     NF_CUDA_TRY((set_mf_attr<2, 2>()));
     NF_CUDA_TRY((set_mf_attr<4, 2>()));
@@ -513,8 +805,43 @@ static nf_status launch_mf_packed(nf_operator *op, int B, int b_base, int groups
     return NF_OK;
 }
 
-// Default before (or without) autotuning: small node sets want more, smaller blocks.
-static int default_variant(int64_t n_pad) { return n_pad >= 16384 ? 1 : 0; }
+// Launch shape of the packed kernel (single trajectories inside a multi-trajectory call):
+// small node sets want more, smaller blocks.
+static int default_variant(int64_t n_pad) { return n_pad >= 16384 ? 3 : 0; }
+
+// ---- symmetric kernel launch (B = 1)
+static int64_t sym_pairs(const nf_operator *op) {
+    const int64_t nb = op->n_pad / MS_BLK;
+    return nb * (nb + 1) / 2;
+}
+
+template <int R>
+static void launch_sym_r(nf_operator *op, int B, int b_base, cudaStream_t s) {
+    const nf_kernel &k = op->kp;
+    const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
+    dim3 grid((unsigned)sym_pairs(op), 1, 1);
+#define NF_SYM_ARGS op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, op->partial
+    switch (mf_width_ratio(k)) {
+        case 2: mf_sym_kernel<R, 2><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
+        case 3: mf_sym_kernel<R, 3><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
+        case 4: mf_sym_kernel<R, 4><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
+        default: mf_sym_kernel<R, 0><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
+    }
+#undef NF_SYM_ARGS
+}
+
+static nf_status launch_sym(nf_operator *op, int B, int b_base, cudaStream_t s) {
+    if (op->mf_sym_r == 4)
+        launch_sym_r<4>(op, B, b_base, s);
+    else
+        launch_sym_r<8>(op, B, b_base, s);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+int mf_splits(nf_operator *op, int B) {
+    return B == 1 ? (int)(op->n_pad / MS_BLK) : mf_plan(op).splits;
+}
 
 static SplitPlan variant_plan(int64_t n_pad, int v) {
     return plan_splits(n_pad, MF_WARPS * kMfVariants[v].R, kMfVariants[v].TJ, variant_resident(v));
@@ -525,62 +852,67 @@ SplitPlan mf_plan(nf_operator *op) {
     return variant_plan(op->n_pad, op->mf_variant);
 }
 
+// Shape of the single-trajectory (symmetric) launch: rows per warp, block width, slots.
 void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits) {
-    const SplitPlan pl = mf_plan(op);
-    *R = kMfVariants[op->mf_variant].R;
-    *TJ = kMfVariants[op->mf_variant].TJ;
-    *splits = pl.splits;
+    *R = op->mf_sym_r;
+    *TJ = MS_BLK;
+    *splits = (int)(op->n_pad / MS_BLK);
 }
 
 // Rows per warp of the scalar multi-trajectory kernel (2 or 4 are instantiated).
 static int mf_rows_per_warp(int64_t n_pad) { return n_pad >= 16384 ? 4 : 2; }
 
-// Time every launch shape once on this operator's size and keep the fastest (cached
-// per padded size and device).  Runs outside any stream capture.
+// Time the symmetric kernel's launch shapes (rows per warp 4 or 8) once on this operator's
+// size and keep the fastest (cached per device, padded size and width ratio).  Runs
+// outside any stream capture.
 nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     static std::mutex mu;
-    static std::map<std::pair<int, int64_t>, int> cache;
-    const auto key = std::make_pair(op->device, op->n_pad);
+    static std::map<std::tuple<int, int64_t, int>, int> cache;
+    op->mf_variant = default_variant(op->n_pad);
+    const auto key = std::make_tuple(op->device, op->n_pad, mf_width_ratio(op->kp));
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            op->mf_variant = it->second;
+            op->mf_sym_r = it->second;
             return NF_OK;
         }
     }
-    int max_splits = 1;
-    for (int v = 0; v < kNumMfVariants; ++v) max_splits = std::max(max_splits, variant_plan(op->n_pad, v).splits);
-    NF_TRY(ensure_workspace(op, 1, max_splits));
+    NF_TRY(ensure_workspace(op, 1, mf_splits(op, 1)));
+    NF_CUDA_TRY(cudaMemsetAsync(op->g, 0, sizeof(float) * op->n_pad, s));
     cudaEvent_t e0, e1;
     NF_CUDA_TRY(cudaEventCreate(&e0));
     NF_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_v = default_variant(op->n_pad);
-    for (int v = 0; v < kNumMfVariants; ++v) {
-        op->mf_variant = v;
-        const SplitPlan pl = variant_plan(op->n_pad, v);
-        NF_TRY(launch_mf_packed(op, 1, 0, 1, pl, s));  // warm-up
+    int best_r = 8;
+    for (int r : {4, 8}) {
+        op->mf_sym_r = r;
+        NF_TRY(launch_sym(op, 1, 0, s));  // warm-up
         NF_CUDA_TRY(cudaEventRecord(e0, s));
-        for (int rep = 0; rep < 2; ++rep) NF_TRY(launch_mf_packed(op, 1, 0, 1, pl, s));
+        for (int rep = 0; rep < 2; ++rep) NF_TRY(launch_sym(op, 1, 0, s));
         NF_CUDA_TRY(cudaEventRecord(e1, s));
         NF_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
         NF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) {
             best = ms;
-            best_v = v;
+            best_r = r;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    op->mf_variant = best_v;
+    op->mf_sym_r = best_r;
     std::lock_guard<std::mutex> lock(mu);
-    cache[key] = best_v;
+    cache[key] = best_r;
     return NF_OK;
 }
 
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
+    if (B == 1) {  // one trajectory: symmetric kernel, one partial slot per node block
+        NF_TRY(launch_sym(op, 1, 0, s));
+        *splits_out = (int)(op->n_pad / MS_BLK);
+        return NF_OK;
+    }
     // the column splits (and so the partial-sum layout) come from the packed kernel's
     // plan; the scalar multi-trajectory kernels block rows their own way over the same splits
     const SplitPlan pl = mf_plan(op);
