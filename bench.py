@@ -137,9 +137,21 @@ def peaks():
         return {}
 
 
-# MUFU.EX2 lane-ops per clock per SM on GB300, measured with a dependent-chain
-# throughput probe (32.0 at 1,976-1,984 MHz on all 152 SMs)
-EX2_PER_CLK_SM = 32.0
+# FP32 FMA-pipe lane operations per clock per SM (f32x2 instructions count two), and the
+# lane operations per ordered pair of the symmetric matrix-free kernel in its expanded form
+# with s2^2 / s1^2 = 4 (the workload's kernel): per unordered pair 3 FMA (exponent) +
+# 2 MUL (e1 = e2^4) + 2 FMA (row sums) + 2 FMA (column sums), plus per column and 8-row
+# pass 3 SUB + 3 MUL + 3 FMA (centred, rescaled column and n_j) and 1 ADD (column sums
+# into shared memory): 10.25 per unordered pair, 5.125 per ordered pair.  Diagonal block
+# pairs evaluate their ordered pairs one by one, a 1/nb share of the work.
+FMA_LANES_PER_CLK_SM = 128.0
+LANE_OPS_PER_PAIR = 10.25 / 2.0
+
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels:
+# mf_sym_kernel<8, 4> on the n = 100,000 torus; tc_grouped_kernel on the batched workload at
+# half node counts, scaled to full size by the W bytes a launch streams (4x)
+MF_TRAFFIC_BYTES = 2.16e6 + 0.24e6
+TC_TRAFFIC_BYTES = (2.956e9 + 0.104e9) * 4.0
 
 
 def run_reference(args, rank, world):
@@ -270,6 +282,8 @@ def run_batched(args, dev, steps):
         "ms_per_step": ms, "rk4_steps_per_s": 1e3 / ms, "pair_evals_per_s": 4 * pairs_per_stage / (ms * 1e-3),
         "kernel_ms_per_launch": kms, "build_ms": build_ms, "clocks": clocks,
         "roofline": {"bound": "hbm" if hbm / hbm_peak >= tfl / tc_peak else "tensor",
+                     "traffic": TC_TRAFFIC_BYTES if args.batched_scale == 1.0 else None,
+                     "traffic_unit": "bytes per launch",
                      "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak},
                      "tensor": {"achieved": tfl, "peak": tc_peak, "unit": "TFLOP/s", "frac": tfl / tc_peak,
                                 "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (kernel inside a long step)"}},
@@ -461,11 +475,15 @@ def run_ours(args, rank, world, local_rank):
     if best == "mf":
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clocks["sm_mhz"] or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 1432.0
-        peak = sms * EX2_PER_CLK_SM / 2.0 * mhz * 1e6 / 1e9          # Gpair/s: 2 SFU exponentials per pair
+        nb = -(-n // 1024)
+        ops = LANE_OPS_PER_PAIR * (1.0 + 1.0 / nb)
+        peak = sms * FMA_LANES_PER_CLK_SM * mhz * 1e6 / ops / 1e9     # Gpair/s on the FP32 FMA pipe
         achieved = n * n / (kms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
-                "traffic": None, "peak_basis": f"{sms} SMs x {EX2_PER_CLK_SM:g} MUFU.EX2/clk/SM / 2 per pair x "
-                                               f"{mhz:.0f} MHz (median SM clock in the timed region)"}
+                "traffic": MF_TRAFFIC_BYTES if n == 100000 else None, "traffic_unit": "bytes per launch",
+                "peak_basis": f"{sms} SMs x {FMA_LANES_PER_CLK_SM:g} FP32 FMA-pipe lanes/clk x {mhz:.0f} MHz "
+                              f"(median SM clock in the timed region) / {ops:.3f} lane operations per ordered pair "
+                              f"(symmetric kernel, expanded form, m = 4; SFU: 0.5 exponentials per pair, not binding)"}
     else:
         bytes_per = 4.0 * n * n
         achieved = bytes_per / (kms * 1e-3) / 1e9
