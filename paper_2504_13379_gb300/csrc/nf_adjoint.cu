@@ -8,115 +8,17 @@
 // with W symmetric because the kernel is radial.  Kernel-parameter gradients add
 //     <nu_s, (d_theta W) (q o f(U_s))>,  d w / dA1 = e1, d w / ds1 = 2 A1 r^2 e1 / s1^3,
 //     d w / dA2 = -e2,  d w / ds2 = -2 A2 r^2 e2 / s2^3.
-// The adjoint pair kernel computes, per row i and in one pass over the columns,
-//     sum_j e1 nu_j, sum_j e2 nu_j, sum_j e1 g_j, sum_j r^2 e1 g_j, sum_j e2 g_j,
-//     sum_j r^2 e2 g_j   (two SFU exponentials per pair, six FP32 accumulators),
-// staged like the forward kernel (TMA bulk tiles of x and of (nu, g) pairs).  The
-// epilogue applies the recurrences, writes per-row gradient contributions and prepares
-// (nu, g) of the next stage; a fixed-order reduction accumulates the parameter
-// gradients in FP64.  Stage inputs are recomputed segment by segment from checkpoints.
+// The adjoint pair kernel (adj_sym_kernel, with the forward symmetric kernel's block-pair
+// schedule: each unordered pair evaluated once) computes W nu as partial-slot sums and the
+// four parameter sums sum_ij nu_i g_j (e1, r^2 e1, e2, r^2 e2) as per-CTA partials.  The
+// epilogue adds the slots, applies the recurrences and prepares (nu, g) of the next stage;
+// a fixed-order FP64 reduction accumulates the parameter gradients.  Stage inputs are
+// recomputed segment by segment from checkpoints.
 #include "nf_internal.cuh"
 
 #include <algorithm>
 
 namespace nfi {
-
-constexpr int AD_THREADS = 256;
-constexpr int AD_WARPS = AD_THREADS / 32;
-constexpr int AD_TJ = 512;
-constexpr int AD_R = 2;  // rows per warp (6 accumulators each)
-static_assert(kNodePad % AD_TJ == 0, "tile must divide the node padding");
-
-struct AdSmem {
-    float4 xs[2][AD_TJ];
-    float2 vg[2][AD_TJ];
-    uint64_t bar[2];
-};
-
-// partial layout: [6][splits][B][n_pad]
-__global__ void __launch_bounds__(AD_THREADS)
-adj_pair_kernel(const float4 *__restrict__ x4, const float2 *__restrict__ vg, int64_t n_pad, int B, int b,
-                int64_t jchunk, float c1, float c2, float *__restrict__ partial, int *__restrict__ err) {
-    __shared__ __align__(128) AdSmem sm;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int split = blockIdx.y, nsplit = gridDim.y;
-    const int64_t j0 = (int64_t)split * jchunk, j1 = min(n_pad, j0 + jchunk);
-    const int ntiles = (int)((j1 - j0) / AD_TJ);
-    const int64_t row0 = ((int64_t)blockIdx.x * AD_WARPS + warp) * AD_R;
-    const float2 *vgb = vg + (int64_t)b * n_pad;
-    constexpr uint32_t kTileBytes = AD_TJ * 16 + AD_TJ * 8;
-    if (tid == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    auto issue = [&](int t) {
-        const int buf = t & 1;
-        const int64_t jt = j0 + (int64_t)t * AD_TJ;
-        mbar_arrive_expect_tx(&sm.bar[buf], kTileBytes);
-        bulk_g2s(sm.xs[buf], x4 + jt, AD_TJ * 16, &sm.bar[buf]);
-        bulk_g2s(sm.vg[buf], vgb + jt, AD_TJ * 8, &sm.bar[buf]);
-    };
-    if (tid == 0) {
-        if (ntiles > 0) issue(0);
-        if (ntiles > 1) issue(1);
-    }
-    float xi[AD_R], yi[AD_R], zi[AD_R];
-    float acc[AD_R][6];
-#pragma unroll
-    for (int r = 0; r < AD_R; ++r) {
-        const float4 p = x4[row0 + r];
-        xi[r] = p.x;
-        yi[r] = p.y;
-        zi[r] = p.z;
-#pragma unroll
-        for (int a = 0; a < 6; ++a) acc[r][a] = 0.f;
-    }
-    bool timed_out = false;
-    for (int t = 0; t < ntiles; ++t) {
-        const int buf = t & 1;
-        const bool ok = mbar_wait_bounded(&sm.bar[buf], (uint32_t)((t >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            timed_out = true;
-            break;
-        }
-        if (tid == 0 && t >= 1 && t + 1 < ntiles) issue(t + 1);
-#pragma unroll 2
-        for (int jj = lane; jj < AD_TJ; jj += 32) {
-            const float4 xj = sm.xs[buf][jj];
-            const float2 p = sm.vg[buf][jj];  // (nu_j, g_j)
-#pragma unroll
-            for (int r = 0; r < AD_R; ++r) {
-                const float dx = xi[r] - xj.x, dy = yi[r] - xj.y, dz = zi[r] - xj.z;
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const float e1 = ex2_sfu(r2 * c1), e2 = ex2_sfu(r2 * c2);
-                const float e1g = e1 * p.y, e2g = e2 * p.y;
-                acc[r][0] = fmaf(e1, p.x, acc[r][0]);
-                acc[r][1] = fmaf(e2, p.x, acc[r][1]);
-                acc[r][2] += e1g;
-                acc[r][3] = fmaf(r2, e1g, acc[r][3]);
-                acc[r][4] += e2g;
-                acc[r][5] = fmaf(r2, e2g, acc[r][5]);
-            }
-        }
-    }
-    if (timed_out) {
-        if (tid == 0) {
-            set_dev_error(err, DEV_TIMEOUT);
-            for (int bb = 0; bb < 2; ++bb) (void)mbar_wait_bounded(&sm.bar[bb], 0), (void)mbar_wait_bounded(&sm.bar[bb], 1);
-        }
-        return;
-    }
-    const int64_t plane = (int64_t)nsplit * B * n_pad;
-#pragma unroll
-    for (int r = 0; r < AD_R; ++r)
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            const float v = warp_sum(acc[r][a]);
-            if (lane == 0) partial[a * plane + ((int64_t)split * B + b) * n_pad + row0 + r] = v;
-        }
-}
 
 __device__ __forceinline__ float sigmoid_rate(float u, float beta, float theta) {
     return 1.0f / (1.0f + expf(-beta * (u - theta)));
@@ -134,8 +36,8 @@ __global__ void adj_prep_kernel(const float *__restrict__ lam, const float *__re
 }
 
 struct AdjEpiArgs {
-    const float *partial;
-    int splits;
+    const float *wpart;      // [slots][B][n_pad]: partial sums of W nu
+    int slots;
     int64_t n, n_pad;
     int B;
     int stg;                 // 0..3 (stage s = stg + 1)
@@ -143,9 +45,7 @@ struct AdjEpiArgs {
     const float *Uprev;      // U_{s-1} (stg > 0), U_4 of the previous step (stg == 0), or null
     float *lam, *acc;
     float2 *vg;
-    float *contrib;          // [B][4][n]
     const float *q, *beta, *theta;
-    float A1, A2, dA1c, dA2c;  // dA1c = 2 A1 / s1^3, dA2c = 2 A2 / s2^3
     float dt;
 };
 
@@ -154,25 +54,14 @@ __global__ void adj_epilogue_kernel(AdjEpiArgs a) {
     if (idx >= (int64_t)a.B * a.n) return;
     const int b = (int)(idx / a.n);
     const int64_t i = idx - (int64_t)b * a.n;
-    const int64_t plane = (int64_t)a.splits * a.B * a.n_pad;
-    float s6[6] = {0, 0, 0, 0, 0, 0};
-    for (int sp = 0; sp < a.splits; ++sp) {
-        const int64_t off = ((int64_t)sp * a.B + b) * a.n_pad + i;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) s6[k] += a.partial[k * plane + off];
-    }
+    float Wnu = 0.f;
+    for (int sp = 0; sp < a.slots; ++sp) Wnu += a.wpart[((int64_t)sp * a.B + b) * a.n_pad + i];
     const int64_t vi = (int64_t)b * a.n_pad + i;
     const float nu = a.vg[vi].x;
     const float bb = a.beta[b], th = a.theta[b];
     const float f = sigmoid_rate(a.Ucur[idx], bb, th);
     const float fp = a.q[i] * bb * f * (1.f - f);
-    const float Wnu = a.A1 * s6[0] - a.A2 * s6[1];
     const float mu = -nu + fp * Wnu;
-    float* cb = a.contrib + ((int64_t)b * 4) * a.n + i;
-    cb[0] = nu * s6[2];
-    cb[a.n] = nu * a.dA1c * s6[3];
-    cb[2 * a.n] = -nu * s6[4];
-    cb[3 * a.n] = -nu * a.dA2c * s6[5];
     const float bw[4] = {1.f / 6.f, 2.f / 6.f, 2.f / 6.f, 1.f / 6.f};
     const float cprev[4] = {0.f, 0.5f, 0.5f, 1.f};
     if (a.stg > 0) {
@@ -188,33 +77,31 @@ __global__ void adj_epilogue_kernel(AdjEpiArgs a) {
     }
 }
 
-// gk[b][k] += sum_i contrib[b][k][i], one block per (b, k), fixed order
-__global__ void adj_reduce_kernel(const float *__restrict__ contrib, int64_t n, double *__restrict__ gk) {
+// gk[b][k] += scale[k] * sum_c gpart[b][c][k] over the CTAs c of the stage's pair launch,
+// one block per (b, k), fixed order.  scale = (1, 2 A1 / s1^3 * r2phys, -1, -2 A2 / s2^3 *
+// r2phys): d w / dA1 = e1, d w / ds1 = 2 A1 r^2 e1 / s1^3, d w / dA2 = -e2,
+// d w / ds2 = -2 A2 r^2 e2 / s2^3, with r^2 converted from exponent units.
+struct AdjScale {
+    double k[4];
+};
+__global__ void adj_reduce_kernel(const float *__restrict__ gpart, int64_t ncta, AdjScale sc, double *__restrict__ gk) {
     __shared__ double red[256];
-    const int64_t bk = blockIdx.x;
-    const float *c = contrib + bk * n;
+    const int b = blockIdx.x >> 2, k = blockIdx.x & 3;
+    const float *c = gpart + (int64_t)b * ncta * 4 + k;
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)c[i];
+    for (int64_t i = threadIdx.x; i < ncta; i += blockDim.x) s += (double)c[i * 4];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
         if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gk[bk] += red[0];
+    if (threadIdx.x == 0) gk[blockIdx.x] += sc.k[k] * red[0];
 }
 
 __global__ void adj_finish_kernel(const double *__restrict__ gk, int cnt, float *__restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < cnt) out[t] = (float)gk[t];
-}
-
-SplitPlan mf_plan(nf_operator *op);
-
-static SplitPlan adj_plan(nf_operator *op) {
-    int res = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, adj_pair_kernel, AD_THREADS, 0);
-    return plan_splits(op->n_pad, AD_WARPS * AD_R, AD_TJ, std::max(res, 1));
 }
 
 }  // namespace nfi
@@ -236,17 +123,18 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     const int64_t n = op->n, n_pad = op->n_pad;
     const size_t BN = (size_t)B * n;
     NF_TRY(ensure_workspace(op, B, mf_splits(op, B)));
-    const SplitPlan apl = adj_plan(op);
+    const int slots = mf_splits(op, 1);  // one W nu slot per node block
+    const int64_t ncta = sym_pair_count(op);
     const int Cseg = std::min(C, std::max(nsteps, 1));
-    float *stages = nullptr, *lam = nullptr, *acc = nullptr, *ubuf = nullptr, *part6 = nullptr, *contrib = nullptr;
+    float *stages = nullptr, *lam = nullptr, *acc = nullptr, *ubuf = nullptr, *wpart = nullptr, *gpart = nullptr;
     float2 *vg = nullptr;
     double *gk = nullptr;
     NF_CUDA_TRY(cudaMallocAsync(&stages, sizeof(float) * BN * 4 * Cseg, s));
     NF_CUDA_TRY(cudaMallocAsync(&lam, sizeof(float) * BN, s));
     NF_CUDA_TRY(cudaMallocAsync(&acc, sizeof(float) * BN, s));
     NF_CUDA_TRY(cudaMallocAsync(&ubuf, sizeof(float) * BN, s));
-    NF_CUDA_TRY(cudaMallocAsync(&part6, sizeof(float) * 6 * apl.splits * (size_t)B * n_pad, s));
-    NF_CUDA_TRY(cudaMallocAsync(&contrib, sizeof(float) * 4 * BN, s));
+    NF_CUDA_TRY(cudaMallocAsync(&wpart, sizeof(float) * (size_t)slots * B * n_pad, s));
+    NF_CUDA_TRY(cudaMallocAsync(&gpart, sizeof(float) * 4 * (size_t)B * ncta, s));
     NF_CUDA_TRY(cudaMallocAsync(&vg, sizeof(float2) * (size_t)B * n_pad, s));
     NF_CUDA_TRY(cudaMallocAsync(&gk, sizeof(double) * 4 * B, s));
     NF_CUDA_TRY(cudaMemsetAsync(vg, 0, sizeof(float2) * (size_t)B * n_pad, s));  // padded columns stay zero
@@ -255,8 +143,6 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     static const nf_forcing none{NF_FORCE_NONE, nullptr, nullptr, 0, 0, 0, 0, 0};
     const nf_forcing F = g ? *g : none;
     const nf_kernel &kp = op->kp;
-    const float L2E = 1.4426950408889634f;
-    const float c1 = -L2E / (kp.s1 * kp.s1), c2 = -L2E / (kp.s2 * kp.s2);
     const int T = 256;
     const unsigned eg = (unsigned)ceil_div((int64_t)BN, T);
     const int nseg = (nsteps + C - 1) / C;
@@ -296,13 +182,11 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
         NF_CUDA_TRY(cudaGetLastError());
         for (int j = cnt - 1; j >= 0; --j) {
             for (int stg = 3; stg >= 0; --stg) {
-                dim3 grid((unsigned)apl.row_blocks, (unsigned)apl.splits);
-                for (int b = 0; b < B; ++b)
-                    adj_pair_kernel<<<grid, AD_THREADS, 0, s>>>(op->x4, vg, n_pad, B, b, apl.jchunk, c1, c2, part6,
-                                                                op->err);
+                float r2phys = 1.f;
+                for (int b = 0; b < B; ++b) NF_TRY(launch_adj_sym(op, vg, B, b, wpart, gpart, &r2phys, s));
                 AdjEpiArgs ea{};
-                ea.partial = part6;
-                ea.splits = apl.splits;
+                ea.wpart = wpart;
+                ea.slots = slots;
                 ea.n = n;
                 ea.n_pad = n_pad;
                 ea.B = B;
@@ -313,17 +197,14 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
                 ea.lam = lam;
                 ea.acc = acc;
                 ea.vg = vg;
-                ea.contrib = contrib;
                 ea.q = op->q;
                 ea.beta = beta;
                 ea.theta = theta;
-                ea.A1 = kp.A1;
-                ea.A2 = kp.A2;
-                ea.dA1c = 2.f * kp.A1 / (kp.s1 * kp.s1 * kp.s1);
-                ea.dA2c = 2.f * kp.A2 / (kp.s2 * kp.s2 * kp.s2);
                 ea.dt = (float)dt;
+                AdjScale sc{{1.0, 2.0 * kp.A1 / ((double)kp.s1 * kp.s1 * kp.s1) * r2phys, -1.0,
+                             -2.0 * kp.A2 / ((double)kp.s2 * kp.s2 * kp.s2) * r2phys}};
+                adj_reduce_kernel<<<(unsigned)(4 * B), 256, 0, s>>>(gpart, ncta, sc, gk);
                 adj_epilogue_kernel<<<eg, T, 0, s>>>(ea);
-                adj_reduce_kernel<<<(unsigned)(4 * B), 256, 0, s>>>(contrib, n, gk);
                 NF_CUDA_TRY(cudaGetLastError());
             }
         }
@@ -335,8 +216,8 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     cudaFreeAsync(lam, s);
     cudaFreeAsync(acc, s);
     cudaFreeAsync(ubuf, s);
-    cudaFreeAsync(part6, s);
-    cudaFreeAsync(contrib, s);
+    cudaFreeAsync(wpart, s);
+    cudaFreeAsync(gpart, s);
     cudaFreeAsync(vg, s);
     cudaFreeAsync(gk, s);
     return st;

@@ -210,6 +210,9 @@ nf_status mf_init_attrs();
 nf_status mf_build_row_order(nf_operator *op, cudaStream_t s);
 SplitPlan mf_plan(nf_operator *op);     // column splits of the multi-trajectory matrix-free launches
 int mf_splits(nf_operator *op, int B);  // partial-sum slots of a matrix-free launch over B trajectories
+int64_t sym_pair_count(const nf_operator *op);  // block pairs of the symmetric kernels
+nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
+                         float *r2_phys, cudaStream_t s);
 nf_status mf_autotune(nf_operator *op, cudaStream_t s);
 void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits);
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out);

@@ -660,6 +660,242 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
 }
 
 // ----------------------------------------------------------------------------
+// Symmetric adjoint pair kernel (one trajectory b).  W is symmetric, so each unordered
+// pair of nodes is evaluated once, as in the forward symmetric kernel: one CTA per pair of
+// 1024-node Morton blocks (I <= J), rows of block I swept R at a time against block J in
+// shared memory, expanded about the pass's centre when its rows are close.  Per pair it
+//   * adds e1, e2 times nu to the row sums (W nu)_i and, per warp in shared memory, to the
+//     column sums (W nu)_j: row sums go to slot J, column sums to slot I of wpart, the
+//     stage epilogue adds the slots in a fixed order;
+//   * adds the pair's share of the kernel-parameter sums
+//         P1 = sum nu_i g_j e1, Q1 = sum nu_i g_j r^2 e1, P2 = sum nu_i g_j e2, Q2 = ... r^2 e2
+//     over ordered pairs: off the diagonal an unordered pair carries the weight
+//     nu_i g_j + nu_j g_i, on a diagonal block pair every ordered pair is swept with
+//     nu_i g_j.  Each CTA writes its four sums (r^2 in exponent units: of s2 when M > 0,
+//     else of s1) to gpart; a fixed-order FP64 reduction adds them.
+constexpr size_t AS_SMEM_FLOATS = (size_t)(5 + 14 + 1 + MS_WARPS) * MS_BLK;
+
+template <int R, int M>
+__global__ void __launch_bounds__(MS_THREADS, 2)
+adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all, const int *__restrict__ rowperm,
+               int64_t n_pad, int B, int b, float k2, float A1, float A2, float *__restrict__ wpart,
+               float *__restrict__ gpart) {
+    static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
+    static_assert(R == 2 || R == 4, "rows per warp");
+    constexpr int NPASS = MS_BLK / R;
+    extern __shared__ __align__(16) float as_smem[];
+    // column block: x, y, z, nu, g (floats), node (int)
+    float *xs = as_smem, *ys = xs + MS_BLK, *zs = ys + MS_BLK, *vs = zs + MS_BLK, *gsm = vs + MS_BLK;
+    int *cnode = reinterpret_cast<int *>(gsm + MS_BLK);
+    // row block: node; per row (mx, my, mz, n_i), (h1, h2, rf1, rf2), (v1, u1, v2, u2) as float4
+    int *rnode = cnode + MS_BLK;
+    float4 *rgeo = reinterpret_cast<float4 *>(rnode + MS_BLK);
+    float4 *rwn = rgeo + MS_BLK, *rgw = rwn + MS_BLK;
+    float4 *pc = rgw + MS_BLK;                               // per pass: centre, form
+    float *colacc = reinterpret_cast<float *>(pc + MS_BLK / 4);  // [MS_WARPS][MS_BLK]
+    __shared__ float gred[MS_WARPS][4];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int I, J;
+    sym_pair(blockIdx.x, I, J);
+    const bool diag = I == J;
+    const float2 *vg = vg_all + (int64_t)b * n_pad;
+    const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
+    const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
+    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+        const int node = __ldg(rowperm + cbase + k);
+        cnode[k] = node;
+        xs[k] = X[node];
+        ys[k] = Y[node];
+        zs[k] = Z[node];
+        const float2 p = vg[node];
+        vs[k] = p.x;
+        gsm[k] = p.y;
+        const int rn = diag ? node : __ldg(rowperm + rbase + k);
+        rnode[k] = rn;
+        const float2 pr = diag ? p : vg[rn];
+        rgeo[k] = make_float4(X[rn], Y[rn], Z[rn], 0.f);
+        rgw[k] = make_float4(pr.x, pr.y, 0.f, 0.f);
+    }
+    for (int k = tid; k < MS_WARPS * MS_BLK; k += MS_THREADS) colacc[k] = 0.f;
+    __syncthreads();
+    const float sk = M > 0 ? sqrtf(k2) : 1.f;
+    // one thread per pass: centre, form and the rows' operands (see mf_sym_kernel)
+    for (int ps = tid; ps < NPASS; ps += MS_THREADS) {
+        const int r0 = ps * R;
+        float lox = 3.4e38f, loy = 3.4e38f, loz = 3.4e38f, hix = -3.4e38f, hiy = -3.4e38f, hiz = -3.4e38f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 p = rgeo[r0 + r];
+            lox = fminf(lox, p.x), hix = fmaxf(hix, p.x);
+            loy = fminf(loy, p.y), hiy = fmaxf(hiy, p.y);
+            loz = fminf(loz, p.z), hiz = fmaxf(hiz, p.z);
+        }
+        const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy), cz = 0.5f * (loz + hiz);
+        float spread = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 p = rgeo[r0 + r];
+            const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
+            spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
+        }
+        const bool local = spread <= kMfLocalSpread;
+        pc[ps] = make_float4(cx, cy, cz, local ? 1.f : 0.f);
+        const float lsc = -2.f * sk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = r0 + r;
+            const float4 p = rgeo[k];
+            const float x = local ? lsc * (p.x - cx) : p.x;
+            const float y = local ? lsc * (p.y - cy) : p.y;
+            const float z = local ? lsc * (p.z - cz) : p.z;
+            const float ni = local ? 0.25f * (x * x + y * y + z * z) : 0.f;  // exponent units
+            const float f1 = local ? exp2f(M > 0 ? -(float)M * ni : -ni) : 1.f;
+            const float f2 = local ? exp2f(M > 0 ? -ni : -k2 * ni) : 1.f;
+            const float nu = rgw[k].x, gi = rgw[k].y;
+            rgeo[k] = make_float4(x, y, z, ni);
+            rwn[k] = make_float4(A1 * f1 * nu, -A2 * f2 * nu, A1 * f1, -A2 * f2);
+            rgw[k] = make_float4(f1 * nu, diag ? 0.f : f1 * gi, f2 * nu, diag ? 0.f : f2 * gi);
+        }
+    }
+    __syncthreads();
+    const u64 nk2 = f2_pack(-k2, -k2), skp = f2_pack(sk, sk), k2p = f2_pack(k2, k2);
+    const u64 *xs2 = reinterpret_cast<const u64 *>(xs), *ys2 = reinterpret_cast<const u64 *>(ys);
+    const u64 *zs2 = reinterpret_cast<const u64 *>(zs), *vs2 = reinterpret_cast<const u64 *>(vs);
+    const u64 *gs2 = reinterpret_cast<const u64 *>(gsm);
+    u64 *cw2 = reinterpret_cast<u64 *>(colacc + warp * MS_BLK);
+    float *out_rows = wpart + ((int64_t)J * B + b) * n_pad;
+    auto exps = [&](u64 arg, u64 &e1, u64 &e2) {
+        float s0, s1v;
+        f2_unpack(arg, s0, s1v);
+        if constexpr (M > 0) {
+            e2 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+            const u64 sq = f2_mul(e2, e2);
+            e1 = M == 2 ? sq : (M == 3 ? f2_mul(sq, e2) : f2_mul(sq, sq));
+        } else {
+            e1 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+            e2 = f2_ex2(f2_mul(arg, nk2));
+        }
+    };
+    u64 P1 = 0ull, Q1 = 0ull, P2 = 0ull, Q2 = 0ull;  // per lane, over all its pairs
+    for (int ps = warp; ps < NPASS; ps += MS_WARPS) {
+        const int r0 = ps * R;
+        const float4 c = pc[ps];
+        const bool local = c.w != 0.f;
+        u64 xi[R], yi[R], zi[R], nir[R], h1[R], h2[R], v1[R], u1[R], v2[R], u2[R], a1[R], a2[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 p = rgeo[r0 + r], w = rwn[r0 + r], q = rgw[r0 + r];
+            xi[r] = f2_pack(p.x, p.x);
+            yi[r] = f2_pack(p.y, p.y);
+            zi[r] = f2_pack(p.z, p.z);
+            nir[r] = f2_pack(p.w, p.w);
+            h1[r] = f2_pack(w.x, w.x);
+            h2[r] = f2_pack(w.y, w.y);
+            v1[r] = f2_pack(q.x, q.x);
+            u1[r] = f2_pack(q.y, q.y);
+            v2[r] = f2_pack(q.z, q.z);
+            u2[r] = f2_pack(q.w, q.w);
+            a1[r] = 0ull;
+            a2[r] = 0ull;
+        }
+        const u64 cxp = f2_pack(c.x, c.x), cyp = f2_pack(c.y, c.y), czp = f2_pack(c.z, c.z);
+        // per (row, column pair): e1, e2 from the exponent argument arg (r^2 - n_i in the
+        // expanded form, r^2 otherwise), then the W nu and parameter-sum updates
+        auto pair = [&](int r, u64 arg, u64 vj, u64 gj, u64 &cacc) {
+            u64 e1, e2;
+            exps(arg, e1, e2);
+            a1[r] = f2_fma(e1, vj, a1[r]);
+            a2[r] = f2_fma(e2, vj, a2[r]);
+            cacc = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc));
+            const u64 r2 = f2_add(arg, nir[r]);
+            const u64 t1 = f2_mul(e1, f2_fma(v1[r], gj, f2_mul(u1[r], vj)));
+            const u64 t2 = f2_mul(e2, f2_fma(v2[r], gj, f2_mul(u2[r], vj)));
+            P1 = f2_add(P1, t1);
+            Q1 = f2_fma(r2, t1, Q1);
+            P2 = f2_add(P2, t2);
+            Q2 = f2_fma(r2, t2, Q2);
+        };
+        if (local) {
+#pragma unroll 2
+            for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
+                u64 xt = f2_sub(xs2[jp], cxp), yt = f2_sub(ys2[jp], cyp), zt = f2_sub(zs2[jp], czp);
+                if constexpr (M > 0) {
+                    xt = f2_mul(xt, skp);
+                    yt = f2_mul(yt, skp);
+                    zt = f2_mul(zt, skp);
+                }
+                const u64 nj = f2_fma(zt, zt, f2_fma(yt, yt, f2_mul(xt, xt)));
+                const u64 vj = vs2[jp], gj = gs2[jp];
+                u64 cacc = 0ull;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    pair(r, f2_fma(xi[r], xt, f2_fma(yi[r], yt, f2_fma(zi[r], zt, nj))), vj, gj, cacc);
+                if (!diag) cw2[jp] = f2_add(cw2[jp], cacc);
+            }
+        } else {
+#pragma unroll 2
+            for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
+                const u64 xj = xs2[jp], yj = ys2[jp], zj = zs2[jp], vj = vs2[jp], gj = gs2[jp];
+                u64 cacc = 0ull;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj), dz = f2_sub(zi[r], zj);
+                    u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                    if constexpr (M > 0) r2s = f2_mul(r2s, k2p);  // in units of s2
+                    pair(r, r2s, vj, gj, cacc);
+                }
+                if (!diag) cw2[jp] = f2_add(cw2[jp], cacc);
+            }
+        }
+        float v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float p0, p1, q0, q1;
+            f2_unpack(a1[r], p0, p1);
+            f2_unpack(a2[r], q0, q1);
+            const float4 w = rwn[r0 + r];
+            v[r] = w.z * (p0 + p1) + w.w * (q0 + q1);
+        }
+        int row;
+        const float tot = warp_reduce_rows<R>(v, lane, row);
+        if ((lane & (32 / R - 1)) == 0) out_rows[rnode[r0 + row]] = tot;
+    }
+    // the CTA's parameter sums: lanes, then warps, in a fixed order
+    float gs4[4];
+    {
+        float a, bq;
+        f2_unpack(P1, a, bq);
+        gs4[0] = a + bq;
+        f2_unpack(Q1, a, bq);
+        gs4[1] = a + bq;
+        f2_unpack(P2, a, bq);
+        gs4[2] = a + bq;
+        f2_unpack(Q2, a, bq);
+        gs4[3] = a + bq;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gs4[k] = warp_sum(gs4[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gred[warp][k] = gs4[k];
+    __syncthreads();
+    if (tid < 4) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < MS_WARPS; ++w) s += gred[w][tid];
+        gpart[((int64_t)b * gridDim.x + blockIdx.x) * 4 + tid] = s;
+    }
+    if (diag) return;
+    float *out_cols = wpart + ((int64_t)I * B + b) * n_pad;
+    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < MS_WARPS; ++w) s += colacc[w * MS_BLK + k];
+        out_cols[cnode[k]] = s;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // split planner: (row blocks x column splits) items of equal cost; pick the number
 // of splits that best fills whole waves of resident blocks.
 SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm) {
@@ -703,7 +939,17 @@ static cudaError_t set_sym_attr() {
     return cudaFuncSetAttribute(mf_sym_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MS_SMEM);
 }
 
+template <int R, int M>
+static cudaError_t set_adj_attr() {
+    return cudaFuncSetAttribute(adj_sym_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(AS_SMEM_FLOATS * sizeof(float)));
+}
+
 nf_status mf_init_attrs() {
+    NF_CUDA_TRY((set_adj_attr<4, 0>()));
+    NF_CUDA_TRY((set_adj_attr<4, 2>()));
+    NF_CUDA_TRY((set_adj_attr<4, 3>()));
+    NF_CUDA_TRY((set_adj_attr<4, 4>()));
     NF_CUDA_TRY((set_sym_attr<4, 0>()));
     NF_CUDA_TRY((set_sym_attr<4, 2>()));
     NF_CUDA_TRY((set_sym_attr<4, 3>()));
@@ -835,6 +1081,32 @@ static nf_status launch_sym(nf_operator *op, int B, int b_base, cudaStream_t s) 
         launch_sym_r<4>(op, B, b_base, s);
     else
         launch_sym_r<8>(op, B, b_base, s);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+// Adjoint pair sums of trajectory b over all block pairs (see adj_sym_kernel): W nu slots
+// into wpart [n_pad / MS_BLK][B][n_pad], parameter sums into gpart [B][pairs][4] with r^2 in
+// exponent units; *r2_phys receives the factor to physical r^2.
+int64_t sym_pair_count(const nf_operator *op) { return sym_pairs(op); }
+
+nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
+                         float *r2_phys, cudaStream_t s) {
+    const nf_kernel &k = op->kp;
+    const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
+    const int m = mf_width_ratio(k);
+    const double L2E = 1.4426950408889634;
+    *r2_phys = (float)((m > 0 ? (double)k.s2 * k.s2 : (double)k.s1 * k.s1) / L2E);
+    dim3 grid((unsigned)sym_pairs(op), 1, 1);
+    const size_t smem = AS_SMEM_FLOATS * sizeof(float);
+#define NF_ADJ_ARGS op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, wpart, gpart
+    switch (m) {
+        case 2: adj_sym_kernel<4, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+        case 3: adj_sym_kernel<4, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+        case 4: adj_sym_kernel<4, 4><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+        default: adj_sym_kernel<4, 0><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+    }
+#undef NF_ADJ_ARGS
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
 }

@@ -27,14 +27,18 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
 
 
-@pytest.mark.parametrize("n,B,nsteps,C", [(900, 1, 12, 5), (1500, 2, 10, 10), (2100, 1, 7, 3)])
-def test_adjoint_matches_oracle(nf, n, B, nsteps, C):
+M4 = (1.0, 0.1, 0.5, 0.2)          # s2 = 2 s1: e1 = e2^4 inside the kernels
+GENERAL = (1.2, 0.08, 0.6, 0.25)   # non-integer width ratio: two exponentials per pair
+
+
+@pytest.mark.parametrize("n,B,nsteps,C,kern", [(900, 1, 12, 5, M4), (1500, 2, 10, 10, M4), (2100, 1, 7, 3, M4),
+                                               (1300, 1, 6, 3, GENERAL)])
+def test_adjoint_matches_oracle(nf, n, B, nsteps, C, kern):
     ns = nodesets.torus_lattice(n if n % 2 == 0 else n + 1, seed=n)
     n = ns.n
     X = ns.nodes.astype(np.float32)
     q = np.full(n, ns.area / n, dtype=np.float32)
     u0 = np.stack([nodesets.spiral_bumps_u0(ns, count=3 + b) for b in range(B)]).astype(np.float32)
-    kern = (1.0, 0.1, 0.5, 0.2)
     beta = np.array([20.0, 12.0][:B], dtype=np.float32)
     theta = np.array([0.2, 0.25][:B], dtype=np.float32)
     dt = 0.02

@@ -161,6 +161,25 @@ def test_nonlocal_apply_row_order_forms(nf, s1):
     assert np.abs(got - want).max() / np.abs(want).max() < REL_L2
 
 
+@pytest.mark.parametrize("ratio,n", [(2.0, 2048), (2 ** 0.5, 1024), (3 ** 0.5, 1025), (1.7, 3073), (2.0, 1023)])
+def test_nonlocal_apply_width_ratios_and_blocks(nf, ratio, n):
+    """One trajectory: the symmetric kernel's forms for s2^2 / s1^2 = 4, 2, 3 (e1 = e2^m
+    by squaring) and a non-integer ratio (two exponentials), on node counts at and just
+    past the 1024-node block boundaries (one block, a ragged second block, exact blocks)."""
+    rng = np.random.default_rng(int(ratio * 1000) + n)
+    X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
+    u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
+    s1 = 0.15
+    kern = (1.0, s1, 0.5, float(np.float32(s1) * np.float32(ratio)))
+    op = _op(nf, X, q, kern, 0)
+    got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), 20.0, 0.2).cpu().numpy()
+    op.check()
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
+    assert rel_l2(got, want) < REL_L2
+    assert np.abs(got - want).max() / np.abs(want).max() < REL_L2
+
+
 def test_nonlocal_apply_paper_kernel_torus_sampled_full_size(nf):
     """Full precision-workload size (n = 100,000 torus nodes), the launch
     configuration the benchmark times; the oracle evaluates 384 sampled rows."""
