@@ -141,16 +141,16 @@ def peaks():
 # lane operations per ordered pair of the symmetric matrix-free kernel in its expanded form
 # with s2^2 / s1^2 = 4 (the workload's kernel): per unordered pair 3 FMA (exponent) +
 # 2 MUL (e1 = e2^4) + 2 FMA (row sums) + 2 FMA (column sums), plus per column and 8-row
-# pass 3 SUB + 3 MUL + 3 FMA (centred, rescaled column and n_j) and 1 ADD (column sums
-# into shared memory): 10.25 per unordered pair, 5.125 per ordered pair.  Diagonal block
-# pairs evaluate their ordered pairs one by one, a 1/nb share of the work.
+# pass 3 SUB + 3 FMA (centred column and n_j) and 1 ADD (column sums into shared memory):
+# 9.875 per unordered pair, 4.9375 per ordered pair.  Diagonal block pairs evaluate their
+# ordered pairs one by one, a 1/nb share of the work.
 FMA_LANES_PER_CLK_SM = 128.0
-LANE_OPS_PER_PAIR = 10.25 / 2.0
+LANE_OPS_PER_PAIR = 9.875 / 2.0
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels:
 # mf_sym_kernel<8, 4> on the n = 100,000 torus; tc_grouped_kernel on the batched workload at
 # half node counts, scaled to full size by the W bytes a launch streams (4x)
-MF_TRAFFIC_BYTES = 2.16e6 + 0.24e6
+MF_TRAFFIC_BYTES = 2.162e6 + 0.243e6
 TC_TRAFFIC_BYTES = (2.956e9 + 0.104e9) * 4.0
 
 

@@ -469,26 +469,28 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     const float *g = g_all + (int64_t)b * n_pad;
     const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
     const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
+    // exponent units: s1 (coordinates as stored), or s2 when M > 0 (times sk = s1 / s2,
+    // applied once here, so r^2 and s_ij arrive as the exponent of e2)
+    const float sk = M > 0 ? sqrtf(k2) : 1.f;
     // gather the column block, and the row block's raw data (x, y, z, g in mx, my, mz, h1)
     for (int k = tid; k < MS_BLK; k += MS_THREADS) {
         const int node = __ldg(rowperm + cbase + k);
         cnode[k] = node;
-        xs[k] = X[node];
-        ys[k] = Y[node];
-        zs[k] = Z[node];
+        xs[k] = X[node] * sk;
+        ys[k] = Y[node] * sk;
+        zs[k] = Z[node] * sk;
         gs[k] = g[node];
         const int rn = diag ? node : __ldg(rowperm + rbase + k);
         rnode[k] = rn;
-        rmx[k] = X[rn];
-        rmy[k] = Y[rn];
-        rmz[k] = Z[rn];
+        rmx[k] = X[rn] * sk;
+        rmy[k] = Y[rn] * sk;
+        rmz[k] = Z[rn] * sk;
         rh1[k] = g[rn];
     }
     for (int k = tid; k < MS_WARPS * MS_BLK; k += MS_THREADS) colacc[k] = 0.f;
     __syncthreads();
-    const float sk = M > 0 ? sqrtf(k2) : 1.f;
     // one thread per pass: centre of the pass's R rows, the form, and the row operands:
-    // expanded form -2 (x_i - c) (times s1/s2 when M > 0), else x_i; f1, f2 the row factors
+    // expanded form -2 (x_i - c), else x_i; f1, f2 the row factors
     // 2^(-n_i) of e1 and e2 (1 in the difference form); h1 = A1 f1 g_i and h2 = -A2 f2 g_i
     // weight the row's terms in the column sums
     for (int ps = tid; ps < NPASS; ps += MS_THREADS) {
@@ -507,9 +509,9 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
             const float dx = rmx[r0 + r] - cx, dy = rmy[r0 + r] - cy, dz = rmz[r0 + r] - cz;
             spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
         }
-        const bool local = spread <= kMfLocalSpread;
+        const bool local = spread <= kMfLocalSpread * sk * sk;  // the threshold in units of s1
         pc[ps] = make_float4(cx, cy, cz, local ? 1.f : 0.f);
-        const float lsc = -2.f * sk;
+        const float lsc = -2.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int k = r0 + r;
@@ -530,7 +532,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         }
     }
     __syncthreads();
-    const u64 nk2 = f2_pack(-k2, -k2), skp = f2_pack(sk, sk), k2p = f2_pack(k2, k2);
+    const u64 nk2 = f2_pack(-k2, -k2);
     const float4 *xs4 = reinterpret_cast<const float4 *>(xs), *ys4 = reinterpret_cast<const float4 *>(ys);
     const float4 *zs4 = reinterpret_cast<const float4 *>(zs), *gs4 = reinterpret_cast<const float4 *>(gs);
     float4 *cw4 = reinterpret_cast<float4 *>(colacc + warp * MS_BLK);
@@ -572,20 +574,13 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
 #pragma unroll 1
             for (int q = lane; q < MS_BLK / 4; q += 32) {
                 const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
-                u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
-                u64 yt[2] = {f2_sub(lo2(y4), cyp), f2_sub(hi2(y4), cyp)};
-                u64 zt[2] = {f2_sub(lo2(z4), czp), f2_sub(hi2(z4), czp)};
+                const u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
+                const u64 yt[2] = {f2_sub(lo2(y4), cyp), f2_sub(hi2(y4), cyp)};
+                const u64 zt[2] = {f2_sub(lo2(z4), czp), f2_sub(hi2(z4), czp)};
                 const u64 gj[2] = {lo2(g4), hi2(g4)};
                 u64 nj[2], cacc[2] = {0ull, 0ull};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if constexpr (M > 0) {
-                        xt[h] = f2_mul(xt[h], skp);
-                        yt[h] = f2_mul(yt[h], skp);
-                        zt[h] = f2_mul(zt[h], skp);
-                    }
-                    nj[h] = f2_fma(zt[h], zt[h], f2_fma(yt[h], yt[h], f2_mul(xt[h], xt[h])));
-                }
+                for (int h = 0; h < 2; ++h) nj[h] = f2_fma(zt[h], zt[h], f2_fma(yt[h], yt[h], f2_mul(xt[h], xt[h])));
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
 #pragma unroll
@@ -618,8 +613,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const u64 dx = f2_sub(xi[r], xj[h]), dy = f2_sub(yi[r], yj[h]), dz = f2_sub(zi[r], zj[h]);
-                        u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
-                        if constexpr (M > 0) r2s = f2_mul(r2s, k2p);  // in units of s2
+                        const u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
                         u64 e1, e2;
                         exps(r2s, e1, e2);
                         a1[r] = f2_fma(e1, gj[h], a1[r]);
@@ -701,24 +695,25 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     const float2 *vg = vg_all + (int64_t)b * n_pad;
     const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
     const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
+    // exponent units: s1, or s2 when M > 0 (coordinates times sk = s1 / s2, once here)
+    const float sk = M > 0 ? sqrtf(k2) : 1.f;
     for (int k = tid; k < MS_BLK; k += MS_THREADS) {
         const int node = __ldg(rowperm + cbase + k);
         cnode[k] = node;
-        xs[k] = X[node];
-        ys[k] = Y[node];
-        zs[k] = Z[node];
+        xs[k] = X[node] * sk;
+        ys[k] = Y[node] * sk;
+        zs[k] = Z[node] * sk;
         const float2 p = vg[node];
         vs[k] = p.x;
         gsm[k] = p.y;
         const int rn = diag ? node : __ldg(rowperm + rbase + k);
         rnode[k] = rn;
         const float2 pr = diag ? p : vg[rn];
-        rgeo[k] = make_float4(X[rn], Y[rn], Z[rn], 0.f);
+        rgeo[k] = make_float4(X[rn] * sk, Y[rn] * sk, Z[rn] * sk, 0.f);
         rgw[k] = make_float4(pr.x, pr.y, 0.f, 0.f);
     }
     for (int k = tid; k < MS_WARPS * MS_BLK; k += MS_THREADS) colacc[k] = 0.f;
     __syncthreads();
-    const float sk = M > 0 ? sqrtf(k2) : 1.f;
     // one thread per pass: centre, form and the rows' operands (see mf_sym_kernel)
     for (int ps = tid; ps < NPASS; ps += MS_THREADS) {
         const int r0 = ps * R;
@@ -738,9 +733,9 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
             spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
         }
-        const bool local = spread <= kMfLocalSpread;
+        const bool local = spread <= kMfLocalSpread * sk * sk;  // the threshold in units of s1
         pc[ps] = make_float4(cx, cy, cz, local ? 1.f : 0.f);
-        const float lsc = -2.f * sk;
+        const float lsc = -2.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int k = r0 + r;
@@ -758,7 +753,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         }
     }
     __syncthreads();
-    const u64 nk2 = f2_pack(-k2, -k2), skp = f2_pack(sk, sk), k2p = f2_pack(k2, k2);
+    const u64 nk2 = f2_pack(-k2, -k2);
     const u64 *xs2 = reinterpret_cast<const u64 *>(xs), *ys2 = reinterpret_cast<const u64 *>(ys);
     const u64 *zs2 = reinterpret_cast<const u64 *>(zs), *vs2 = reinterpret_cast<const u64 *>(vs);
     const u64 *gs2 = reinterpret_cast<const u64 *>(gsm);
@@ -818,12 +813,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         if (local) {
 #pragma unroll 2
             for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
-                u64 xt = f2_sub(xs2[jp], cxp), yt = f2_sub(ys2[jp], cyp), zt = f2_sub(zs2[jp], czp);
-                if constexpr (M > 0) {
-                    xt = f2_mul(xt, skp);
-                    yt = f2_mul(yt, skp);
-                    zt = f2_mul(zt, skp);
-                }
+                const u64 xt = f2_sub(xs2[jp], cxp), yt = f2_sub(ys2[jp], cyp), zt = f2_sub(zs2[jp], czp);
                 const u64 nj = f2_fma(zt, zt, f2_fma(yt, yt, f2_mul(xt, xt)));
                 const u64 vj = vs2[jp], gj = gs2[jp];
                 u64 cacc = 0ull;
@@ -840,9 +830,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj), dz = f2_sub(zi[r], zj);
-                    u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
-                    if constexpr (M > 0) r2s = f2_mul(r2s, k2p);  // in units of s2
-                    pair(r, r2s, vj, gj, cacc);
+                    pair(r, f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx))), vj, gj, cacc);
                 }
                 if (!diag) cw2[jp] = f2_add(cw2[jp], cacc);
             }
@@ -995,7 +983,6 @@ struct MfVariant {
     int R, TJ;
 };
 constexpr MfVariant kMfVariants[] = {{2, 512}, {4, 512}, {4, 1024}, {8, 1024}};
-constexpr int kNumMfVariants = 4;
 
 // Integer width ratio m = s2^2 / s1^2 in {2, 3, 4} (to FP32 rounding of the k2 the kernel
 // receives), else 0: selects the one-exponential form of the packed kernel.
