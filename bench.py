@@ -38,7 +38,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PATHS = {"mf": 0, "dense_fp32": 1, "bf16x2": 2}
+PATHS = {"mf": 0, "dense_fp32": 1, "bf16x2": 2, "dense_sym": 4}
 METRIC = "pair-evals/s & RK4 steps/s at N=1e5, mixed/batched vs plain FP32, same GB300"
 
 
@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--paths", default="mf,dense_fp32,bf16x2")
+    ap.add_argument("--paths", default="mf,dense_fp32,bf16x2,dense_sym")
     ap.add_argument("--n", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -192,22 +192,52 @@ def run_reference(args, rank, world):
     return line
 
 
-def cpu_baseline(wl, q, seconds):
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def cpu_baseline(wl, q32, seconds, gpu_sums):
+    """The FP64 oracle's nonlocal sum of the first stage input on the host cores, timed on
+    a bounded random row sample; its values on that sample also give each GPU path's
+    relative L2 error (gpu_sums: path -> the path's sum of the same input)."""
     import oracle
 
-    x = wl.ns.nodes.astype(np.float32).astype(np.float64)
-    u = wl.u0.astype(np.float32).astype(np.float64)
+    x = f32(wl.ns.nodes)
+    u = f32(wl.u0)
     kern = tuple(float(np.float32(v)) for v in wl.kernel)
+    beta, theta = f32(wl.beta), f32(wl.theta)
     t = time.perf_counter()
-    oracle.nonlocal_sum(x, q, u, kern, wl.beta, wl.theta, rows=np.arange(32))
+    oracle.nonlocal_sum(x, q32, u, kern, beta, theta, rows=np.arange(32))
     per_row = (time.perf_counter() - t) / 32
     rows = int(min(wl.n, max(64, seconds / per_row)))
     sel = np.random.default_rng(1).choice(wl.n, rows, replace=False)
     t = time.perf_counter()
-    oracle.nonlocal_sum(x, q, u, kern, wl.beta, wl.theta, rows=sel)
+    want = np.asarray(oracle.nonlocal_sum(x, q32, u, kern, beta, theta, rows=sel)).ravel()
     dt = time.perf_counter() - t
+    acc = {p: float(np.linalg.norm(got[sel] - want) / np.linalg.norm(want)) for p, got in gpu_sums.items()}
     return {"value": rows * wl.n / dt, "unit": "pair-evals/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one nonlocal stage on {rows} random rows x {wl.n} columns (FP64, {dt:.1f} s)"}
+            "sample": f"one nonlocal stage on {rows} random rows x {wl.n} columns (FP64, {dt:.1f} s)"}, acc
+
+
+def batched_accuracy(wls, xs, qs, u0, beta, theta, got, rows_per_group=8):
+    """Relative L2 error of the batched path's first-stage sums against the FP64 oracle on
+    a few sampled rows of every node set (all trajectories); part of the CPU-baseline leg."""
+    import oracle
+
+    rng = np.random.default_rng(2)
+    err2 = ref2 = 0.0
+    off = toff = 0
+    for wl, x, q in zip(wls, xs, qs):
+        rows = rng.choice(wl.n, rows_per_group, replace=False)
+        ub = u0[off:off + wl.B * wl.n].reshape(wl.B, wl.n)
+        want = np.asarray(oracle.nonlocal_sum(f32(x), f32(q), f32(ub), tuple(float(np.float32(v)) for v in wl.kernel),
+                                              f32(beta[toff:toff + wl.B]), f32(theta[toff:toff + wl.B]), rows=rows))
+        g = got[off:off + wl.B * wl.n].reshape(wl.B, wl.n)[:, rows]
+        err2 += float(np.sum((g - want) ** 2))
+        ref2 += float(np.sum(want ** 2))
+        off += wl.B * wl.n
+        toff += wl.B
+    return (err2 / ref2) ** 0.5
 
 
 def run_batched(args, dev, steps):
@@ -267,6 +297,7 @@ def run_batched(args, dev, steps):
     torch.cuda.synchronize(dev)
     build_ms = 1e3 * (time.perf_counter() - t0)
     grp.profile(True)
+    first_sums = nf.nf_nonlocal_apply(grp, u0.view(1, -1), beta, theta).double().cpu().numpy().ravel()
     u = u0.clone()
     sampler = ClockSampler(dev.index or 0)
     sampler.start()
@@ -288,6 +319,11 @@ def run_batched(args, dev, steps):
                      "tensor": {"achieved": tfl, "peak": tc_peak, "unit": "TFLOP/s", "frac": tfl / tc_peak,
                                 "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (kernel inside a long step)"}},
         "gpu_launches_per_step": 4}
+    if args.accuracy:
+        out["tc_bf16x3"]["rel_l2_vs_oracle"] = batched_accuracy(
+            wls, [x.cpu().numpy() for x in xs], [q.cpu().numpy() for q in qs], u0.cpu().numpy(),
+            beta.cpu().numpy(), theta.cpu().numpy(), first_sums)
+        out["tc_bf16x3"]["accuracy_sample"] = "8 random rows of each node set, all trajectories, first stage"
     grp.close()
     for op in ops:
         op.close()
@@ -377,6 +413,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    # accuracy vs the FP64 oracle is computed in the CPU-baseline leg (rank 0, one GPU)
+    args.accuracy = rank == 0 and world == 1 and not args.no_cpu_baseline
     wl = W.precision(args.n)
     n = wl.n
     # ---- setup on the GPU: stencils and quadrature weights (§3.1-3.3)
@@ -399,6 +437,7 @@ def run_ours(args, rank, world, local_rank):
     beta, theta = float(wl.beta[0]), float(wl.theta[0])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     results = {}
+    first_sums = {}
     clocks_all = []
     launches_total = 0
     for pname in [p for p in args.paths.split(",") if p]:
@@ -408,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
         op = nf.Operator(x32, q32, wl.kernel, path)
         torch.cuda.synchronize(dev)
         build_ms = 1e3 * (time.perf_counter() - tb)
+        first_sums[pname] = nf.nf_nonlocal_apply(op, u0.view(1, -1), beta, theta).double().cpu().numpy().ravel()
         op.profile(True)
         u = u0.clone()
         t_sim = 0.0
@@ -458,6 +498,11 @@ def run_ours(args, rank, world, local_rank):
                "e2e_ms_per_step": e2e_ms, "clocks": clocks}
         if path == nf.MATRIX_FREE:
             res["launch_shape"] = op.launch_shape()
+        else:  # HBM stream: stored bytes per launch / kernel time
+            nb = -(-n // 1024)
+            stored = 4.0 * (nb * (nb + 1) // 2) * 1024 * 1024 if path == nf.DENSE_SYM_FP32 else 4.0 * n * nb * 1024
+            res["hbm_gbs"] = stored / (res["kernel_ms_per_launch"] * 1e-3) / 1e9
+            res["stored_bytes"] = stored
         results[pname] = res
         op.close()
         del op
@@ -512,7 +557,11 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, q.double().cpu().numpy(), args.cpu_seconds)
+        line["cpu_baseline"], acc = cpu_baseline(wl, q32.double().cpu().numpy(), args.cpu_seconds, first_sums)
+        for p, e in acc.items():
+            line["paths"][p]["rel_l2_vs_oracle"] = e
+        line["accuracy"] = {"metric": "relative L2 error of the first-stage sum vs the FP64 oracle",
+                            "sample": line["cpu_baseline"]["sample"], **acc}
     return line if rank == 0 else None
 
 

@@ -114,7 +114,11 @@ typedef struct {
 typedef enum {
     NF_MATRIX_FREE = 0,   /* pair sum evaluated on the fly every stage (FP32) */
     NF_DENSE_FP32 = 1,    /* W diag(q) precomputed once, FP32, streamed every stage */
-    NF_DENSE_BF16X2 = 2   /* W diag(q) / s_i stored as bf16 hi + bf16 lo, FP32 accumulate */
+    NF_DENSE_BF16X2 = 2,  /* W diag(q) / s_i stored as bf16 hi + bf16 lo, FP32 accumulate */
+    NF_DENSE_SYM_FP32 = 4 /* the symmetric kernel matrix W (w is radial, §2.2) stored once as
+                             its upper-triangle 1024 x 1024 blocks, FP32; q applied on the
+                             vector side; each block serves a row and a column sum, half the
+                             bytes of NF_DENSE_FP32 per stage */
 } nf_path;
 
 typedef struct nf_operator nf_operator;

@@ -30,10 +30,10 @@ from . import _build
 __all__ = [
     "NFError", "lib", "build", "nf_build_stencils", "nf_quad_weights", "Operator", "nf_nonlocal_apply",
     "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
-    "DENSE_BF16X2", "STATUS",
+    "DENSE_BF16X2", "DENSE_SYM_FP32", "STATUS",
 ]
 
-MATRIX_FREE, DENSE_FP32, DENSE_BF16X2 = 0, 1, 2
+MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32 = 0, 1, 2, 4
 STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINITE", 4: "NF_ERR_TIMEOUT",
           5: "NF_ERR_NOMEM", 6: "NF_ERR_CUDA", 7: "NF_ERR_UNSUPPORTED"}
 

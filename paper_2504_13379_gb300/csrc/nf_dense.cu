@@ -10,6 +10,12 @@
 //                    The two planes use the blocked layout (128 x 64 blocks of 16 KB), the
 //                    tile the batched tensor-core GEMM reads with one sequential copy.
 // Apply (every stage): HBM-bound stream of 4 bytes per entry for either plane type.
+//   NF_DENSE_SYM_FP32: the kernel matrix K_ij = w(|x_i - x_j|) itself (q moves to the vector
+//                    side, g = q o f), symmetric, so only its upper-triangle 1024 x 1024
+//                    blocks are stored (n_pad^2 / 2 + n_pad * 512 entries).  One CTA streams
+//                    a block (I <= J) once and produces both its row sums (K_IJ g_J, to
+//                    partial slot J) and its column sums (K_IJ^T g_I, to slot I): half the
+//                    HBM bytes of the full matrix per stage.
 // Work items (32-row block, column split) write partial sums like the matrix-free
 // kernel, so the same stage kernel finishes the RK4 step.
 #include "nf_internal.cuh"
@@ -87,10 +93,46 @@ __global__ void dense_build_bf16x2_kernel(const float4 *__restrict__ x4, const f
     }
 }
 
+// ---- symmetric blocks: block pair t = J (J + 1) / 2 + I (I <= J) holds K over rows of node
+// block I and columns of node block J, row-major, SB x SB
+constexpr int SB = 1024;
+constexpr int SYM_THREADS = 256;
+constexpr int SYM_WARPS = SYM_THREADS / 32;
+
+__device__ __forceinline__ void sym_block_pair(int64_t t, int &I, int &J) {
+    int64_t j = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (j * (j + 1) / 2 > t) --j;
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    J = (int)j;
+    I = (int)(t - j * (j + 1) / 2);
+}
+
+// grid (pairs, SB / 16): each block writes 16 rows of one block pair
+__global__ void dense_build_sym_kernel(const float4 *__restrict__ x4, float A1, float is1, float A2, float is2,
+                                       float *__restrict__ K) {
+    int I, J;
+    sym_block_pair(blockIdx.x, I, J);
+    float *blk = K + (int64_t)blockIdx.x * SB * SB;
+    for (int rr = 0; rr < 16; ++rr) {
+        const int r = blockIdx.y * 16 + rr;
+        const float4 xi = x4[(int64_t)I * SB + r];
+        for (int c = threadIdx.x; c < SB; c += blockDim.x) {
+            const float4 xj = x4[(int64_t)J * SB + c];
+            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            blk[(int64_t)r * SB + c] = mexhat(r2, A1, is1, A2, is2);
+        }
+    }
+}
+
 nf_status launch_dense_build(nf_operator *op, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float is1 = 1.f / (k.s1 * k.s1), is2 = 1.f / (k.s2 * k.s2);
-    if (op->path == NF_DENSE_FP32) {
+    if (op->path == NF_DENSE_SYM_FP32) {
+        const int64_t nb = op->n_pad / SB;
+        dense_build_sym_kernel<<<dim3((unsigned)(nb * (nb + 1) / 2), SB / 16), 256, 0, s>>>(op->x4, k.A1, is1, k.A2,
+                                                                                       is2, op->W32);
+    } else if (op->path == NF_DENSE_FP32) {
         dense_build_fp32_kernel<<<(unsigned)op->n_pad, 256, 0, s>>>(op->x4, op->q, op->n, op->n_pad, k.A1, is1, k.A2,
                                                                is2, op->W32);
     } else {
@@ -213,6 +255,94 @@ gemv_bf16x2_kernel(const uint16_t *__restrict__ Whi, const uint16_t *__restrict_
     }
 }
 
+// One CTA per stored block pair (I <= J).  Warp w takes rows w, w + 8, ... of the block;
+// lane l covers the columns 4 l + 128 u (u = 0..7) with 16-byte streaming loads.  Row sums:
+// dot products with g_J (shared memory), 8 rows at a time reduced across the warp by a
+// transposed butterfly; column sums: per lane in registers over the warp's 128 rows,
+// then added over the warps in a fixed order.  Diagonal blocks write their row sums only.
+__global__ void __launch_bounds__(SYM_THREADS, 2)
+gemv_sym_fp32_kernel(const float *__restrict__ K, const float *__restrict__ g_all, int64_t n_pad, int B, int b,
+                     float *__restrict__ partial) {
+    __shared__ __align__(16) float gI[SB], gJ[SB];
+    __shared__ __align__(16) float colred[SYM_WARPS][SB];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int I, J;
+    sym_block_pair(blockIdx.x, I, J);
+    const bool diag = I == J;
+    const float *g = g_all + (int64_t)b * n_pad;
+    for (int k = tid; k < SB; k += SYM_THREADS) {
+        gI[k] = g[(int64_t)I * SB + k];
+        gJ[k] = g[(int64_t)J * SB + k];
+    }
+    __syncthreads();
+    const float *blk = K + (int64_t)blockIdx.x * SB * SB;
+    float col[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) col[c] = 0.f;
+    float *out_rows = partial + ((int64_t)J * B + b) * n_pad + (int64_t)I * SB;
+    for (int r0 = warp; r0 < SB; r0 += 8 * SYM_WARPS) {  // 8 rows per group: r0, r0 + 8, ..., r0 + 56
+        float dot[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = r0 + 8 * k;
+            const float *row = blk + (int64_t)r * SB;
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = ld_stream_f4(row + 4 * lane + 128 * u);
+            const float gi = gI[r];
+            float d = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 gj = *reinterpret_cast<const float4 *>(gJ + 4 * lane + 128 * u);
+                d = fmaf(v[u].x, gj.x, d);
+                d = fmaf(v[u].y, gj.y, d);
+                d = fmaf(v[u].z, gj.z, d);
+                d = fmaf(v[u].w, gj.w, d);
+                col[4 * u] = fmaf(v[u].x, gi, col[4 * u]);
+                col[4 * u + 1] = fmaf(v[u].y, gi, col[4 * u + 1]);
+                col[4 * u + 2] = fmaf(v[u].z, gi, col[4 * u + 2]);
+                col[4 * u + 3] = fmaf(v[u].w, gi, col[4 * u + 3]);
+            }
+            dot[k] = d;
+        }
+        // transposed butterfly: 7 shuffles reduce the 8 rows' dot products over the warp
+        int base = 0, cnt = 8;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            if (cnt > 1) {
+                const int h = cnt >> 1;
+                const bool upper = (lane & off) != 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k < h) {
+                        const float send = upper ? dot[k] : dot[k + h];
+                        const float keep = upper ? dot[k + h] : dot[k];
+                        dot[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                    }
+                }
+                if (upper) base += h;
+                cnt = h;
+            } else {
+                dot[0] += __shfl_xor_sync(0xffffffffu, dot[0], off);
+            }
+        }
+        if ((lane & 3) == 0) out_rows[r0 + 8 * base] = dot[0];
+    }
+    if (diag) return;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        *reinterpret_cast<float4 *>(&colred[warp][4 * lane + 128 * u]) =
+            make_float4(col[4 * u], col[4 * u + 1], col[4 * u + 2], col[4 * u + 3]);
+    __syncthreads();
+    float *out_cols = partial + ((int64_t)I * B + b) * n_pad + (int64_t)J * SB;
+    for (int k = tid; k < SB; k += SYM_THREADS) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < SYM_WARPS; ++w) v += colred[w][k];
+        out_cols[k] = v;
+    }
+}
+
 SplitPlan dense_plan(nf_operator *op) {
     int res = 0;
     if (op->path == NF_DENSE_FP32)
@@ -222,7 +352,26 @@ SplitPlan dense_plan(nf_operator *op) {
     return plan_splits(op->n_pad, DG_ROWS, DG_TILE, std::max(res, 1));
 }
 
+int dense_splits(nf_operator *op) {
+    return op->path == NF_DENSE_SYM_FP32 ? (int)(op->n_pad / SB) : dense_plan(op).splits;
+}
+
+size_t dense_sym_entries(int64_t n_pad) {
+    const int64_t nb = n_pad / SB;
+    return (size_t)(nb * (nb + 1) / 2) * SB * SB;
+}
+
 nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
+    if (op->path == NF_DENSE_SYM_FP32) {
+        const int64_t nb = op->n_pad / SB;
+        for (int b = 0; b < B; ++b) {
+            gemv_sym_fp32_kernel<<<(unsigned)(nb * (nb + 1) / 2), SYM_THREADS, 0, s>>>(op->W32, op->g, op->n_pad, B, b,
+                                                                                     op->partial);
+            NF_CUDA_TRY(cudaGetLastError());
+        }
+        *splits_out = (int)nb;
+        return NF_OK;
+    }
     const SplitPlan pl = dense_plan(op);
     dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits);
     for (int b = 0; b < B; ++b) {

@@ -219,6 +219,12 @@ nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out
 nf_status launch_mf_pair_single(const float4 *x4, const float *g, int64_t n_pad, const nf_kernel &k, int max_splits,
                                 float *partial, int *err, cudaStream_t s, int *splits_out);
 nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_out);
+int dense_splits(nf_operator *op);           // partial-sum slots of a dense launch
+size_t dense_sym_entries(int64_t n_pad);     // stored entries of the symmetric blocked matrix
+// q is applied on the vector side (g = q o f) unless it is folded into a dense operator
+inline bool q_on_vector(const nf_operator *op) {
+    return op->path == NF_MATRIX_FREE || op->path == NF_DENSE_SYM_FP32;
+}
 nf_status launch_dense_build(nf_operator *op, cudaStream_t s);
 
 // elementwise kernels

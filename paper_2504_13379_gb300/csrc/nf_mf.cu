@@ -1366,7 +1366,7 @@ nf_status launch_prep_g(nf_operator *op, const float *u, int B, const float *bet
                         bool copy_to_U, cudaStream_t s) {
     const int64_t tot = (int64_t)B * op->n;
     const int T = 256;
-    const bool mf = (op->path == NF_MATRIX_FREE);
+    const bool mf = q_on_vector(op);
     prep_g_kernel<<<(unsigned)ceil_div(tot, T), T, 0, s>>>(u, op->n, op->n_pad, B, mf ? op->q : nullptr, beta,
                                                           theta, op->g, copy_to_U ? op->U : nullptr);
     NF_CUDA_TRY(cudaGetLastError());
@@ -1502,7 +1502,7 @@ nf_status launch_stage(nf_operator *op, int B, const StageParams &p, cudaStream_
     a.U = op->U;
     a.ks = op->ks;
     a.g = op->g;
-    a.q = (op->path == NF_MATRIX_FREE) ? op->q : nullptr;
+    a.q = q_on_vector(op) ? op->q : nullptr;
     a.rs = (op->path == NF_DENSE_BF16X2) ? op->rs : nullptr;
     a.beta = p.beta;
     a.theta = p.theta;

@@ -122,8 +122,8 @@ def _op(nf, X, q, kernel, path):
     return nf.Operator(dev(X, torch.float32), dev(q, torch.float32), kernel, path)
 
 
-@pytest.mark.parametrize("path", [0, 1, 2])
-@pytest.mark.parametrize("n,B", [(3001, 1), (2500, 3), (1100, 7), (5, 2), (1, 1)])
+@pytest.mark.parametrize("path", [0, 1, 2, 4])
+@pytest.mark.parametrize("n,B", [(3001, 1), (2500, 3), (1100, 7), (5, 2), (1, 1), (2048, 2)])
 def test_nonlocal_apply_matches_oracle(nf, path, n, B):
     rng = np.random.default_rng(n + B)
     X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
@@ -190,7 +190,7 @@ def test_nonlocal_apply_paper_kernel_torus_sampled_full_size(nf):
     u = wl.u0.astype(np.float32)
     rows = np.sort(rng.choice(wl.n, 384, replace=False))
     want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(wl.kernel), f32(wl.beta), f32(wl.theta), rows=rows)
-    for path in (0, 2, 1):
+    for path in (0, 2, 1, 4):
         op = _op(nf, X, q, wl.kernel, path)
         got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), float(wl.beta[0]), float(wl.theta[0]))
         op.check()
@@ -218,7 +218,7 @@ def _rk4_pair(nf, X, q, u0, kernel, beta, theta, dt, nsteps, path, forcing=None,
     return u.cpu().numpy(), want
 
 
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 4])
 def test_rk4_flat_workload_full(nf, path):
     """The flat unit-square workload end to end: oracle stencils and weights, then
     100 RK4 steps (t = 0..5) on the GPU vs the FP64 oracle."""
