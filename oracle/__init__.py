@@ -16,6 +16,10 @@ paper passage it follows:
 * :func:`rk4`              classical RK4 on Eq. (2.9)
 * :func:`adjoint`          discrete adjoint of that RK4 map
 * :func:`mms_sphere_eigs`  Funk-Hecke eigenvalues for the manufactured solution (§4, Eq. (4.5))
+* :func:`rate`             §5 firing rates: sigmoid, C^4 smooth step (Eq. (smoothf))
+* :func:`ab5_weights`      Adams-Bashforth 5 weights from their definition
+* :func:`field_advance`    §5 models (neural field, synaptic depression, Eq. (nfsyndep)) by
+                           RK4 or AB5
 """
 from __future__ import annotations
 
@@ -62,6 +66,11 @@ def lib():
         L.or_mms_sphere_solution.argtypes = [_dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_double, _dp]
         L.or_num_threads.restype = C.c_int
+        L.or_rate.argtypes = [_dp, C.c_double, C.c_double, C.c_double]
+        L.or_rate.restype = C.c_double
+        L.or_ab5_weights.argtypes = [_dp]
+        L.or_field_advance.argtypes = [_dp, _dp, C.c_int64, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_int,
+                                       _dp, _dp, _dp, _dp, C.c_int]
         _lib = L
     return _lib
 
@@ -291,3 +300,42 @@ def mms_sphere_solution(x, t, beta, theta, c=0.5, a0=0.3):
     u = np.empty(x.shape[0])
     lib().or_mms_sphere_solution(px, x.shape[0], t, c, a0, beta, theta, u.ctypes.data_as(_dp))
     return u
+
+
+def _model_arr(kind=0, rate=0, a=0.06, b=0.54, tau=1.0, beta_d=0.0):
+    return np.array([kind, rate, a, b, tau, beta_d], dtype=np.float64)
+
+
+def rate(u, beta=1.0, theta=0.0, kind=0, a=0.06, b=0.54):
+    """Firing rate of the §5 models at every entry of u: kind 0 sigmoid (beta, theta),
+    kind 1 the C^4 smooth step on [a, b] (Eq. (smoothf))."""
+    m, pm = _d(_model_arr(0, kind, a, b))
+    u = np.asarray(u, dtype=np.float64)
+    return np.vectorize(lambda v: lib().or_rate(pm, float(v), float(beta), float(theta)))(u)
+
+
+def ab5_weights():
+    """Adams-Bashforth 5 weights c_0..c_4 (for F_n, F_{n-1}, ..., F_{n-4})."""
+    c = np.empty(5)
+    lib().or_ab5_weights(c.ctypes.data_as(_dp))
+    return c
+
+
+def field_advance(x, mu, u0, kernel, beta, theta, dt, nsteps, s0=None, kind=0, rate_kind=0, a=0.06, b=0.54,
+                  tau=1.0, beta_d=0.0, integrator="rk4"):
+    """§5 models on the nodes: kind 0 the neural field of Eq. (2.9), kind 1 the
+    synaptic-depression model (Eq. (nfsyndep), efficacy s); rate_kind 0 sigmoid, 1 smooth
+    step on [a, b]; integrator "rk4" or "ab5" (started by four RK4 steps).
+    Returns u (B x n), or (u, s) for kind 1."""
+    x, px = _d(x)
+    mu, pq = _d(mu)
+    u = np.array(np.atleast_2d(u0), dtype=np.float64, order="C")
+    B, n = u.shape
+    s = np.array(np.atleast_2d(s0), dtype=np.float64, order="C") if kind == 1 else None
+    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
+    th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
+    m, pm = _d(_model_arr(kind, rate_kind, a, b, tau, beta_d))
+    lib().or_field_advance(px, pq, n, u.ctypes.data_as(_dp), s.ctypes.data_as(_dp) if s is not None else None, B,
+                           0.0, dt, nsteps, pk, pbe, pth, pm, 1 if integrator == "ab5" else 0)
+    return (u, s) if kind == 1 else u

@@ -25,6 +25,8 @@
  *                   initial-state gradients of a terminal loss)
  *   manufactured    the manufactured-solution technique of §4, Eq. (4.5), on the
  *   forcing         unit sphere (Funk-Hecke eigenvalues by numerical quadrature)
+ *   §5 models       C^4 smooth-step firing rate, synaptic-depression two-field model,
+ *                   Adams-Bashforth 5 (started by four RK4 steps)
  */
 #include <math.h>
 #include <stdint.h>
@@ -781,4 +783,127 @@ double or_loss(const double *X, const double *q, int64_t n, const double *u0, in
     for (size_t i = 0; i < sz; ++i) L += (u[i] - target[i]) * (u[i] - target[i]);
     free(u);
     return L;
+}
+
+/* ================================================================================
+ * §5 examples: the C^4 smooth-step firing rate (labyrinth patterns, Eq. (smoothf)), the
+ * synaptic-depression two-field model (travelling spots, Eq. (nfsyndep)) and the
+ * Adams-Bashforth 5 integrator both examples use.
+ *
+ * model[] = {kind, rate, a, b, tau, beta_d}:
+ *   kind 0: du/dt = -u + sum_j w_ij mu_j f(u_j)                       (Eq. (2.9), no forcing)
+ *   kind 1: du/dt = -u + sum_j w_ij mu_j s_j f(u_j),
+ *           tau ds/dt = 1 - s - beta_d s f(u)                           (s: synaptic efficacy)
+ *   rate 0: f(u) = 1 / (1 + exp(-beta (u - theta)))   (per-trajectory beta, theta)
+ *   rate 1: f = 0 for u < a, 1 for u >= b, p(u) in between, p the degree-9 polynomial with
+ *           p(a) = 0, p(b) = 1 and its first four derivatives zero at a and at b.  With
+ *           t = (u - a)/(b - a): p' is proportional to t^4 (1 - t)^4, so
+ *           p = 630 int_0^t s^4 (1 - s)^4 ds = 126 t^5 - 420 t^6 + 540 t^7 - 315 t^8 + 70 t^9.
+ * ============================================================================== */
+static double smooth_step(double u, double a, double b) {
+    if (u < a) return 0.0;
+    if (u >= b) return 1.0;
+    double t = (u - a) / (b - a);
+    double t2 = t * t, t4 = t2 * t2, t5 = t4 * t;
+    return t5 * (126.0 - 420.0 * t + 540.0 * t2 - 315.0 * t2 * t + 70.0 * t4);
+}
+
+double or_rate(const double *model, double u, double beta, double theta) {
+    return (int)model[1] == 1 ? smooth_step(u, model[2], model[3]) : firing(u, beta, theta);
+}
+
+/* Vector field of the model for B trajectories: Fu (and Fs for kind 1). */
+static void model_field(const double *X, const double *mu, int64_t n, const double *u, const double *s, int B,
+                        const double *kpar, const double *beta, const double *theta, const double *model,
+                        double *Fu, double *Fs) {
+    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3]};
+    int kind = (int)model[0];
+    double *g = (double *)malloc(sizeof(double) * (size_t)(n * B));
+    for (int b = 0; b < B; ++b)
+        for (int64_t j = 0; j < n; ++j) {
+            double f = or_rate(model, u[b * n + j], beta[b], theta[b]);
+            g[b * n + j] = mu[j] * (kind == 1 ? s[b * n + j] : 1.0) * f;
+            if (kind == 1) Fs[b * n + j] = (1.0 - s[b * n + j] - model[5] * s[b * n + j] * f) / model[4];
+        }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int b = 0; b < B; ++b) {
+            double acc = 0.0;
+            for (int64_t j = 0; j < n; ++j) acc += kernel_w(&kp, pair_r2(X, i, j)) * g[b * n + j];
+            Fu[b * n + i] = -u[b * n + i] + acc;
+        }
+    free(g);
+}
+
+/* Adams-Bashforth 5 weights from their definition: y_{n+1} = y_n + dt sum_m c_m F_{n-m},
+ * c_m = int_0^1 L_m(s) ds with L_m the Lagrange basis polynomial through the nodes
+ * s = 0, -1, -2, -3, -4 (times t_n, t_{n-1}, ...) that is 1 at s = -m.  5-point
+ * Gauss-Legendre integrates the degree-4 integrands exactly. */
+void or_ab5_weights(double *c) {
+    double gx[5], gw[5];
+    gauss_legendre(5, gx, gw);
+    for (int m = 0; m < 5; ++m) {
+        double acc = 0.0;
+        for (int g = 0; g < 5; ++g) {
+            double sv = 0.5 * (gx[g] + 1.0), L = 1.0;
+            for (int k = 0; k < 5; ++k)
+                if (k != m) L *= (sv + k) / (double)(k - m);
+            acc += 0.5 * gw[g] * L;
+        }
+        c[m] = acc;
+    }
+}
+
+/* Advance the model nsteps steps of dt from t0 (autonomous: t0 only labels time).
+ * integrator 0: classical RK4 (tableau of or_rk4) on (u, s) together.
+ * integrator 1: Adams-Bashforth 5; the paper does not say how it is started, and here the
+ * first four steps are RK4 steps, each recording F at its start as AB5 history. */
+void or_field_advance(const double *X, const double *mu, int64_t n, double *u, double *s, int B, double t0,
+                      double dt, int nsteps, const double *kpar, const double *beta, const double *theta,
+                      const double *model, int integrator) {
+    (void)t0;
+    int kind = (int)model[0];
+    size_t sz = (size_t)(n * B);
+    double *ku[4], *ks[4], *U = malloc(sizeof(double) * sz), *S = malloc(sizeof(double) * sz);
+    for (int i = 0; i < 4; ++i) { ku[i] = malloc(sizeof(double) * sz); ks[i] = malloc(sizeof(double) * sz); }
+    double *hu[5], *hs[5];
+    for (int i = 0; i < 5; ++i) { hu[i] = malloc(sizeof(double) * sz); hs[i] = malloc(sizeof(double) * sz); }
+    double c[5];
+    or_ab5_weights(c);
+    const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int step = 0; step < nsteps; ++step) {
+        if (integrator == 1 && step >= 4) {
+            /* history slot of F_step: step % 5; F_{step-m} in slot (step - m) % 5 */
+            double *fu = hu[step % 5], *fs = hs[step % 5];
+            model_field(X, mu, n, u, s, B, kpar, beta, theta, model, fu, fs);
+            for (size_t i = 0; i < sz; ++i) {
+                double du = 0.0, dsv = 0.0;
+                for (int m = 0; m < 5; ++m) {
+                    du += c[m] * hu[(step - m) % 5][i];
+                    if (kind == 1) dsv += c[m] * hs[(step - m) % 5][i];
+                }
+                u[i] += dt * du;
+                if (kind == 1) s[i] += dt * dsv;
+            }
+            continue;
+        }
+        for (int st = 0; st < 4; ++st) {
+            for (size_t i = 0; i < sz; ++i) {
+                U[i] = st == 0 ? u[i] : u[i] + cs[st] * dt * ku[st - 1][i];
+                if (kind == 1) S[i] = st == 0 ? s[i] : s[i] + cs[st] * dt * ks[st - 1][i];
+            }
+            model_field(X, mu, n, U, kind == 1 ? S : NULL, B, kpar, beta, theta, model, ku[st], ks[st]);
+        }
+        if (integrator == 1) {
+            memcpy(hu[step % 5], ku[0], sizeof(double) * sz);
+            if (kind == 1) memcpy(hs[step % 5], ks[0], sizeof(double) * sz);
+        }
+        for (size_t i = 0; i < sz; ++i) {
+            u[i] += dt / 6.0 * (ku[0][i] + 2.0 * ku[1][i] + 2.0 * ku[2][i] + ku[3][i]);
+            if (kind == 1) s[i] += dt / 6.0 * (ks[0][i] + 2.0 * ks[1][i] + 2.0 * ks[2][i] + ks[3][i]);
+        }
+    }
+    for (int i = 0; i < 4; ++i) { free(ku[i]); free(ks[i]); }
+    for (int i = 0; i < 5; ++i) { free(hu[i]); free(hs[i]); }
+    free(U); free(S);
 }
