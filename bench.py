@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched tensor-core section")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation section")
+    ap.add_argument("--no-models", action="store_true", help="skip the §5 models section (depression, AB5)")
     ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="scale the batched node counts (profiling captures use a smaller case)")
     return ap.parse_args()
@@ -354,6 +355,45 @@ def run_batched(args, dev, steps):
     return out
 
 
+def run_models(args, dev, wl, x32, q32, u0):
+    """§5 models on the precision workload (matrix-free path): the synaptic-depression model
+    with the C^4 smooth-step rate, stepped by AB5 (one nonlocal sum per step) and by RK4.
+    AB5 steady state: the time of 4 + K steps minus the time of its 4 RK4 start-up steps."""
+    import torch
+
+    import paper_2504_13379_gb300 as nf
+
+    op = nf.Operator(x32, q32, wl.kernel, nf.MATRIX_FREE)
+    stream = torch.cuda.current_stream(dev)
+    K = max(8, min(args.steps, 40))
+    model = dict(rate=nf.RATE_SMOOTHSTEP, a=0.06, b=0.54, tau=20.0, beta_d=0.5)
+
+    def timed(nsteps, integrator):
+        u = u0.clone().view(1, -1)
+        s = torch.ones_like(u)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nf.nf_field_advance(op, u, wl.dt, nsteps, 20.0, 0.2, s=s, integrator=integrator, **model)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    timed(6, "ab5")  # warm-up
+    t_start = timed(4, "ab5")
+    t_ab5 = (timed(4 + K, "ab5") - t_start) / K
+    t_rk4 = timed(K, "rk4") / K
+    op.check()
+    op.close()
+    n = wl.n
+    return {"workload": f"synaptic depression (tau 20, beta_d 0.5) with the C^4 smooth step on [0.06, 0.54], "
+                        f"precision torus n={n}, matrix-free, dt={wl.dt}",
+            "ab5": {"ms_per_step": t_ab5, "steps_per_s": 1e3 / t_ab5, "pair_evals_per_s": n * n / (t_ab5 * 1e-3),
+                    "nonlocal_sums_per_step": 1, "steps_timed": K},
+            "rk4": {"ms_per_step": t_rk4, "steps_per_s": 1e3 / t_rk4, "pair_evals_per_s": 4 * n * n / (t_rk4 * 1e-3),
+                    "nonlocal_sums_per_step": 4, "steps_timed": K}}
+
+
 def run_adjoint(args, dev):
     """Differentiation workload: gradient of L = |u(T) - u_target|^2 w.r.t. the kernel
     parameters and u0 through the discrete RK4 adjoint (checkpoints every C steps)."""
@@ -556,6 +596,8 @@ def run_ours(args, rank, world, local_rank):
         line["gpu_launches"] += 4 * args.steps  # tensor-core path: one grouped GEMM per stage
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, dev)
+    if not args.no_models:
+        line["models"] = run_models(args, dev, wl, x32, q32, u0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], acc = cpu_baseline(wl, q32.double().cpu().numpy(), args.cpu_seconds, first_sums)
         for p, e in acc.items():

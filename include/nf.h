@@ -233,6 +233,41 @@ NF_API nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, dou
                          const float *beta, const float *theta, const nf_forcing *g,
                          float *ckpt, int C, void *stream);
 
+/* The models of §5, on any single operator path.
+ *   kind NF_MODEL_FIELD:      du/dt = -u + sum_j w_ij mu_j f(u_j)          (Eq. (2.9), no forcing)
+ *   kind NF_MODEL_DEPRESSION: du/dt = -u + sum_j w_ij mu_j s_j f(u_j),
+ *                             tau ds/dt = 1 - s - beta_d s f(u)          (Eq. (nfsyndep); s is the
+ *                             synaptic efficacy, 0 depleted .. 1 available)
+ *   rate NF_RATE_SIGMOID:     f(u) = 1 / (1 + exp(-beta_b (u - theta_b)))  (per trajectory)
+ *   rate NF_RATE_SMOOTHSTEP:  f = 0 below a, 1 from b on, between them the degree-9
+ *                             polynomial that is C^4 at both ends (Eq. (smoothf); the
+ *                             paper's labyrinth example uses a = 0.06, b = 0.54)
+ * The paper's examples integrate with Adams-Bashforth 5. */
+enum { NF_MODEL_FIELD = 0, NF_MODEL_DEPRESSION = 1 };
+enum { NF_RATE_SIGMOID = 0, NF_RATE_SMOOTHSTEP = 1 };
+enum { NF_INTEGRATOR_RK4 = 0, NF_INTEGRATOR_AB5 = 1 };
+typedef struct {
+    int kind, rate;
+    float a, b;          /* smooth-step transition interval */
+    float tau, beta_d;   /* depression time constant and strength */
+} nf_model;
+
+/* Advance a §5 model nsteps steps of dt, in place:
+ *   model       host pointer to nf_model
+ *   integrator  NF_INTEGRATOR_RK4 (classical tableau, 4 nonlocal sums per step) or
+ *               NF_INTEGRATOR_AB5 (y += dt (1901 F_n - 2774 F_{n-1} + 2616 F_{n-2}
+ *               - 1274 F_{n-3} + 251 F_{n-4}) / 720, one nonlocal sum per step; the paper
+ *               does not say how to start it, and the first four steps are RK4 steps whose
+ *               first-stage derivatives seed the history)
+ *   u           B x n FP32 device, in/out
+ *   s           B x n FP32 device, in/out, efficacy (NF_MODEL_DEPRESSION), else NULL
+ *   beta, theta B FP32 device (used by the sigmoid rate)
+ * The operator must be a single (not grouped) operator; its W (with mu) is reused
+ * unchanged.  Allocates stage and history buffers on `stream` for the call.
+ * Errors: NF_ERR_ARG, NF_ERR_NOMEM, NF_ERR_CUDA. */
+NF_API nf_status nf_field_advance(nf_operator *op, const nf_model *model, int integrator, float *u, float *s, int B,
+                                  double dt, int nsteps, const float *beta, const float *theta, void *stream);
+
 /* Discrete adjoint of nf_rk4_advance for a terminal loss L(u_N):
  *   lambda_T  B x n FP32   dL/du_N
  *   ckpt      checkpoints written by nf_rk4_advance with the same arguments

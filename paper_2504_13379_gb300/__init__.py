@@ -30,7 +30,8 @@ from . import _build
 __all__ = [
     "NFError", "lib", "build", "nf_build_stencils", "nf_quad_weights", "Operator", "nf_nonlocal_apply",
     "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
-    "DENSE_BF16X2", "DENSE_SYM_FP32", "STATUS",
+    "DENSE_BF16X2", "DENSE_SYM_FP32", "STATUS", "nf_field_advance", "MODEL_FIELD", "MODEL_DEPRESSION",
+    "RATE_SIGMOID", "RATE_SMOOTHSTEP",
 ]
 
 MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32 = 0, 1, 2, 4
@@ -41,7 +42,8 @@ STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINIT
 EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights", "nf_operator_create",
            "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
            "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms",
-           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout"]
+           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout",
+           "nf_field_advance"]
 
 
 class NFError(RuntimeError):
@@ -53,6 +55,11 @@ class NFError(RuntimeError):
 
 class _Kernel(C.Structure):
     _fields_ = [("A1", C.c_float), ("s1", C.c_float), ("A2", C.c_float), ("s2", C.c_float)]
+
+
+class _Model(C.Structure):
+    _fields_ = [("kind", C.c_int), ("rate", C.c_int), ("a", C.c_float), ("b", C.c_float), ("tau", C.c_float),
+                ("beta_d", C.c_float)]
 
 
 class _Forcing(C.Structure):
@@ -98,6 +105,8 @@ def lib(path: str | None = None):
     L.nf_mms_sphere_eigs.argtypes = [_Kernel, C.POINTER(C.c_double)]
     L.nf_rk4_advance.argtypes = [_vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp,
                                  C.POINTER(_Forcing), _vp, C.c_int, _vp]
+    L.nf_field_advance.argtypes = [_vp, C.POINTER(_Model), C.c_int, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp,
+                                   _vp, _vp]
     L.nf_adjoint.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp,
                              C.POINTER(_Forcing), _vp, _vp, _vp, _vp]
     _lib = L
@@ -301,6 +310,30 @@ def nf_rk4_advance(op: Operator, u: torch.Tensor, t0: float, dt: float, nsteps: 
     # keep the per-trajectory arrays alive until the queued work has consumed them
     op._keep = (be, th, forcing)
     return u
+
+
+MODEL_FIELD, MODEL_DEPRESSION = 0, 1
+RATE_SIGMOID, RATE_SMOOTHSTEP = 0, 1
+
+
+def nf_field_advance(op: Operator, u: torch.Tensor, dt: float, nsteps: int, beta=1.0, theta=0.0,
+                     s: torch.Tensor | None = None, rate: int = RATE_SIGMOID, a: float = 0.06, b: float = 0.54,
+                     tau: float = 1.0, beta_d: float = 0.0, integrator: str = "rk4"):
+    """Advance a §5 model in place: the neural field (s None) or the synaptic-depression
+    model (s: B x n efficacy), sigmoid or C^4 smooth-step rate, RK4 or AB5."""
+    u2 = u if u.dim() == 2 else u.view(1, -1)
+    B = u2.shape[0]
+    s2 = None if s is None else (s if s.dim() == 2 else s.view(1, -1))
+    be, th = _per_traj(beta, B, u.device), _per_traj(theta, B, u.device)
+    m = _Model(MODEL_DEPRESSION if s is not None else MODEL_FIELD, int(rate), float(a), float(b), float(tau),
+               float(beta_d))
+    integ = {"rk4": 0, "ab5": 1}[integrator]
+    _check(lib().nf_field_advance(op.handle, C.byref(m), integ, _dptr(u2, torch.float32, "u"),
+                                  _dptr(s2, torch.float32, "s") if s2 is not None else None, B, float(dt),
+                                  int(nsteps), _dptr(be, torch.float32, "beta"), _dptr(th, torch.float32, "theta"),
+                                  _stream(u)))
+    op._keep = (be, th)
+    return (u, s) if s is not None else u
 
 
 def nf_adjoint(op: Operator, ckpt: torch.Tensor, C_every: int, t0: float, dt: float, nsteps: int, beta, theta,

@@ -84,7 +84,7 @@ nf_status ensure_workspace(nf_operator *op, int B, int splits) {
 SplitPlan mf_plan(nf_operator *op);
 SplitPlan dense_plan(nf_operator *op);
 
-static int path_splits(nf_operator *op, int B) {
+int nonlocal_splits(nf_operator *op, int B) {
     return (op->path == NF_MATRIX_FREE) ? mf_splits(op, B) : dense_splits(op);
 }
 
@@ -377,7 +377,7 @@ nf_status nf_nonlocal_apply(nf_operator *op, const float *u, int B, const float 
         NF_TRY(tc_prep(op, u, beta, theta, false, 0, s));
         return tc_launch(op, 0, 0, I, nullptr, beta, theta, 0.0, 0, nullptr, 1, s);
     }
-    NF_TRY(ensure_workspace(op, B, path_splits(op, B)));
+    NF_TRY(ensure_workspace(op, B, nonlocal_splits(op, B)));
     NF_TRY(launch_prep_g(op, u, B, beta, theta, false, s));
     int splits = 1;
     NF_TRY(launch_nonlocal_partial(op, B, s, &splits));
@@ -413,7 +413,7 @@ nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt,
     }
     if (ckpt) NF_CUDA_TRY(cudaMemcpyAsync(ckpt, u, sizeof(float) * B * op->n, cudaMemcpyDeviceToDevice, s));
     if (nsteps == 0) return NF_OK;
-    NF_TRY(ensure_workspace(op, B, path_splits(op, B)));
+    NF_TRY(ensure_workspace(op, B, nonlocal_splits(op, B)));
     cudaGraphExec_t exec = nullptr;
     NF_TRY(rk4_step_graph(op, u, B, dt, beta, theta, *F, ckpt, ckpt ? C : 1, &exec));
     NF_TRY(launch_prep_g(op, u, B, beta, theta, true, s));

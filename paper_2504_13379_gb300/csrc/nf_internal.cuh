@@ -247,6 +247,7 @@ nf_status launch_set_clock(nf_operator *op, double t0, cudaStream_t s);
 
 // nonlocal sum of the current g into partial (path dispatch)
 nf_status launch_nonlocal_partial(nf_operator *op, int B, cudaStream_t s, int *splits_out);
+int nonlocal_splits(nf_operator *op, int B);  // partial-sum slots of launch_nonlocal_partial
 
 void destroy_graphs(nf_operator *op);
 
