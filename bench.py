@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched tensor-core section")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation section")
     ap.add_argument("--no-models", action="store_true", help="skip the §5 models section (depression, AB5)")
+    ap.add_argument("--no-geometries", action="store_true", help="skip the curved-geometry weights section")
     ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="scale the batched node counts (profiling captures use a smaller case)")
     return ap.parse_args()
@@ -394,6 +395,32 @@ def run_models(args, dev, wl, x32, q32, u0):
                     "nonlocal_sums_per_step": 4, "steps_timed": K}}
 
 
+def run_geometries(dev, n=100000):
+    """Surface quadrature setup on the paper's deformed sphere (gamma = 0.8) and ring Dupin
+    cyclide at n ~ 1e5 nodes (k = 32, degree 3): GPU stencils + weights time, and the
+    relative error of sum(q) against the surface area (parameter-space reference)."""
+    import torch
+
+    import nodesets
+    import paper_2504_13379_gb300 as nf
+
+    out = {}
+    for name, ns in (("deformed_sphere_gamma0.8", nodesets.deformed_sphere(n, 0.8)),
+                     ("dupin_cyclide_ring", nodesets.cyclide_lattice(n))):
+        nodes = torch.as_tensor(ns.nodes, device=dev)
+        tris = torch.as_tensor(ns.tris, device=dev)
+        normals = torch.as_tensor(ns.normals, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st = nf.nf_build_stencils(nodes, tris, 32)
+        q = nf.nf_quad_weights(nodes, tris, st, 3, normals=normals)
+        torch.cuda.synchronize(dev)
+        ms = 1e3 * (time.perf_counter() - t0)
+        out[name] = {"n": ns.n, "elements": ns.m, "stencils_plus_weights_ms": ms,
+                     "sum_q_minus_area_rel": float((q.sum().item() - ns.area) / ns.area)}
+    return out
+
+
 def run_adjoint(args, dev):
     """Differentiation workload: gradient of L = |u(T) - u_target|^2 w.r.t. the kernel
     parameters and u0 through the discrete RK4 adjoint (checkpoints every C steps)."""
@@ -598,6 +625,8 @@ def run_ours(args, rank, world, local_rank):
         line["adjoint"] = run_adjoint(args, dev)
     if not args.no_models:
         line["models"] = run_models(args, dev, wl, x32, q32, u0)
+    if not args.no_geometries:
+        line["geometries"] = run_geometries(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], acc = cpu_baseline(wl, q32.double().cpu().numpy(), args.cpu_seconds, first_sums)
         for p, e in acc.items():

@@ -241,6 +241,27 @@ def _torus_rows(n: int, R: float, r: float) -> int:
     return best
 
 
+def _lattice_tris(rows: int, cols: int) -> np.ndarray:
+    """Triangles of the doubly periodic staggered lattice (node t * cols + p; odd rows
+    shifted by half a spacing)."""
+    tris = []
+    for t in range(rows):
+        t1 = (t + 1) % rows
+        p = np.arange(cols)
+        p1 = (p + 1) % cols
+        a = t * cols + p
+        b = t * cols + p1
+        c = t1 * cols + p
+        d = t1 * cols + p1
+        if t % 2 == 0:       # next row is shifted by +1/2
+            tris.append(np.stack([a, b, c], 1))
+            tris.append(np.stack([b, d, c], 1))
+        else:                # this row is shifted by +1/2
+            tris.append(np.stack([a, d, c], 1))
+            tris.append(np.stack([a, b, d], 1))
+    return np.concatenate(tris).astype(np.int32)
+
+
 def torus_lattice(n: int = 100000, R: float = 1.0, r: float = 0.4, jitter: float = 0.15,
                   seed: int = 0) -> NodeSet:
     """Torus of major radius R and minor radius r sampled on the staggered triangular
@@ -262,23 +283,7 @@ def torus_lattice(n: int = 100000, R: float = 1.0, r: float = 0.4, jitter: float
         th = th + j[:, 1] * dth
     x = torus_point(phi, th, R, r)
     nrm = np.stack([np.cos(th) * np.cos(phi), np.cos(th) * np.sin(phi), np.sin(th)], 1)
-    tris = []
-    for t in range(rows):
-        t1 = (t + 1) % rows
-        p = np.arange(cols)
-        p1 = (p + 1) % cols
-        a = t * cols + p
-        b = t * cols + p1
-        c = t1 * cols + p
-        d = t1 * cols + p1
-        if t % 2 == 0:       # next row is shifted by +1/2
-            tris.append(np.stack([a, b, c], 1))
-            tris.append(np.stack([b, d, c], 1))
-        else:                # this row is shifted by +1/2
-            tris.append(np.stack([a, d, c], 1))
-            tris.append(np.stack([a, b, d], 1))
-    tris = np.concatenate(tris).astype(np.int32)
-    tris = _orient_outward(x, tris, nrm)
+    tris = _orient_outward(x, _lattice_tris(rows, cols), nrm)
     return NodeSet(np.ascontiguousarray(x), tris, np.ascontiguousarray(nrm), 3,
                    area=4.0 * math.pi ** 2 * R * r,
                    meta={"kind": "torus", "R": R, "r": r, "rows": rows, "cols": cols,
@@ -337,3 +342,112 @@ def random_bumps(ns: NodeSet, B: int, seed: int, axes=(1.0, 1.0, 1.0)):
     theta = rng.uniform(0.1, 0.3, B)
     u0 = np.stack([bump_u0(ns.nodes, c[b], amp[b], wid[b]) for b in range(B)])
     return u0, beta, theta
+
+
+# ----------------------------------------------------------------------------------
+# further curved geometries of the paper (§5 deformed spheres; the ring Dupin cyclide of
+# the convergence appendix)
+# ----------------------------------------------------------------------------------
+
+def _deformed_h(rho2, gamma):
+    return np.sqrt(1.0 - gamma / (1.0 + rho2 / 2.89))
+
+
+def deformed_sphere(n: int, gamma: float = 0.4, jitter: float = 0.1, seed: int = 0) -> NodeSet:
+    """The one-parameter family D_gamma of §5: 1 = x^2 + y^2 + z^2 / (1 - gamma / (1 +
+    (x^2 + y^2) / 2.89)).  A jittered Fibonacci sphere mapped by z -> z h(x^2 + y^2),
+    h = sqrt(1 - gamma / (1 + rho^2 / 2.89)) (rho^2 = x^2 + y^2 is kept), with the sphere's
+    hull connectivity; normals are the normalised gradients of the implicit form."""
+    s = sphere_fibonacci(n, jitter, seed)
+    p = s.nodes.copy()
+    rho2 = p[:, 0] ** 2 + p[:, 1] ** 2
+    p[:, 2] *= _deformed_h(rho2, gamma)
+    g = 1.0 - gamma / (1.0 + rho2 / 2.89)
+    dg = gamma / (2.89 * (1.0 + rho2 / 2.89) ** 2)        # dg / d(rho^2)
+    z2 = p[:, 2] ** 2
+    grad = np.stack([2 * p[:, 0] * (1 - z2 * dg / g ** 2), 2 * p[:, 1] * (1 - z2 * dg / g ** 2), 2 * p[:, 2] / g], 1)
+    nrm = grad / np.linalg.norm(grad, axis=1, keepdims=True)
+    tris = _orient_outward(p, s.tris, nrm)
+    return NodeSet(np.ascontiguousarray(p), tris, np.ascontiguousarray(nrm), 3, area=deformed_sphere_area(gamma),
+                   meta={"kind": "deformed_sphere", "gamma": gamma, "seed": seed})
+
+
+def deformed_sphere_area(gamma: float) -> float:
+    """Area of D_gamma: surface of revolution rho = sin t, z = cos t h(sin^2 t), integrated
+    in t by 400-point Gauss-Legendre (the profile is smooth)."""
+    x, w = np.polynomial.legendre.leggauss(400)
+    t = 0.5 * math.pi * (x + 1.0)
+    eps = 1e-6
+    def prof(tt):
+        return np.sin(tt), np.cos(tt) * _deformed_h(np.sin(tt) ** 2, gamma)
+    r0, z0 = prof(t)
+    rp, zp = prof(t + eps)
+    rm, zm = prof(t - eps)
+    ds = np.hypot((rp - rm) / (2 * eps), (zp - zm) / (2 * eps))
+    return float(2.0 * math.pi * 0.5 * math.pi * np.sum(w * r0 * ds))
+
+
+def cyclide_point(phi, theta, a=1.0, b=0.98, c=0.1983, d=0.5) -> np.ndarray:
+    """Dupin cyclide, standard parametrisation over (phi, theta) in [0, 2 pi)^2 (ring case
+    for c < d < a)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    theta = np.asarray(theta, dtype=np.float64)
+    den = a - c * np.cos(theta) * np.cos(phi)
+    x = (d * (c - a * np.cos(theta) * np.cos(phi)) + b * b * np.cos(theta)) / den
+    y = b * np.sin(theta) * (a - d * np.cos(phi)) / den
+    z = b * np.sin(phi) * (c * np.cos(theta) - d) / den
+    return np.stack([x, y, z], -1)
+
+
+def _cyclide_frame(phi, theta, eps=1e-6, **kw):
+    xp = (cyclide_point(phi + eps, theta, **kw) - cyclide_point(phi - eps, theta, **kw)) / (2 * eps)
+    xt = (cyclide_point(phi, theta + eps, **kw) - cyclide_point(phi, theta - eps, **kw)) / (2 * eps)
+    return np.cross(xp, xt)
+
+
+def cyclide_area(a=1.0, b=0.98, c=0.1983, d=0.5, m: int = 600) -> float:
+    """Area of the cyclide by the periodic trapezoid rule on an m x m parameter grid
+    (spectrally accurate for the smooth periodic area element)."""
+    g = 2.0 * math.pi * np.arange(m) / m
+    P, T = np.meshgrid(g, g, indexing="ij")
+    J = np.linalg.norm(_cyclide_frame(P, T, a=a, b=b, c=c, d=d), axis=-1)
+    return float(J.sum() * (2.0 * math.pi / m) ** 2)
+
+
+def cyclide_integral(f, a=1.0, b=0.98, c=0.1983, d=0.5, m: int = 600) -> float:
+    """Integral of f(x, y, z) over the cyclide (periodic trapezoid rule, m x m grid)."""
+    g = 2.0 * math.pi * np.arange(m) / m
+    P, T = np.meshgrid(g, g, indexing="ij")
+    X = cyclide_point(P, T, a=a, b=b, c=c, d=d)
+    J = np.linalg.norm(_cyclide_frame(P, T, a=a, b=b, c=c, d=d), axis=-1)
+    return float((f(X[..., 0], X[..., 1], X[..., 2]) * J).sum() * (2.0 * math.pi / m) ** 2)
+
+
+def cyclide_lattice(n: int, a=1.0, b=0.98, c=0.1983, d=0.5, rows: int | None = None) -> NodeSet:
+    """Ring Dupin cyclide on a non-random staggered triangular lattice in (phi, theta)
+    parameter space (the appendix's mesh): rows of constant theta, odd rows shifted by
+    half a spacing.  Normals from the parametrisation's tangent vectors, oriented outward
+    (positive enclosed volume)."""
+    if rows is None:
+        # near-equilateral triangles: the theta circles are about twice as long as the phi
+        # circles (mean 2 pi vs pi for these parameters), so theta gets rows spaced
+        # sqrt(3)/2 of the phi spacing: cols / rows = (sqrt(3)/2) (1 / 2)
+        rows = max(4, int(round(math.sqrt(n / (0.25 * math.sqrt(3.0))) / 2.0)) * 2)
+    cols = n // rows
+    t_idx = np.repeat(np.arange(rows), cols)
+    p_idx = np.tile(np.arange(cols), rows)
+    th = t_idx * (2.0 * math.pi / rows)
+    ph = (p_idx + 0.5 * (t_idx % 2)) * (2.0 * math.pi / cols)
+    x = cyclide_point(ph, th, a=a, b=b, c=c, d=d)
+    nrm = _cyclide_frame(ph, th, a=a, b=b, c=c, d=d)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    tris = _lattice_tris(rows, cols)
+    # orient normals outward: the triangulated surface must enclose a positive volume
+    tri_n = np.cross(x[tris[:, 1]] - x[tris[:, 0]], x[tris[:, 2]] - x[tris[:, 0]])
+    align = np.sign(np.einsum("ij,ij->i", tri_n, nrm[tris[:, 0]]))
+    vol = np.sum(np.einsum("ij,ij->i", x[tris[:, 0]], tri_n) * align) / 6.0
+    if vol < 0:
+        nrm = -nrm
+    tris = _orient_outward(x, tris, nrm)
+    return NodeSet(np.ascontiguousarray(x), tris, np.ascontiguousarray(nrm), 3, area=cyclide_area(a, b, c, d),
+                   meta={"kind": "cyclide", "abcd": (a, b, c, d), "rows": rows, "cols": cols})

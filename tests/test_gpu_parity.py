@@ -88,7 +88,7 @@ def _weights_pair(nf, ns, k, deg):
     return got, want
 
 
-@pytest.mark.parametrize("case", ["flat", "sphere", "torus", "ellipsoid", "regular"])
+@pytest.mark.parametrize("case", ["flat", "sphere", "torus", "ellipsoid", "regular", "deformed", "cyclide"])
 def test_quad_weights_match_oracle(nf, case):
     if case == "flat":
         ns, k, deg = nodesets.square_halton(1500), 24, 2
@@ -98,6 +98,10 @@ def test_quad_weights_match_oracle(nf, case):
         ns, k, deg = nodesets.torus_lattice(8000, seed=2), 48, 4
     elif case == "ellipsoid":
         ns, k, deg = nodesets.ellipsoid_fibonacci(5000, seed=3), 32, 3
+    elif case == "deformed":
+        ns, k, deg = nodesets.deformed_sphere(4000, 0.8, seed=6), 32, 3
+    elif case == "cyclide":
+        ns, k, deg = nodesets.cyclide_lattice(4000), 32, 3
     else:
         ns, k, deg = nodesets.square_regular(24), 21, 3
     got, want = _weights_pair(nf, ns, k, deg)
