@@ -66,6 +66,12 @@ def lib():
         L.or_mms_sphere_solution.argtypes = [_dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_double, _dp]
         L.or_num_threads.restype = C.c_int
+        L.or_mms_flat_solution.argtypes = [_dp, C.c_int64, C.c_double, _dp, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_double, _dp]
+        L.or_mms_flat_solution.restype = None
+        L.or_mms_flat_forcing.argtypes = [_dp, C.c_int64, C.c_double, _dp, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, C.c_double, _dp]
+        L.or_mms_flat_forcing.restype = None
         L.or_rate.argtypes = [_dp, C.c_double, C.c_double, C.c_double]
         L.or_rate.restype = C.c_double
         L.or_ab5_weights.argtypes = [_dp]
@@ -203,15 +209,25 @@ def quad_weights(nodes, tris, stencils, deg, normals=None, return_elem=False):
 
 # ---------------------------------------------------------------------------- §2.2
 
-def nonlocal_sum(x, q, u, kernel, beta, theta, rows=None):
+def _kern(kernel, period=0.0):
+    """(A1, s1, A2, s2) plus the period L of the flat doubly periodic square (0: Euclidean
+    distance).  A fifth entry of ``kernel`` is taken as the period when given."""
+    k = [float(v) for v in kernel]
+    if len(k) == 4:
+        k.append(float(period))
+    return _d(np.asarray(k[:5], dtype=np.float64))
+
+
+def nonlocal_sum(x, q, u, kernel, beta, theta, rows=None, period=0.0):
     """I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]) for all rows (or ``rows``).
-    x: n x 3, u: B x n (or n), kernel: (A1, s1, A2, s2)."""
+    x: n x 3, u: B x n (or n), kernel: (A1, s1, A2, s2); period > 0 takes |x_i - x_j| as
+    the doubly periodic distance of Eq. (dist) on the square of that side."""
     x, px = _d(x)
     q, pq = _d(q)
     u = np.atleast_2d(u)
     u, pu = _d(u)
     B, n = u.shape
-    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    kp, pk = _kern(kernel, period)
     be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
     th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
     if rows is None:
@@ -227,17 +243,21 @@ def nonlocal_sum(x, q, u, kernel, beta, theta, rows=None):
 def _forcing_arr(forcing):
     if forcing is None:
         return None, None
-    f = np.asarray([forcing["kind"], forcing["c"], forcing["a0"], *forcing["lam"]], dtype=np.float64)
+    if forcing["kind"] == 2:
+        f = np.asarray([2, forcing["c"], forcing["radius"], forcing["sigma"], forcing["scale"], 0.0],
+                       dtype=np.float64)
+    else:
+        f = np.asarray([forcing["kind"], forcing["c"], forcing["a0"], *forcing["lam"]], dtype=np.float64)
     return _d(f)
 
 
-def rk4(x, q, u0, kernel, beta, theta, t0, dt, nsteps, forcing=None, return_stages=False):
+def rk4(x, q, u0, kernel, beta, theta, t0, dt, nsteps, forcing=None, return_stages=False, period=0.0):
     """Classical RK4 for Eq. (2.9); returns u(t0 + nsteps dt) (B x n)."""
     x, px = _d(x)
     q, pq = _d(q)
     u = np.array(np.atleast_2d(u0), dtype=np.float64, order="C")
     B, n = u.shape
-    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    kp, pk = _kern(kernel, period)
     be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
     th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
     f, pf = _forcing_arr(forcing)
@@ -247,14 +267,14 @@ def rk4(x, q, u0, kernel, beta, theta, t0, dt, nsteps, forcing=None, return_stag
     return (u, st) if return_stages else u
 
 
-def adjoint(x, q, u0, kernel, beta, theta, t0, dt, nsteps, lam_T, forcing=None):
+def adjoint(x, q, u0, kernel, beta, theta, t0, dt, nsteps, lam_T, forcing=None, period=0.0):
     """Discrete RK4 adjoint: returns (dL/du0 (B x n), dL/d(A1,s1,A2,s2) (B x 4))."""
     x, px = _d(x)
     q, pq = _d(q)
     u0 = np.atleast_2d(u0)
     u0, pu = _d(u0)
     B, n = u0.shape
-    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    kp, pk = _kern(kernel, period)
     be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
     th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
     f, pf = _forcing_arr(forcing)
@@ -266,14 +286,14 @@ def adjoint(x, q, u0, kernel, beta, theta, t0, dt, nsteps, lam_T, forcing=None):
     return gu, gk
 
 
-def loss(x, q, u0, kernel, beta, theta, t0, dt, nsteps, target, forcing=None):
+def loss(x, q, u0, kernel, beta, theta, t0, dt, nsteps, target, forcing=None, period=0.0):
     """L = sum (u_N - target)^2 after nsteps RK4 steps."""
     x, px = _d(x)
     q, pq = _d(q)
     u0 = np.atleast_2d(u0)
     u0, pu = _d(u0)
     B, n = u0.shape
-    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    kp, pk = _kern(kernel, period)
     be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
     th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
     f, pf = _forcing_arr(forcing)
@@ -281,10 +301,10 @@ def loss(x, q, u0, kernel, beta, theta, t0, dt, nsteps, target, forcing=None):
     return float(lib().or_loss(px, pq, n, pu, B, t0, dt, nsteps, pk, pbe, pth, pf, ptg))
 
 
-def mms_sphere_eigs(kernel):
+def mms_sphere_eigs(kernel, period=0.0):
     """Funk-Hecke eigenvalues (lambda_0, lambda_1, lambda_2) of the radial kernel on the
     unit sphere, by composite Gauss-Legendre quadrature."""
-    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    kp, pk = _kern(kernel, period)
     lam = np.empty(3)
     lib().or_mms_sphere_eigs(pk, lam.ctypes.data_as(_dp))
     return lam
@@ -300,6 +320,31 @@ def mms_sphere_solution(x, t, beta, theta, c=0.5, a0=0.3):
     u = np.empty(x.shape[0])
     lib().or_mms_sphere_solution(px, x.shape[0], t, c, a0, beta, theta, u.ctypes.data_as(_dp))
     return u
+
+
+def mms_flat_forcing(c=0.1, radius=0.2, sigma=1.1, scale=1.0):
+    """Forcing descriptor for the manufactured solution on the flat periodic square
+    (kind 2): a Gaussian of width sigma whose centre circles the origin at ``radius``, plus
+    c, as the firing rate; ``scale`` multiplies the convolution term (1 flat, r torus)."""
+    return {"kind": 2, "c": c, "radius": radius, "sigma": sigma, "scale": scale}
+
+
+def mms_flat_solution(x, t, kernel, period, beta, theta, c=0.1, radius=0.2, sigma=1.1):
+    """u*(t, x) of the kind-2 manufactured solution at nodes (x, y, .) of the square."""
+    x, px = _d(x)
+    kp, pk = _kern(kernel, period)
+    u = np.empty(x.shape[0])
+    lib().or_mms_flat_solution(px, x.shape[0], t, pk, radius, sigma, c, beta, theta, u.ctypes.data_as(_dp))
+    return u
+
+
+def mms_flat_forcing_values(x, t, kernel, period, beta, theta, c=0.1, radius=0.2, sigma=1.1, scale=1.0):
+    """gamma(t, x) of the kind-2 manufactured solution (the convolution by panel quadrature)."""
+    x, px = _d(x)
+    kp, pk = _kern(kernel, period)
+    g = np.empty(x.shape[0])
+    lib().or_mms_flat_forcing(px, x.shape[0], t, pk, radius, sigma, c, scale, beta, theta, g.ctypes.data_as(_dp))
+    return g
 
 
 def _model_arr(kind=0, rate=0, a=0.06, b=0.54, tau=1.0, beta_d=0.0):
@@ -322,7 +367,7 @@ def ab5_weights():
 
 
 def field_advance(x, mu, u0, kernel, beta, theta, dt, nsteps, s0=None, kind=0, rate_kind=0, a=0.06, b=0.54,
-                  tau=1.0, beta_d=0.0, integrator="rk4"):
+                  tau=1.0, beta_d=0.0, integrator="rk4", period=0.0):
     """§5 models on the nodes: kind 0 the neural field of Eq. (2.9), kind 1 the
     synaptic-depression model (Eq. (nfsyndep), efficacy s); rate_kind 0 sigmoid, 1 smooth
     step on [a, b]; integrator "rk4" or "ab5" (started by four RK4 steps).
@@ -332,7 +377,7 @@ def field_advance(x, mu, u0, kernel, beta, theta, dt, nsteps, s0=None, kind=0, r
     u = np.array(np.atleast_2d(u0), dtype=np.float64, order="C")
     B, n = u.shape
     s = np.array(np.atleast_2d(s0), dtype=np.float64, order="C") if kind == 1 else None
-    kp, pk = _d(np.asarray(kernel, dtype=np.float64))
+    kp, pk = _kern(kernel, period)
     be, pbe = _d(np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,)))
     th, pth = _d(np.broadcast_to(np.asarray(theta, dtype=np.float64), (B,)))
     m, pm = _d(_model_arr(kind, rate_kind, a, b, tau, beta_d))

@@ -526,22 +526,36 @@ int or_quad_weights(const double *X, const double *NS, int64_t n, int dim, const
  * Firing rate (§4, Eq. (4.4)): f(u) = 1 / (1 + exp(-beta (u - theta))).
  * ============================================================================== */
 
-typedef struct { double A1, s1, A2, s2; } or_kernel;
+typedef struct { double A1, s1, A2, s2, period; } or_kernel;
 
 static double kernel_w(const or_kernel *kp, double r2) {
     return kp->A1 * exp(-r2 / (kp->s1 * kp->s1)) - kp->A2 * exp(-r2 / (kp->s2 * kp->s2));
 }
 static double firing(double u, double beta, double theta) { return 1.0 / (1.0 + exp(-beta * (u - theta))); }
-static double pair_r2(const double *X, int64_t i, int64_t j) {
-    double dx = X[3 * i] - X[3 * j], dy = X[3 * i + 1] - X[3 * j + 1], dz = X[3 * i + 2] - X[3 * j + 2];
-    return dx * dx + dy * dy + dz * dz;
+
+/* Squared distance.  period = 0: Euclidean.  period = L > 0: the doubly periodic distance of
+ * §4, Eq. (dist), on the flat square of side L (z = 0): the minimum over the nine shifts
+ * x - y + L (i, j), i, j in {-1, 0, 1}. */
+static double dist2p(double dx, double dy, double dz, double period) {
+    if (period <= 0.0) return dx * dx + dy * dy + dz * dz;
+    double best = -1.0;
+    for (int i = -1; i <= 1; ++i)
+        for (int j = -1; j <= 1; ++j) {
+            double ex = dx + period * i, ey = dy + period * j;
+            double d = ex * ex + ey * ey + dz * dz;
+            if (best < 0.0 || d < best) best = d;
+        }
+    return best;
+}
+static double pair_r2p(const double *X, int64_t i, int64_t j, double period) {
+    return dist2p(X[3 * i] - X[3 * j], X[3 * i + 1] - X[3 * j + 1], X[3 * i + 2] - X[3 * j + 2], period);
 }
 
 /* I[b, rows[t]] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]).  X: n x 3.
  * rows == NULL: all rows, output I is B x n.  Otherwise output is B x nrows. */
 void or_nonlocal(const double *X, const double *q, int64_t n, const double *u, int B, const double *kpar,
                  const double *beta, const double *theta, const int64_t *rows, int64_t nrows, double *I) {
-    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3]};
+    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3], kpar[4]};
     if (!rows) nrows = n;
     double *g = (double *)malloc(sizeof(double) * (size_t)(n * B));
     for (int b = 0; b < B; ++b)
@@ -551,7 +565,7 @@ void or_nonlocal(const double *X, const double *q, int64_t n, const double *u, i
         int64_t i = rows ? rows[t] : t;
         for (int b = 0; b < B; ++b) {
             double s = 0.0;
-            for (int64_t j = 0; j < n; ++j) s += kernel_w(&kp, pair_r2(X, i, j)) * g[b * n + j];
+            for (int64_t j = 0; j < n; ++j) s += kernel_w(&kp, pair_r2p(X, i, j, kp.period)) * g[b * n + j];
             I[b * nrows + t] = s;
         }
     }
@@ -568,13 +582,128 @@ void or_nonlocal(const double *X, const double *q, int64_t n, const double *u, i
  * --------------------------------------------------------------------------------- */
 typedef struct {
     int kind;
-    double c, a0, lam0, lam1, lam2;
+    double c, a0, lam0, lam1, lam2;   /* kind 1 */
+    double radius, sigma, scale;       /* kind 2 */
 } or_forcing;
 
-static void forcing_eval(const or_forcing *F, const double *X, int64_t n, double t, double beta, double theta,
-                         double *gam) {
+static void gauss_legendre(int N, double *x, double *w);
+
+/* ---------------------------------------------------------------------------------
+ * Forcing kind 2: the manufactured solution of the convergence study on the square (§4.3),
+ * on the doubly periodic square of side L (the kernel's period), coordinates (x, y):
+ *   z(t, x) = G(x, x0(t); sigma) + c,  x0(t) = radius (cos t, sin t),
+ *   G(x, y; s) = exp(-dist^2(x, y) / (2 s^2)) / (2 pi s^2)   (dist: Eq. (dist)),
+ *   u*(t, x) = theta + ln(z / (1 - z)) / beta,  so that f(u*) = z,
+ *   gamma = d(u*)/dt + u* - scale * C(t, x),  C = int over one period cell of w(dist(x, y)) z(t, y) dy.
+ * scale = 1 on the square.  On the torus of §4.4 the kernel is divided by R + r cos(theta)
+ * of the source point and the surface element is r (R + r cos theta) dphi dtheta, which
+ * leaves the same integral over the (phi, theta) square times scale = r.
+ * d(u*)/dt = (dz/dt) / (beta z (1 - z)), dz/dt = G (x - x0) . x0'(t) / sigma^2 with the
+ * minimum-image displacement x - x0.
+ * C by quadrature over the displacement d = x - y, which runs over the square
+ * [-L/2, L/2]^2 as y runs over a cell (so w(dist) = w(|d|)).  Where the kernel is negligible
+ * (beyond 8 of its standard deviations) the square is cut down to that window.  z(x - d) is
+ * smooth except on the lines where its nearest image of x0 changes (x - d - x0 = L/2 + kL in
+ * a coordinate); those lines split the window into panels, each integrated by a 40 x 40
+ * Gauss-Legendre product rule. */
+static double min_image(double d, double L) { return d - L * nearbyint(d / L); }
+
+static double gauss2(double dx, double dy, double s) {
+    return exp(-(dx * dx + dy * dy) / (2.0 * s * s)) / (2.0 * M_PI * s * s);
+}
+
+/* Breakpoints of one displacement coordinate: window ends and the cut points in between. */
+static int conv_breaks(double xc, double x0c, double h, double L, double *bp) {
+    int nb = 0;
+    bp[nb++] = -h;
+    for (int k = -3; k <= 3; ++k) {
+        double d = xc - x0c - 0.5 * L - k * L;
+        if (d > -h && d < h) bp[nb++] = d;
+    }
+    bp[nb++] = h;
+    for (int i = 1; i < nb; ++i)  /* sort (at most a few entries) */
+        for (int j = i; j > 0 && bp[j] < bp[j - 1]; --j) {
+            double t = bp[j]; bp[j] = bp[j - 1]; bp[j - 1] = t;
+        }
+    return nb;
+}
+
+static double conv_window(const or_kernel *kp, double x, double y, double x0, double y0, double sigma, double c) {
+    enum { NGL = 40 };
+    static double gx[NGL], gw[NGL];
+    static int init = 0;
+    if (!init) {
+#pragma omp critical(or_gl_init)
+        {
+            if (!init) { gauss_legendre(NGL, gx, gw); init = 1; }
+        }
+    }
+    const double L = kp->period;
+    double sd = kp->s1 / sqrt(2.0);
+    if (kp->A2 != 0.0 && kp->s2 / sqrt(2.0) > sd) sd = kp->s2 / sqrt(2.0);
+    double h = 8.0 * sd;
+    if (h > 0.5 * L) h = 0.5 * L;
+    double bx[10], by[10];
+    int nbx = conv_breaks(x, x0, h, L, bx), nby = conv_breaks(y, y0, h, L, by);
+    double acc = 0.0;
+    for (int px = 0; px + 1 < nbx; ++px)
+        for (int py = 0; py + 1 < nby; ++py) {
+            double ax = bx[px], hx = 0.5 * (bx[px + 1] - ax), ay = by[py], hy = 0.5 * (by[py + 1] - ay);
+            for (int i = 0; i < NGL; ++i) {
+                double dx = ax + hx * (gx[i] + 1.0);
+                for (int j = 0; j < NGL; ++j) {
+                    double dy = ay + hy * (gx[j] + 1.0);
+                    double w = kernel_w(kp, dx * dx + dy * dy);
+                    double z = gauss2(min_image(x - dx - x0, L), min_image(y - dy - y0, L), sigma) + c;
+                    acc += hx * hy * gw[i] * gw[j] * w * z;
+                }
+            }
+        }
+    return acc;
+}
+
+/* u*(t, x) and gamma of kind 2 at one node (x, y). */
+static void mms_flat_point(const or_forcing *F, const or_kernel *kp, double x, double y, double t, double beta,
+                           double theta, double *us, double *gam) {
+    const double L = kp->period, s = F->sigma;
+    double x0 = F->radius * cos(t), y0 = F->radius * sin(t);
+    double dx = min_image(x - x0, L), dy = min_image(y - y0, L);
+    double G = gauss2(dx, dy, s), z = G + F->c;
+    double dz = G * (dx * (-F->radius * sin(t)) + dy * (F->radius * cos(t))) / (s * s);
+    *us = theta + log(z / (1.0 - z)) / beta;
+    if (gam) *gam = dz / (beta * z * (1.0 - z)) + *us - F->scale * conv_window(kp, x, y, x0, y0, s, F->c);
+}
+
+void or_mms_flat_solution(const double *X, int64_t n, double t, const double *kpar, double radius, double sigma,
+                          double c, double beta, double theta, double *u) {
+    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3], kpar[4]};
+    or_forcing F = {2, c, 0, 0, 0, 0, radius, sigma, 1.0};
+    for (int64_t i = 0; i < n; ++i) mms_flat_point(&F, &kp, X[3 * i], X[3 * i + 1], t, beta, theta, &u[i], NULL);
+}
+
+void or_mms_flat_forcing(const double *X, int64_t n, double t, const double *kpar, double radius, double sigma,
+                         double c, double scale, double beta, double theta, double *gam) {
+    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3], kpar[4]};
+    or_forcing F = {2, c, 0, 0, 0, 0, radius, sigma, scale};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double us;
+        mms_flat_point(&F, &kp, X[3 * i], X[3 * i + 1], t, beta, theta, &us, &gam[i]);
+    }
+}
+
+static void forcing_eval(const or_forcing *F, const or_kernel *kp, const double *X, int64_t n, double t, double beta,
+                         double theta, double *gam) {
     if (!F || F->kind == 0) {
         for (int64_t i = 0; i < n; ++i) gam[i] = 0.0;
+        return;
+    }
+    if (F->kind == 2) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double us;
+            mms_flat_point(F, kp, X[3 * i], X[3 * i + 1], t, beta, theta, &us, &gam[i]);
+        }
         return;
     }
     double a = F->a0 * cos(t), da = -F->a0 * sin(t);
@@ -609,7 +738,7 @@ static void gauss_legendre(int N, double *x, double *w) {
  * by composite Gauss-Legendre quadrature (panels refined toward t = 1 where the
  * Gaussians concentrate). */
 void or_mms_sphere_eigs(const double *kpar, double *lam) {
-    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3]};
+    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3], kpar[4]};
     enum { NG = 20, NPAN = 400 };
     double gx[NG], gw[NG];
     gauss_legendre(NG, gx, gw);
@@ -648,7 +777,8 @@ static void vector_field(const double *X, const double *q, int64_t n, const doub
     or_nonlocal(X, q, n, U, B, kpar, beta, theta, NULL, 0, K);
     double *gam = (double *)malloc(sizeof(double) * (size_t)n);
     for (int b = 0; b < B; ++b) {
-        forcing_eval(F, X, n, t, beta[b], theta[b], gam);
+        or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3], kpar[4]};
+        forcing_eval(F, &kp, X, n, t, beta[b], theta[b], gam);
         for (int64_t i = 0; i < n; ++i) K[b * n + i] = -U[b * n + i] + K[b * n + i] + gam[i];
     }
     free(gam);
@@ -661,8 +791,12 @@ static void vector_field(const double *X, const double *q, int64_t n, const doub
 void or_rk4(const double *X, const double *q, int64_t n, double *u, int B, double t0, double dt, int nsteps,
             const double *kpar, const double *beta, const double *theta, const double *forcing,
             double *stages) {
-    or_forcing F = {0, 0, 0, 0, 0, 0};
-    if (forcing) { F.kind = (int)forcing[0]; F.c = forcing[1]; F.a0 = forcing[2]; F.lam0 = forcing[3]; F.lam1 = forcing[4]; F.lam2 = forcing[5]; }
+    or_forcing F = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (forcing) {
+        F.kind = (int)forcing[0];
+        if (F.kind == 2) { F.c = forcing[1]; F.radius = forcing[2]; F.sigma = forcing[3]; F.scale = forcing[4]; }
+        else { F.c = forcing[1]; F.a0 = forcing[2]; F.lam0 = forcing[3]; F.lam1 = forcing[4]; F.lam2 = forcing[5]; }
+    }
     size_t sz = (size_t)(n * B);
     double *k1 = malloc(sizeof(double) * sz), *k2 = malloc(sizeof(double) * sz), *k3 = malloc(sizeof(double) * sz),
            *k4 = malloc(sizeof(double) * sz), *U = malloc(sizeof(double) * sz);
@@ -702,7 +836,7 @@ void or_rk4(const double *X, const double *q, int64_t n, double *u, int B, doubl
  * ============================================================================== */
 static void adj_stage(const double *X, const double *q, int64_t n, const double *U, const double *nu, int B,
                       const double *kpar, const double *beta, const double *theta, double *mu, double *gk) {
-    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3]};
+    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3], kpar[4]};
     double is1 = 1.0 / (kp.s1 * kp.s1), is2 = 1.0 / (kp.s2 * kp.s2);
     double *g = malloc(sizeof(double) * (size_t)n), *fp = malloc(sizeof(double) * (size_t)n);
     for (int b = 0; b < B; ++b) {
@@ -716,7 +850,7 @@ static void adj_stage(const double *X, const double *q, int64_t n, const double 
         for (int64_t i = 0; i < n; ++i) {
             double Wnu = 0, E1 = 0, R1 = 0, E2 = 0, R2 = 0;
             for (int64_t j = 0; j < n; ++j) {
-                double r2 = pair_r2(X, i, j);
+                double r2 = pair_r2p(X, i, j, kp.period);
                 double e1 = exp(-r2 * is1), e2 = exp(-r2 * is2);
                 Wnu += (kp.A1 * e1 - kp.A2 * e2) * nu[b * n + j];
                 E1 += e1 * g[j];
@@ -816,7 +950,7 @@ double or_rate(const double *model, double u, double beta, double theta) {
 static void model_field(const double *X, const double *mu, int64_t n, const double *u, const double *s, int B,
                         const double *kpar, const double *beta, const double *theta, const double *model,
                         double *Fu, double *Fs) {
-    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3]};
+    or_kernel kp = {kpar[0], kpar[1], kpar[2], kpar[3], kpar[4]};
     int kind = (int)model[0];
     double *g = (double *)malloc(sizeof(double) * (size_t)(n * B));
     for (int b = 0; b < B; ++b)
@@ -829,7 +963,7 @@ static void model_field(const double *X, const double *mu, int64_t n, const doub
     for (int64_t i = 0; i < n; ++i)
         for (int b = 0; b < B; ++b) {
             double acc = 0.0;
-            for (int64_t j = 0; j < n; ++j) acc += kernel_w(&kp, pair_r2(X, i, j)) * g[b * n + j];
+            for (int64_t j = 0; j < n; ++j) acc += kernel_w(&kp, pair_r2p(X, i, j, kp.period)) * g[b * n + j];
             Fu[b * n + i] = -u[b * n + i] + acc;
         }
     free(g);
