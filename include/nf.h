@@ -106,9 +106,14 @@ NF_API nf_status nf_quad_weights(const double *nodes, const double *normals, int
  *     w(r) = A1 exp(-r^2 / s1^2) - A2 exp(-r^2 / s2^2),   r = |x_i - x_j| (Euclidean,
  * chord distance on surfaces).  Firing rate §4 Eq. (4.4):
  *     f(u) = 1 / (1 + exp(-beta (u - theta))), per-trajectory beta, theta.
+ * period = L > 0 takes r as the doubly periodic distance of §4, Eq. (dist), on the flat
+ * square of side L: the x and y differences are reduced to their nearest images
+ * (|dx|, |dy| <= L/2), z differences are not.  Nodes may lie anywhere; the square's
+ * flat-torus metric is the same for every cell.  period = 0: Euclidean.
  * ---------------------------------------------------------------------------- */
 typedef struct {
     float A1, s1, A2, s2;
+    float period;
 } nf_kernel;
 
 typedef enum {
@@ -207,12 +212,23 @@ NF_API nf_status nf_nonlocal_apply_noalloc(const float *x, const float *q, int64
  *      z = c + a(t) (Y1 + Y2),  a(t) = a0 cos t,  u* = theta + ln(z / (1 - z)) / beta,
  *      gamma = d(u*)/dt + u* - [lam0 c + a(t) (lam1 Y1 + lam2 Y2)],
  *    so that f(u*) = z solves the continuous problem exactly.  Y1, Y2: n FP32 device. */
-enum { NF_FORCE_NONE = 0, NF_FORCE_MMS_EIGEN = 1 };
+/*  NF_FORCE_MMS_FLAT: the manufactured solution of the convergence study on the square,
+ *    §4.3 (and, with scale = r, on the torus of §4.4 in its (phi, theta) coordinates), on
+ *    the operator's periodic square (kernel period L > 0; nodes' x, y are the square's
+ *    coordinates):
+ *      z = G(x, x0(t); sigma) + c,  x0(t) = radius (cos t, sin t),
+ *      G(x, y; s) = exp(-dist^2(x, y) / (2 s^2)) / (2 pi s^2),  u* = theta + ln(z / (1 - z)) / beta,
+ *      gamma = d(u*)/dt + u* - scale * int_cell w(dist(x, y)) z(t, y) dy,
+ *    the integral in closed form (w and G are products of one-dimensional Gaussians; each
+ *    factor splits where the nearest image of x0 changes and integrates with erf).
+ *    Fields used: c, radius, sigma, scale; Y1, Y2 unused. */
+enum { NF_FORCE_NONE = 0, NF_FORCE_MMS_EIGEN = 1, NF_FORCE_MMS_FLAT = 2 };
 typedef struct {
     int kind;
     const float *Y1;
     const float *Y2;
     double c, a0, lam0, lam1, lam2;
+    double radius, sigma, scale;
 } nf_forcing;
 
 /* Funk-Hecke eigenvalues lam_l, l = 0, 1, 2, of the kernel w on the unit sphere

@@ -31,10 +31,11 @@ __all__ = [
     "NFError", "lib", "build", "nf_build_stencils", "nf_quad_weights", "Operator", "nf_nonlocal_apply",
     "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
     "DENSE_BF16X2", "DENSE_SYM_FP32", "STATUS", "nf_field_advance", "MODEL_FIELD", "MODEL_DEPRESSION",
-    "RATE_SIGMOID", "RATE_SMOOTHSTEP",
+    "RATE_SIGMOID", "RATE_SMOOTHSTEP", "FORCE_NONE", "FORCE_MMS_EIGEN", "FORCE_MMS_FLAT",
 ]
 
 MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32 = 0, 1, 2, 4
+FORCE_NONE, FORCE_MMS_EIGEN, FORCE_MMS_FLAT = 0, 1, 2
 STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINITE", 4: "NF_ERR_TIMEOUT",
           5: "NF_ERR_NOMEM", 6: "NF_ERR_CUDA", 7: "NF_ERR_UNSUPPORTED"}
 
@@ -54,7 +55,7 @@ class NFError(RuntimeError):
 
 
 class _Kernel(C.Structure):
-    _fields_ = [("A1", C.c_float), ("s1", C.c_float), ("A2", C.c_float), ("s2", C.c_float)]
+    _fields_ = [("A1", C.c_float), ("s1", C.c_float), ("A2", C.c_float), ("s2", C.c_float), ("period", C.c_float)]
 
 
 class _Model(C.Structure):
@@ -64,7 +65,8 @@ class _Model(C.Structure):
 
 class _Forcing(C.Structure):
     _fields_ = [("kind", C.c_int), ("Y1", C.c_void_p), ("Y2", C.c_void_p), ("c", C.c_double),
-                ("a0", C.c_double), ("lam0", C.c_double), ("lam1", C.c_double), ("lam2", C.c_double)]
+                ("a0", C.c_double), ("lam0", C.c_double), ("lam1", C.c_double), ("lam2", C.c_double),
+                ("radius", C.c_double), ("sigma", C.c_double), ("scale", C.c_double)]
 
 
 _lib = None
@@ -134,8 +136,14 @@ def _dptr(t: torch.Tensor, dtype: torch.dtype, name: str):
 
 
 def _kernel(kp) -> _Kernel:
-    A1, s1, A2, s2 = (float(v) for v in kp)
-    return _Kernel(A1, s1, A2, s2)
+    """(A1, s1, A2, s2) or (A1, s1, A2, s2, period); period L > 0: doubly periodic distance
+    on the square of side L (x and y differences to their nearest images)."""
+    v = [float(x) for x in kp]
+    if len(v) == 4:
+        v.append(0.0)
+    if len(v) != 5:
+        raise ValueError("kernel must be (A1, s1, A2, s2[, period])")
+    return _Kernel(*v)
 
 
 # ------------------------------------------------------------------------ §3.1-3.3
@@ -168,15 +176,23 @@ def nf_quad_weights(nodes: torch.Tensor, tris: torch.Tensor, stencils: torch.Ten
 # ------------------------------------------------------------------------ operator
 
 class Forcing:
-    """Forcing descriptor: kind 0 (none) or 1 (manufactured, two eigenfunctions)."""
+    """Forcing descriptor: kind 0 (none), 1 (manufactured, two eigenfunctions) or 2 (the
+    moving-Gaussian manufactured solution on the periodic square: c, radius, sigma, scale)."""
 
-    def __init__(self, kind=0, Y1=None, Y2=None, c=0.0, a0=0.0, lam=(0.0, 0.0, 0.0)):
+    def __init__(self, kind=0, Y1=None, Y2=None, c=0.0, a0=0.0, lam=(0.0, 0.0, 0.0), radius=0.0, sigma=0.0,
+                 scale=1.0):
         self.kind, self.Y1, self.Y2, self.c, self.a0, self.lam = kind, Y1, Y2, c, a0, tuple(lam)
+        self.radius, self.sigma, self.scale = radius, sigma, scale
+
+    @classmethod
+    def flat(cls, c=0.1, radius=0.2, sigma=1.1, scale=1.0):
+        return cls(FORCE_MMS_FLAT, c=c, radius=radius, sigma=sigma, scale=scale)
 
     def _struct(self):
         y1 = _dptr(self.Y1, torch.float32, "Y1").value if self.Y1 is not None else None
         y2 = _dptr(self.Y2, torch.float32, "Y2").value if self.Y2 is not None else None
-        return _Forcing(int(self.kind), y1, y2, float(self.c), float(self.a0), *(float(v) for v in self.lam))
+        return _Forcing(int(self.kind), y1, y2, float(self.c), float(self.a0), *(float(v) for v in self.lam),
+                        float(self.radius), float(self.sigma), float(self.scale))
 
 
 class Operator:

@@ -156,7 +156,7 @@ void destroy_graphs(nf_operator *op) {
 
 static bool same_forcing(const nf_forcing &a, const nf_forcing &b) {
     return a.kind == b.kind && a.Y1 == b.Y1 && a.Y2 == b.Y2 && a.c == b.c && a.a0 == b.a0 && a.lam0 == b.lam0 &&
-           a.lam1 == b.lam1 && a.lam2 == b.lam2;
+           a.lam1 == b.lam1 && a.lam2 == b.lam2 && a.radius == b.radius && a.sigma == b.sigma && a.scale == b.scale;
 }
 
 // One RK4 step = 4 x (nonlocal partial sums, fused stage kernel), captured once.
@@ -244,14 +244,21 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
     return NF_OK;
 }
 
-static nf_status check_forcing(const nf_forcing *g, const nf_forcing **out) {
+static nf_status check_forcing(const nf_operator *op, const nf_forcing *g, const nf_forcing **out) {
     static const nf_forcing none{NF_FORCE_NONE, nullptr, nullptr, 0, 0, 0, 0, 0};
     if (!g) {
         *out = &none;
         return NF_OK;
     }
-    NF_ARG(g->kind == NF_FORCE_NONE || g->kind == NF_FORCE_MMS_EIGEN, "unknown forcing kind %d", g->kind);
+    NF_ARG(g->kind == NF_FORCE_NONE || g->kind == NF_FORCE_MMS_EIGEN || g->kind == NF_FORCE_MMS_FLAT,
+           "unknown forcing kind %d", g->kind);
     if (g->kind == NF_FORCE_MMS_EIGEN) NF_ARG(g->Y1 && g->Y2, "forcing: Y1 and Y2 are required");
+    if (g->kind == NF_FORCE_MMS_FLAT) {
+        NF_ARG(op->kp.period > 0.f, "flat manufactured forcing needs a periodic kernel (period > 0)");
+        NF_ARG(g->sigma > 0.0 && g->c > 0.0 && g->c + 1.0 / (2.0 * 3.14159265358979323846 * g->sigma * g->sigma) < 1.0,
+               "flat manufactured forcing: need sigma > 0 and 0 < c, c + 1/(2 pi sigma^2) < 1 (z in (0, 1))");
+        NF_ARG(std::isfinite(g->radius) && std::isfinite(g->scale), "flat manufactured forcing: radius, scale finite");
+    }
     *out = g;
     return NF_OK;
 }
@@ -278,6 +285,7 @@ nf_status nf_operator_create(const float *x, const float *q, int64_t n, nf_kerne
     NF_ARG(std::isfinite(kp.A1) && std::isfinite(kp.A2) && kp.s1 > 0.f && kp.s2 > 0.f && std::isfinite(kp.s1) &&
                std::isfinite(kp.s2),
            "kernel parameters must be finite with s1, s2 > 0");
+    NF_ARG(std::isfinite(kp.period) && kp.period >= 0.f, "period must be finite and >= 0");
     cudaStream_t s = as_stream(stream);
     NF_TRY(mf_init_attrs());
     nf_operator *op = new nf_operator();
@@ -395,7 +403,7 @@ nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt,
     NF_ARG(std::isfinite(t0) && std::isfinite(dt), "t0 and dt must be finite");
     NF_ARG(!ckpt || C >= 1, "checkpoint interval C must be >= 1");
     const nf_forcing *F = nullptr;
-    NF_TRY(check_forcing(g, &F));
+    NF_TRY(check_forcing(op, g, &F));
     cudaStream_t s = as_stream(stream);
     if (op->path == NF_GROUPED) {
         NF_ARG(B == group_traj_total(op), "grouped operator: B = %d must equal the group's %d trajectories", B,

@@ -29,25 +29,36 @@ __device__ __forceinline__ float mexhat(float r2, float A1, float is1, float A2,
     return A1 * expf(-r2 * is1) - A2 * expf(-r2 * is2);
 }
 
+// Squared distance; per > 0: x and y differences reduced to their nearest images (§4,
+// Eq. (dist)), ip = 1 / per.
+__device__ __forceinline__ float pair_r2(float4 a, float4 b, float per, float ip) {
+    float dx = a.x - b.x, dy = a.y - b.y;
+    const float dz = a.z - b.z;
+    if (per > 0.f) {
+        dx = wrap1(dx, per, ip);
+        dy = wrap1(dy, per, ip);
+    }
+    return dx * dx + dy * dy + dz * dz;
+}
+
 // one block per row i; FP32 plane
 __global__ void dense_build_fp32_kernel(const float4 *__restrict__ x4, const float *__restrict__ q, int64_t n,
-                                        int64_t n_pad, float A1, float is1, float A2, float is2,
-                                        float *__restrict__ W) {
+                                        int64_t n_pad, float A1, float is1, float A2, float is2, float per,
+                                        float ip, float *__restrict__ W) {
     const int64_t i = blockIdx.x;
     const float4 xi = x4[i];
     float *row = W + i * n_pad;
     for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x) {
         const float4 xj = x4[j];
-        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r2 = pair_r2(xi, xj, per, ip);
         row[j] = mexhat(r2, A1, is1, A2, is2) * q[j];
     }
 }
 
 // one block per row: row scale s_i (power of two), then hi / lo planes
 __global__ void dense_build_bf16x2_kernel(const float4 *__restrict__ x4, const float *__restrict__ q, int64_t n,
-                                          int64_t n_pad, float A1, float is1, float A2, float is2,
-                                          uint16_t *__restrict__ Whi, uint16_t *__restrict__ Wlo,
+                                          int64_t n_pad, float A1, float is1, float A2, float is2, float per,
+                                          float ip, uint16_t *__restrict__ Whi, uint16_t *__restrict__ Wlo,
                                           float *__restrict__ rs) {
     __shared__ float red[32];
     const int64_t i = blockIdx.x;
@@ -55,8 +66,7 @@ __global__ void dense_build_bf16x2_kernel(const float4 *__restrict__ x4, const f
     float mx = 0.f;
     for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x) {
         const float4 xj = x4[j];
-        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r2 = pair_r2(xi, xj, per, ip);
         mx = fmaxf(mx, fabsf(mexhat(r2, A1, is1, A2, is2) * q[j]));
     }
 #pragma unroll
@@ -82,8 +92,7 @@ __global__ void dense_build_bf16x2_kernel(const float4 *__restrict__ x4, const f
     if (threadIdx.x == 0) rs[i] = s;
     for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x) {
         const float4 xj = x4[j];
-        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r2 = pair_r2(xi, xj, per, ip);
         const float v = mexhat(r2, A1, is1, A2, is2) * q[j] * inv;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
@@ -109,7 +118,7 @@ __device__ __forceinline__ void sym_block_pair(int64_t t, int &I, int &J) {
 
 // grid (pairs, SB / 16): each block writes 16 rows of one block pair
 __global__ void dense_build_sym_kernel(const float4 *__restrict__ x4, float A1, float is1, float A2, float is2,
-                                       float *__restrict__ K) {
+                                       float per, float ip, float *__restrict__ K) {
     int I, J;
     sym_block_pair(blockIdx.x, I, J);
     float *blk = K + (int64_t)blockIdx.x * SB * SB;
@@ -118,8 +127,7 @@ __global__ void dense_build_sym_kernel(const float4 *__restrict__ x4, float A1, 
         const float4 xi = x4[(int64_t)I * SB + r];
         for (int c = threadIdx.x; c < SB; c += blockDim.x) {
             const float4 xj = x4[(int64_t)J * SB + c];
-            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float r2 = pair_r2(xi, xj, per, ip);
             blk[(int64_t)r * SB + c] = mexhat(r2, A1, is1, A2, is2);
         }
     }
@@ -128,16 +136,17 @@ __global__ void dense_build_sym_kernel(const float4 *__restrict__ x4, float A1, 
 nf_status launch_dense_build(nf_operator *op, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float is1 = 1.f / (k.s1 * k.s1), is2 = 1.f / (k.s2 * k.s2);
+    const float per = k.period > 0.f ? k.period : 0.f, ip = per > 0.f ? 1.f / per : 0.f;
     if (op->path == NF_DENSE_SYM_FP32) {
         const int64_t nb = op->n_pad / SB;
         dense_build_sym_kernel<<<dim3((unsigned)(nb * (nb + 1) / 2), SB / 16), 256, 0, s>>>(op->x4, k.A1, is1, k.A2,
-                                                                                       is2, op->W32);
+                                                                                       is2, per, ip, op->W32);
     } else if (op->path == NF_DENSE_FP32) {
         dense_build_fp32_kernel<<<(unsigned)op->n_pad, 256, 0, s>>>(op->x4, op->q, op->n, op->n_pad, k.A1, is1, k.A2,
-                                                               is2, op->W32);
+                                                               is2, per, ip, op->W32);
     } else {
         dense_build_bf16x2_kernel<<<(unsigned)op->n_pad, 256, 0, s>>>(op->x4, op->q, op->n, op->n_pad, k.A1, is1,
-                                                                 k.A2, is2, op->Whi, op->Wlo, op->rs);
+                                                                 k.A2, is2, per, ip, op->Whi, op->Wlo, op->rs);
     }
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;

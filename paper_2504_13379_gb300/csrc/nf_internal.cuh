@@ -123,6 +123,22 @@ __device__ __forceinline__ float ex2_sfu(float x) {
     return y;
 }
 
+// Doubly periodic distance (§4, Eq. (dist)) on the square of side p: a coordinate
+// difference d becomes its nearest image d - p rint(d / p).  rint by adding and removing
+// 1.5 * 2^23 (round to nearest even, exact while |d / p| < 2^22), so it stays on the FMA
+// pipe.  ip = 1 / p.
+constexpr float kRintMagic = 12582912.0f;
+__device__ __forceinline__ float wrap1(float d, float p, float ip) {
+    const float t = __fsub_rn(__fmaf_rn(d, ip, kRintMagic), kRintMagic);
+    return __fmaf_rn(-p, t, d);
+}
+
+// Tag selecting the periodic variant of a pair loop at compile time.
+template <bool P>
+struct PerTag {
+    static constexpr bool value = P;
+};
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -38,9 +38,10 @@ struct MfSmem {
 template <int NB, int R>
 __global__ void __launch_bounds__(MF_THREADS)
 mf_pair_kernel(const float4 *__restrict__ x4, const float *__restrict__ g, int64_t n_pad, int B, int b_base,
-               int64_t jchunk, float c1, float c2, float A1, float A2, float *__restrict__ partial,
+               int64_t jchunk, float c1, float c2, float A1, float A2, float per, float *__restrict__ partial,
                int *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    const float iper = per > 0.f ? 1.f / per : 0.f;
     MfSmem<NB> &sm = *reinterpret_cast<MfSmem<NB> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int split = blockIdx.y;
@@ -98,6 +99,8 @@ mf_pair_kernel(const float4 *__restrict__ x4, const float *__restrict__ g, int64
         }
         if (tid == 0 && t >= 1 && t + 1 < ntiles) issue(t + 1);
         const float4 *xs = sm.xs[buf];
+        auto sweep = [&](auto tag) {
+            constexpr bool P = decltype(tag)::value;
 #pragma unroll 4
         for (int jj = lane; jj < MF_TJ; jj += 32) {
             const float4 xj = xs[jj];
@@ -106,7 +109,12 @@ mf_pair_kernel(const float4 *__restrict__ x4, const float *__restrict__ g, int64
             for (int b = 0; b < NB; ++b) gb[b] = sm.gs[buf][b][jj];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const float dx = xi[r] - xj.x, dy = yi[r] - xj.y, dz = zi[r] - xj.z;
+                float dx = xi[r] - xj.x, dy = yi[r] - xj.y;
+                const float dz = zi[r] - xj.z;
+                if constexpr (P) {
+                    dx = wrap1(dx, per, iper);
+                    dy = wrap1(dy, per, iper);
+                }
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 const float e1 = ex2_sfu(r2 * c1);
                 const float e2 = ex2_sfu(r2 * c2);
@@ -120,6 +128,11 @@ mf_pair_kernel(const float4 *__restrict__ x4, const float *__restrict__ g, int64
                 }
             }
         }
+        };
+        if (per > 0.f)
+            sweep(PerTag<true>{});
+        else
+            sweep(PerTag<false>{});
     }
     if (timed_out) {
         if (tid == 0) set_dev_error(err, DEV_TIMEOUT);
@@ -182,6 +195,12 @@ __device__ __forceinline__ u64 f2_ex2(u64 a) {
     return f2_pack(ex2_sfu(lo), ex2_sfu(hi));
 }
 
+// Nearest image of a packed pair of coordinate differences (see wrap1): ip = 1/p, np = -p,
+// mg = the rounding constant, each in both halves.
+__device__ __forceinline__ u64 f2_wrap(u64 d, u64 ip, u64 np, u64 mg) {
+    return f2_fma(f2_sub(f2_fma(d, ip, mg), mg), np, d);
+}
+
 template <int TJ>
 struct MfPackedSmem {
     float xs[2][TJ], ys[2][TJ], zs[2][TJ], gs[2][TJ];
@@ -219,7 +238,7 @@ template <int R, int TJ, int M>
 __global__ void __launch_bounds__(MF_THREADS, R >= 8 ? 2 : 4)
 mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
                       int64_t n_pad, int B, int b_base, int64_t jchunk, float k2, float A1, float A2,
-                      float *__restrict__ partial, int *__restrict__ err) {
+                      float per, float *__restrict__ partial, int *__restrict__ err) {
     static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
     __shared__ __align__(128) MfPackedSmem<TJ> sm;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -271,7 +290,8 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
         const float dx = xr[r] - cx, dy = yr[r] - cy, dz = zr[r] - cz;
         spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
     }
-    const bool local = spread <= kMfLocalSpread;  // warp-uniform
+    // warp-uniform; periodic distances take the difference form (nearest images per pair)
+    const bool local = spread <= kMfLocalSpread && !(per > 0.f);
     // local: xi, yi, zi hold -2 (x_i - c) (times s1/s2 when M > 0); otherwise x_i itself
     // (both halves of the pair)
     const float sk = M > 0 ? sqrtf(k2) : 1.f;
@@ -292,6 +312,8 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
     // e1 = 2^(-r2s), e2 = 2^(-k2 r2s) with k2 = s1^2 / s2^2
     const u64 nk2 = f2_pack(-k2, -k2);
     const u64 cxp = f2_pack(cx, cx), cyp = f2_pack(cy, cy), czp = f2_pack(cz, cz), skp = f2_pack(sk, sk);
+    const float iper = per > 0.f ? 1.f / per : 0.f;
+    const u64 ipp = f2_pack(iper, iper), npp = f2_pack(-per, -per), mgp = f2_pack(kRintMagic, kRintMagic);
     bool timed_out = false;
     for (int t = 0; t < ntiles; ++t) {
         const int buf = t & 1;
@@ -342,12 +364,19 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
                 }
             }
         } else {
+            auto sweep = [&](auto tag) {
+                constexpr bool P = decltype(tag)::value;
 #pragma unroll 2
             for (int jp = lane; jp < TJ / 2; jp += 32) {
                 const u64 xj = xs[jp], yj = ys[jp], zj = zs[jp], gj = gs[jp];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj), dz = f2_sub(zi[r], zj);
+                    u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj);
+                    const u64 dz = f2_sub(zi[r], zj);
+                    if constexpr (P) {
+                        dx = f2_wrap(dx, ipp, npp, mgp);
+                        dy = f2_wrap(dy, ipp, npp, mgp);
+                    }
                     const u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
                     float s0, s1v;
                     f2_unpack(r2s, s0, s1v);
@@ -357,6 +386,11 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
                     a2[r] = f2_fma(e2, gj, a2[r]);
                 }
             }
+            };
+            if (per > 0.f)
+                sweep(PerTag<true>{});
+            else
+                sweep(PerTag<false>{});
         }
     }
     if (timed_out) {
@@ -449,7 +483,8 @@ __device__ __forceinline__ float warp_reduce_rows(float (&v)[R], int lane, int &
 template <int R, int M>
 __global__ void __launch_bounds__(MS_THREADS, 2)
 mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
-              int64_t n_pad, int B, int b_base, float k2, float A1, float A2, float *__restrict__ partial) {
+              int64_t n_pad, int B, int b_base, float k2, float A1, float A2, float per,
+              float *__restrict__ partial) {
     static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
     static_assert(R == 4 || R == 8, "rows per warp");
     constexpr int NPASS = MS_BLK / R;
@@ -489,10 +524,20 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     }
     for (int k = tid; k < MS_WARPS * MS_BLK; k += MS_THREADS) colacc[k] = 0.f;
     __syncthreads();
-    // one thread per pass: centre of the pass's R rows, the form, and the row operands:
-    // expanded form -2 (x_i - c), else x_i; f1, f2 the row factors
-    // 2^(-n_i) of e1 and e2 (1 in the difference form); h1 = A1 f1 g_i and h2 = -A2 f2 g_i
-    // weight the row's terms in the column sums
+    // period in the units of the gathered coordinates (times sk)
+    const float pers = per * sk, ipers = per > 0.f ? 1.f / pers : 0.f;
+    // exponent of the wider Gaussian per unit of r^2 in these units
+    const float wide = M > 0 ? 1.f : fminf(1.f, k2);
+    // one thread per pass: centre of the pass's R rows, the form, and the row operands.
+    // Forms: 1 expanded about c (rows -2 (x_i - c)); 0 differences (rows x_i); periodic
+    // kernels: 2 differences of centred coordinates (rows x_i - c), and in forms 1 and 2 the
+    // columns taken at their nearest image of c.  That image is the pair's nearest image
+    // unless the column lies within e (the rows' distance from c) of c's antipodal lines;
+    // such a pair is at least L/2 - e apart in both images, and when the wider Gaussian's
+    // exponent there exceeds 160 (log2 units) both images give exactly 0 (ex2 flushes
+    // below 2^-126).  Otherwise form 3: centred differences reduced to their nearest image
+    // pair by pair.  f1, f2 are the row factors 2^(-n_i) of e1 and e2 (1 outside form 1);
+    // h1 = A1 f1 g_i and h2 = -A2 f2 g_i weight the row's terms in the column sums.
     for (int ps = tid; ps < NPASS; ps += MS_THREADS) {
         const int r0 = ps * R;
         float lox = 3.4e38f, loy = 3.4e38f, loz = 3.4e38f, hix = -3.4e38f, hiy = -3.4e38f, hiz = -3.4e38f;
@@ -509,15 +554,26 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
             const float dx = rmx[r0 + r] - cx, dy = rmy[r0 + r] - cy, dz = rmz[r0 + r] - cz;
             spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
         }
-        const bool local = spread <= kMfLocalSpread * sk * sk;  // the threshold in units of s1
-        pc[ps] = make_float4(cx, cy, cz, local ? 1.f : 0.f);
+        bool local = spread <= kMfLocalSpread * sk * sk;  // the threshold in units of s1
+        int form = local ? 1 : 0;
+        if (per > 0.f) {
+            const float m = 0.5f * pers - sqrtf(spread);
+            if (m > 0.f && wide * m * m >= 160.f) {
+                form = local ? 1 : 2;
+            } else {
+                form = 3;
+                local = false;
+            }
+        }
+        pc[ps] = make_float4(cx, cy, cz, (float)form);
+        const bool centred = form >= 2;
         const float lsc = -2.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int k = r0 + r;
-            const float x = local ? lsc * (rmx[k] - cx) : rmx[k];
-            const float y = local ? lsc * (rmy[k] - cy) : rmy[k];
-            const float z = local ? lsc * (rmz[k] - cz) : rmz[k];
+            const float x = local ? lsc * (rmx[k] - cx) : (centred ? rmx[k] - cx : rmx[k]);
+            const float y = local ? lsc * (rmy[k] - cy) : (centred ? rmy[k] - cy : rmy[k]);
+            const float z = local ? lsc * (rmz[k] - cz) : rmz[k];  // z never wraps
             const float ni = 0.25f * (x * x + y * y + z * z);  // n_i, in units of s2 when M > 0
             const float f1 = local ? exp2f(M > 0 ? -(float)M * ni : -ni) : 1.f;
             const float f2 = local ? exp2f(M > 0 ? -ni : -k2 * ni) : 1.f;
@@ -533,6 +589,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     }
     __syncthreads();
     const u64 nk2 = f2_pack(-k2, -k2);
+    const u64 ipp = f2_pack(ipers, ipers), npp = f2_pack(-pers, -pers), mgp = f2_pack(kRintMagic, kRintMagic);
     const float4 *xs4 = reinterpret_cast<const float4 *>(xs), *ys4 = reinterpret_cast<const float4 *>(ys);
     const float4 *zs4 = reinterpret_cast<const float4 *>(zs), *gs4 = reinterpret_cast<const float4 *>(gs);
     float4 *cw4 = reinterpret_cast<float4 *>(colacc + warp * MS_BLK);
@@ -556,7 +613,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     for (int ps = warp; ps < NPASS; ps += MS_WARPS) {
         const int r0 = ps * R;
         const float4 c = pc[ps];
-        const bool local = c.w != 0.f;  // warp-uniform
+        const int form = (int)c.w;  // warp-uniform
         u64 xi[R], yi[R], zi[R], h1[R], h2[R], a1[R], a2[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -569,14 +626,31 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
             a2[r] = 0ull;
         }
         const u64 cxp = f2_pack(c.x, c.x), cyp = f2_pack(c.y, c.y), czp = f2_pack(c.z, c.z);
-        // each lane takes 4 consecutive columns (two f32x2 pairs) per step
-        if (local) {
+        auto add_cols = [&](int q, const u64 (&cacc)[2]) {
+            if (!diag) {
+                float4 cv = cw4[q];
+                u64 c0 = f2_add(lo2(cv), cacc[0]), c1 = f2_add(hi2(cv), cacc[1]);
+                f2_unpack(c0, cv.x, cv.y);
+                f2_unpack(c1, cv.z, cv.w);
+                cw4[q] = cv;
+            }
+        };
+        // form 1: expanded about c; P: columns at their nearest image of c
+        auto sweep_local = [&](auto tag) {
+            constexpr bool P = decltype(tag)::value;
 #pragma unroll 1
             for (int q = lane; q < MS_BLK / 4; q += 32) {
                 const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
-                const u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
-                const u64 yt[2] = {f2_sub(lo2(y4), cyp), f2_sub(hi2(y4), cyp)};
+                u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
+                u64 yt[2] = {f2_sub(lo2(y4), cyp), f2_sub(hi2(y4), cyp)};
                 const u64 zt[2] = {f2_sub(lo2(z4), czp), f2_sub(hi2(z4), czp)};
+                if constexpr (P) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        xt[h] = f2_wrap(xt[h], ipp, npp, mgp);
+                        yt[h] = f2_wrap(yt[h], ipp, npp, mgp);
+                    }
+                }
                 const u64 gj[2] = {lo2(g4), hi2(g4)};
                 u64 nj[2], cacc[2] = {0ull, 0ull};
 #pragma unroll
@@ -593,26 +667,38 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                         cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
                     }
                 }
-                if (!diag) {
-                    float4 cv = cw4[q];
-                    u64 c0 = f2_add(lo2(cv), cacc[0]), c1 = f2_add(hi2(cv), cacc[1]);
-                    f2_unpack(c0, cv.x, cv.y);
-                    f2_unpack(c1, cv.z, cv.w);
-                    cw4[q] = cv;
-                }
+                add_cols(q, cacc);
             }
-        } else {
+        };
+        // forms 0, 2, 3: coordinate differences; CEN: rows centred on c and columns' x, y at
+        // their nearest image of c (forms 2, 3); PW: each pair's x, y differences reduced to
+        // their nearest image (form 3)
+        auto sweep_diff = [&](auto tag_c, auto tag_w) {
+            constexpr bool CEN = decltype(tag_c)::value, PW = decltype(tag_w)::value;
 #pragma unroll 1
             for (int q = lane; q < MS_BLK / 4; q += 32) {
                 const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
-                const u64 xj[2] = {lo2(x4), hi2(x4)}, yj[2] = {lo2(y4), hi2(y4)}, zj[2] = {lo2(z4), hi2(z4)};
+                u64 xj[2] = {lo2(x4), hi2(x4)}, yj[2] = {lo2(y4), hi2(y4)};
+                const u64 zj[2] = {lo2(z4), hi2(z4)};
+                if constexpr (CEN) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        xj[h] = f2_wrap(f2_sub(xj[h], cxp), ipp, npp, mgp);
+                        yj[h] = f2_wrap(f2_sub(yj[h], cyp), ipp, npp, mgp);
+                    }
+                }
                 const u64 gj[2] = {lo2(g4), hi2(g4)};
                 u64 cacc[2] = {0ull, 0ull};
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const u64 dx = f2_sub(xi[r], xj[h]), dy = f2_sub(yi[r], yj[h]), dz = f2_sub(zi[r], zj[h]);
+                        u64 dx = f2_sub(xi[r], xj[h]), dy = f2_sub(yi[r], yj[h]);
+                        const u64 dz = f2_sub(zi[r], zj[h]);
+                        if constexpr (PW) {
+                            dx = f2_wrap(dx, ipp, npp, mgp);
+                            dy = f2_wrap(dy, ipp, npp, mgp);
+                        }
                         const u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
                         u64 e1, e2;
                         exps(r2s, e1, e2);
@@ -621,14 +707,21 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                         cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
                     }
                 }
-                if (!diag) {
-                    float4 cv = cw4[q];
-                    u64 c0 = f2_add(lo2(cv), cacc[0]), c1 = f2_add(hi2(cv), cacc[1]);
-                    f2_unpack(c0, cv.x, cv.y);
-                    f2_unpack(c1, cv.z, cv.w);
-                    cw4[q] = cv;
-                }
+                add_cols(q, cacc);
             }
+        };
+        // each lane takes 4 consecutive columns (two f32x2 pairs) per step
+        if (form == 1) {
+            if (per > 0.f)
+                sweep_local(PerTag<true>{});
+            else
+                sweep_local(PerTag<false>{});
+        } else if (form == 0) {
+            sweep_diff(PerTag<false>{}, PerTag<false>{});
+        } else if (form == 2) {
+            sweep_diff(PerTag<true>{}, PerTag<false>{});
+        } else {
+            sweep_diff(PerTag<true>{}, PerTag<true>{});
         }
         float v[R];
 #pragma unroll
@@ -672,7 +765,7 @@ constexpr size_t AS_SMEM_FLOATS = (size_t)(5 + 14 + 1 + MS_WARPS) * MS_BLK;
 template <int R, int M>
 __global__ void __launch_bounds__(MS_THREADS, 2)
 adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all, const int *__restrict__ rowperm,
-               int64_t n_pad, int B, int b, float k2, float A1, float A2, float *__restrict__ wpart,
+               int64_t n_pad, int B, int b, float k2, float A1, float A2, float per, float *__restrict__ wpart,
                float *__restrict__ gpart) {
     static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
     static_assert(R == 2 || R == 4, "rows per warp");
@@ -733,7 +826,8 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
             spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
         }
-        const bool local = spread <= kMfLocalSpread * sk * sk;  // the threshold in units of s1
+        // the threshold in units of s1; periodic distances take the difference form
+        const bool local = spread <= kMfLocalSpread * sk * sk && !(per > 0.f);
         pc[ps] = make_float4(cx, cy, cz, local ? 1.f : 0.f);
         const float lsc = -2.f;
 #pragma unroll
@@ -754,6 +848,8 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     }
     __syncthreads();
     const u64 nk2 = f2_pack(-k2, -k2);
+    const float pers = per * sk, ipers = per > 0.f ? 1.f / pers : 0.f;
+    const u64 ipp = f2_pack(ipers, ipers), npp = f2_pack(-pers, -pers), mgp = f2_pack(kRintMagic, kRintMagic);
     const u64 *xs2 = reinterpret_cast<const u64 *>(xs), *ys2 = reinterpret_cast<const u64 *>(ys);
     const u64 *zs2 = reinterpret_cast<const u64 *>(zs), *vs2 = reinterpret_cast<const u64 *>(vs);
     const u64 *gs2 = reinterpret_cast<const u64 *>(gsm);
@@ -823,17 +919,29 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
                 if (!diag) cw2[jp] = f2_add(cw2[jp], cacc);
             }
         } else {
+            auto sweep = [&](auto tag) {
+                constexpr bool P = decltype(tag)::value;
 #pragma unroll 2
             for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
                 const u64 xj = xs2[jp], yj = ys2[jp], zj = zs2[jp], vj = vs2[jp], gj = gs2[jp];
                 u64 cacc = 0ull;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj), dz = f2_sub(zi[r], zj);
+                    u64 dx = f2_sub(xi[r], xj), dy = f2_sub(yi[r], yj);
+                    const u64 dz = f2_sub(zi[r], zj);
+                    if constexpr (P) {
+                        dx = f2_wrap(dx, ipp, npp, mgp);
+                        dy = f2_wrap(dy, ipp, npp, mgp);
+                    }
                     pair(r, f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx))), vj, gj, cacc);
                 }
                 if (!diag) cw2[jp] = f2_add(cw2[jp], cacc);
             }
+            };
+            if (per > 0.f)
+                sweep(PerTag<true>{});
+            else
+                sweep(PerTag<false>{});
         }
         float v[R];
 #pragma unroll
@@ -966,7 +1074,7 @@ static nf_status launch_mf_group(nf_operator *op, int B, int b_base, int groups,
     const float c1 = -L2E / (k.s1 * k.s1), c2 = -L2E / (k.s2 * k.s2);
     dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, (unsigned)groups);
     mf_pair_kernel<NB, R><<<grid, MF_THREADS, smem, s>>>(op->x4, op->g, op->n_pad, B, b_base, pl.jchunk, c1, c2,
-                                                         k.A1, k.A2, op->partial, op->err);
+                                                         k.A1, k.A2, k.period, op->partial, op->err);
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
 }
@@ -983,6 +1091,12 @@ struct MfVariant {
     int R, TJ;
 };
 constexpr MfVariant kMfVariants[] = {{2, 512}, {4, 512}, {4, 1024}, {8, 1024}};
+
+// The kernel's period in the units of the pre-scaled coordinates (times sqrt(log2 e) / s1,
+// as the node packing scales them); 0 for the Euclidean distance.
+static float scaled_period(const nf_kernel &k) {
+    return k.period > 0.f ? k.period * (std::sqrt(1.4426950408889634f) / k.s1) : 0.f;
+}
 
 // Integer width ratio m = s2^2 / s1^2 in {2, 3, 4} (to FP32 rounding of the k2 the kernel
 // receives), else 0: selects the one-exponential form of the packed kernel.
@@ -1016,7 +1130,8 @@ static void launch_packed(nf_operator *op, int B, int b_base, int groups, const 
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
     dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, (unsigned)groups);
 #define NF_PACKED_ARGS \
-    op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, pl.jchunk, k2, k.A1, k.A2, op->partial, op->err
+    op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, pl.jchunk, k2, k.A1, k.A2, scaled_period(k), op->partial, \
+        op->err
     switch (mf_width_ratio(k)) {
         case 2: mf_pair_packed_kernel<R, TJ, 2><<<grid, MF_THREADS, 0, s>>>(NF_PACKED_ARGS); break;
         case 3: mf_pair_packed_kernel<R, TJ, 3><<<grid, MF_THREADS, 0, s>>>(NF_PACKED_ARGS); break;
@@ -1053,7 +1168,7 @@ static void launch_sym_r(nf_operator *op, int B, int b_base, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
     dim3 grid((unsigned)sym_pairs(op), 1, 1);
-#define NF_SYM_ARGS op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, op->partial
+#define NF_SYM_ARGS op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, scaled_period(k), op->partial
     switch (mf_width_ratio(k)) {
         case 2: mf_sym_kernel<R, 2><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
         case 3: mf_sym_kernel<R, 3><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
@@ -1086,7 +1201,7 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
     *r2_phys = (float)((m > 0 ? (double)k.s2 * k.s2 : (double)k.s1 * k.s1) / L2E);
     dim3 grid((unsigned)sym_pairs(op), 1, 1);
     const size_t smem = AS_SMEM_FLOATS * sizeof(float);
-#define NF_ADJ_ARGS op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, wpart, gpart
+#define NF_ADJ_ARGS op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, scaled_period(k), wpart, gpart
     switch (m) {
         case 2: adj_sym_kernel<4, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
         case 3: adj_sym_kernel<4, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
@@ -1227,10 +1342,10 @@ nf_status launch_mf_pair_single(const float4 *x4, const float *g, int64_t n_pad,
     dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, 1);
     if (R == 4)
         mf_pair_kernel<1, 4><<<grid, MF_THREADS, sizeof(MfSmem<1>), s>>>(x4, g, n_pad, 1, 0, pl.jchunk, c1, c2, k.A1,
-                                                                      k.A2, partial, err);
+                                                                      k.A2, k.period, partial, err);
     else
         mf_pair_kernel<1, 2><<<grid, MF_THREADS, sizeof(MfSmem<1>), s>>>(x4, g, n_pad, 1, 0, pl.jchunk, c1, c2, k.A1,
-                                                                      k.A2, partial, err);
+                                                                      k.A2, k.period, partial, err);
     NF_CUDA_TRY(cudaGetLastError());
     *splits_out = pl.splits;
     return NF_OK;
@@ -1407,6 +1522,8 @@ struct StageKArgs {
     const float *rs;    // BF16X2 row scale, or null
     const float *beta, *theta;
     nf_forcing F;
+    const float4 *x4;   // node coordinates (the flat manufactured forcing)
+    nf_kernel kp;
     const double *t0;
     double dt;
     int stage;
@@ -1416,8 +1533,52 @@ struct StageKArgs {
     int C;
 };
 
-__device__ __forceinline__ double forcing_value(const nf_forcing &F, int64_t i, double t, float beta,
-                                                float theta) {
+// Flat manufactured forcing (NF_FORCE_MMS_FLAT).  One factor of the convolution term:
+//   J(a) = int_{-L/2}^{L/2} exp(-p d^2) exp(-e(d)^2 / (2 sigma^2)) dd,  e(d) = nearest image of a - d,
+// a = nearest image of x - x0 in one coordinate.  e(d) = a - d except past the point where
+// a - d leaves [-L/2, L/2] (d < a - L/2 for a >= 0, d > a + L/2 for a < 0), where it is
+// a - d -+ L.  Each piece is a Gaussian product integrated in closed form:
+//   int_{d0}^{d1} exp(-p d^2 - r (d - a')^2) dd
+//     = exp(-p r a'^2 / (p + r)) (1/2) sqrt(pi / (p + r)) [erf(k (d1 - m)) - erf(k (d0 - m))],
+// r = 1 / (2 sigma^2), m = r a' / (p + r), k = sqrt(p + r).
+constexpr double kPi = 3.14159265358979323846;
+__device__ __forceinline__ double gauss_piece(double p, double r, double a, double d0, double d1) {
+    const double s = p + r, m = r * a / s, k = sqrt(s);
+    return exp(-p * r * a * a / s) * 0.5 * sqrt(kPi / s) * (erf(k * (d1 - m)) - erf(k * (d0 - m)));
+}
+__device__ __forceinline__ double flat_factor(double a, double p, double r, double L) {
+    const double h = 0.5 * L;
+    if (a >= 0.0) return gauss_piece(p, r, a - L, -h, a - h) + gauss_piece(p, r, a, a - h, h);
+    return gauss_piece(p, r, a, -h, a + h) + gauss_piece(p, r, a + L, a + h, h);
+}
+__device__ __forceinline__ double nearest_image(double d, double L) { return d - L * rint(d / L); }
+
+__device__ __forceinline__ double forcing_value(const nf_forcing &F, const float4 *x4, const nf_kernel &kp,
+                                                int64_t i, double t, float beta, float theta) {
+    if (F.kind == NF_FORCE_MMS_FLAT) {
+        // z = G(x, x0(t); sigma) + c on the periodic square; gamma = du*/dt + u* - scale C,
+        // C = int_cell w(dist(x, y)) z(y) dy: the constant part integrates w over the
+        // displacement square, the Gaussian part is separable (flat_factor per coordinate)
+        const double L = kp.period, sg = F.sigma, r = 1.0 / (2.0 * sg * sg);
+        const double x0 = F.radius * cos(t), y0 = F.radius * sin(t);
+        const float4 xi = x4[i];
+        const double ax = nearest_image((double)xi.x - x0, L), ay = nearest_image((double)xi.y - y0, L);
+        const double G = exp(-(ax * ax + ay * ay) * r) / (2.0 * kPi * sg * sg);
+        const double z = G + F.c;
+        const double dz = G * (ax * (-F.radius * sin(t)) + ay * (F.radius * cos(t))) / (sg * sg);
+        const double us = (double)theta + log(z / (1.0 - z)) / (double)beta;
+        const double dus = dz / ((double)beta * z * (1.0 - z));
+        const double amp[2] = {(double)kp.A1, -(double)kp.A2}, wid[2] = {(double)kp.s1, (double)kp.s2};
+        double C = 0.0;
+        for (int h = 0; h < 2; ++h) {
+            if (amp[h] == 0.0) continue;
+            const double p = 1.0 / (wid[h] * wid[h]);
+            const double e = sqrt(kPi) * wid[h] * erf(0.5 * L / wid[h]);
+            C += amp[h] * (F.c * e * e + flat_factor(ax, p, r, L) * flat_factor(ay, p, r, L) /
+                                             (2.0 * kPi * sg * sg));
+        }
+        return dus + us - F.scale * C;
+    }
     if (F.kind != NF_FORCE_MMS_EIGEN) return 0.0;
     const double Y1 = F.Y1[i], Y2 = F.Y2[i];
     const double Y = Y1 + Y2;
@@ -1440,7 +1601,7 @@ __global__ void rk4_stage_kernel(StageKArgs a) {
         const double cs = (a.stage == 1) ? 0.0 : (a.stage == 4 ? 1.0 : 0.5);
         const double ts = *a.t0 + (double)step * a.dt + cs * a.dt;
         const float bb = a.beta[b], th = a.theta[b];
-        const float gam = (float)forcing_value(a.F, i, ts, bb, th);
+        const float gam = (float)forcing_value(a.F, a.x4, a.kp, i, ts, bb, th);
         const float Uv = a.U[idx], uv = a.u[idx];
         const float k = (-Uv + I) + gam;
         const float dt = (float)a.dt;
@@ -1507,6 +1668,8 @@ nf_status launch_stage(nf_operator *op, int B, const StageParams &p, cudaStream_
     a.beta = p.beta;
     a.theta = p.theta;
     a.F = p.forcing;
+    a.x4 = op->x4;
+    a.kp = op->kp;
     a.t0 = op->t0_dev;
     a.dt = p.dt;
     a.stage = p.stage;

@@ -92,6 +92,7 @@ extern "C" nf_status nf_nonlocal_apply_noalloc(const float *x, const float *q, i
     NF_ARG(n >= 1 && n <= kNoallocMaxN, "n = %lld outside 1..%lld (the fixed scratch size of this entry point)",
            (long long)n, (long long)kNoallocMaxN);
     NF_ARG(kp.s1 > 0.f && kp.s2 > 0.f, "s1, s2 must be > 0");
+    NF_ARG(std::isfinite(kp.period) && kp.period >= 0.f, "period must be finite and >= 0");
     nf_status st = NF_OK;
     unsigned char *base = scratch_address(&st);
     if (!base) return st;
