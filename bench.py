@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation section")
     ap.add_argument("--no-models", action="store_true", help="skip the §5 models section (depression, AB5)")
     ap.add_argument("--no-geometries", action="store_true", help="skip the curved-geometry weights section")
+    ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-square section")
+    ap.add_argument("--convergence", action="store_true",
+                    help="run the manufactured-solution convergence studies on the periodic square and the torus")
     ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="scale the batched node counts (profiling captures use a smaller case)")
     return ap.parse_args()
@@ -421,6 +424,137 @@ def run_geometries(dev, n=100000):
     return out
 
 
+# ------------------------------------------------------------ convergence studies (§4.3, §4.4)
+# Paper parameters: firing rate gain 5, threshold 1/2; w = Gauss(., .; 1/40) under the
+# doubly periodic distance of side 2 pi; u* = f^-1[Gauss(x, x0(t); 11/10) + 1/10],
+# x0(t) = (cos t, sin t) / 5; t in [0, 1/10]; PHS r^3, stencils of 21 nodes.
+MMS_GAIN, MMS_THRESH, MMS_T, MMS_DT = 5.0, 0.5, 0.1, 0.01
+MMS_SIGMA_W, MMS_SIGMA, MMS_C, MMS_RADIUS, MMS_K = 1.0 / 40.0, 1.1, 0.1, 0.2, 21
+TORUS_R, TORUS_r = 3.0, 1.0
+
+
+def mms_kernel():
+    """Gauss(sigma_w) as (A1, s1, A2, s2, period): A1 = 1 / (2 pi sigma_w^2), s1 = sqrt(2) sigma_w, no second
+    Gaussian (s2 = 2 s1 only selects the one-exponential form)."""
+    s1 = math.sqrt(2.0) * MMS_SIGMA_W
+    return (1.0 / (2.0 * math.pi * MMS_SIGMA_W ** 2), s1, 0.0, 2.0 * s1, 2.0 * math.pi)
+
+
+def mms_solution(xy, t):
+    """u*(t, x) on the periodic square of side 2 pi (the closed form the study measures against)."""
+    L = 2.0 * math.pi
+    d = xy - MMS_RADIUS * np.array([math.cos(t), math.sin(t)])
+    d -= L * np.round(d / L)
+    z = np.exp(-(d ** 2).sum(1) / (2 * MMS_SIGMA ** 2)) / (2 * math.pi * MMS_SIGMA ** 2) + MMS_C
+    return MMS_THRESH + np.log(z / (1.0 - z)) / MMS_GAIN
+
+
+def mms_case(geometry, n):
+    """Nodes, elements, normals, and the map to the periodic square: flat -- Halton nodes
+    with a Delaunay triangulation of [0, 2 pi]^2 (§4.3); torus -- the spiral lattice on
+    R = 3, r = 1 (§4.4), square coordinates (phi, theta), weights divided by R + r cos theta."""
+    import nodesets
+
+    if geometry == "flat":
+        ns = nodesets.square_halton(n)
+        xy = ns.coords() * (2.0 * math.pi)
+        return {"nodes": xy, "tris": ns.tris, "normals": None, "xy": xy, "qscale": np.ones(ns.n),
+                "scale": 1.0, "n": ns.n, "h": 2.0 * math.pi / math.sqrt(ns.n)}
+    ns = nodesets.torus_lattice(n, R=TORUS_R, r=TORUS_r, jitter=0.0)
+    th = ns.meta["theta"]
+    xy = np.mod(np.stack([ns.meta["phi"], th], 1), 2.0 * math.pi)
+    return {"nodes": ns.nodes, "tris": ns.tris, "normals": ns.normals, "xy": xy,
+            "qscale": 1.0 / (TORUS_R + TORUS_r * np.cos(th)), "scale": TORUS_r, "n": ns.n,
+            "h": 1.0 / math.sqrt(ns.n)}
+
+
+def mms_run(dev, geometry, n, degs):
+    """One node set: GPU stencils and weights per degree, then RK4 on the matrix-free
+    periodic path with the flat manufactured forcing; errors at T against u*."""
+    import torch
+
+    import paper_2504_13379_gb300 as nf
+
+    cs = mms_case(geometry, n)
+    nodes = torch.as_tensor(cs["nodes"], device=dev)
+    tris = torch.as_tensor(cs["tris"], device=dev)
+    normals = torch.as_tensor(cs["normals"], device=dev) if cs["normals"] is not None else None
+    st = nf.nf_build_stencils(nodes, tris, MMS_K)
+    X = np.concatenate([cs["xy"], np.zeros((cs["n"], 1))], 1).astype(np.float32)
+    x32 = torch.as_tensor(X, device=dev)
+    u0 = torch.as_tensor(mms_solution(cs["xy"], 0.0).astype(np.float32), device=dev).view(1, -1)
+    exact = mms_solution(X[:, :2].astype(np.float64), MMS_T)
+    nsteps = int(round(MMS_T / MMS_DT))
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for deg in degs:
+        try:
+            q = nf.nf_quad_weights(nodes, tris, st, deg, normals=normals)
+        except nf.NFError as e:  # e.g. a stencil on too few lattice rows for the degree
+            rows.append({"deg": deg, "n": cs["n"], "h": cs["h"], "weights": str(e)})
+            continue
+        qd = q.cpu().numpy() * cs["qscale"]
+        op = nf.Operator(x32, torch.as_tensor(qd.astype(np.float32), device=dev), mms_kernel(), nf.MATRIX_FREE)
+        F = nf.Forcing.flat(MMS_C, MMS_RADIUS, MMS_SIGMA, cs["scale"])
+        u = u0.clone()
+        nf.nf_rk4_advance(op, u, 0.0, MMS_DT, 1, MMS_GAIN, MMS_THRESH, forcing=F)  # graph capture
+        u = u0.clone()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nf.nf_rk4_advance(op, u, 0.0, MMS_DT, nsteps, MMS_GAIN, MMS_THRESH, forcing=F)
+        b.record(stream)
+        b.synchronize()
+        op.check()
+        got = u.double().cpu().numpy().ravel()
+        err = got - exact
+        w = np.abs(qd)
+        rows.append({"deg": deg, "n": cs["n"], "h": cs["h"],
+                     "rel_max_err": float(np.abs(err).max() / np.abs(exact).max()),
+                     "rel_l2_err": float(math.sqrt((w * err ** 2).sum() / (w * exact ** 2).sum())),
+                     "rk4_ms": a.elapsed_time(b), "ms_per_nonlocal_sum": a.elapsed_time(b) / (4 * nsteps)})
+        op.close()
+    return rows
+
+
+def observed_orders(rows):
+    """Least-squares slope of log(error) against log(h), per degree."""
+    out = {}
+    for deg in sorted({r["deg"] for r in rows}):
+        rs = [r for r in rows if r["deg"] == deg and "rel_l2_err" in r]
+        if len(rs) < 2:
+            continue
+        lh = np.log([r["h"] for r in rs])
+        le = np.log([r["rel_l2_err"] for r in rs])
+        out[str(deg)] = float(np.polyfit(lh, le, 1)[0])
+    return out
+
+
+def run_periodic(dev):
+    """The periodic-square path at one size: §4.3's manufactured problem on 2^17 Halton
+    nodes (degree 3), error at T and the time per nonlocal sum."""
+    r = mms_run(dev, "flat", 1 << 17, [3])[0]
+    r["workload"] = ("§4.3 manufactured solution on the periodic square of side 2 pi, Gauss(1/40) kernel, "
+                     "matrix-free periodic path, RK4 dt=0.01 to T=0.1")
+    n = r["n"]
+    r["pair_evals_per_s"] = n * n / (r["ms_per_nonlocal_sum"] * 1e-3)
+    return r
+
+
+def run_convergence(dev):
+    """§4.3 (square, degrees 2-4) and §4.4 (torus, degrees 1-3: on the regular spiral
+    lattice a 21-node stencil can lie on four lattice rows, which no degree-4 system
+    resolves) manufactured-solution studies over node counts."""
+    out = {}
+    for geometry, sizes, degs in (("flat", [1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 19], (2, 3, 4)),
+                                  ("torus", [1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20], (1, 2, 3))):
+        rows = []
+        for n in sizes:
+            rows += mms_run(dev, geometry, n, list(degs))
+        out[geometry] = {"rows": rows, "observed_order_l2": observed_orders(rows),
+                         "h": "2 pi / sqrt(n)" if geometry == "flat" else "n^(-1/2)"}
+    return out
+
+
 def run_adjoint(args, dev):
     """Differentiation workload: gradient of L = |u(T) - u_target|^2 w.r.t. the kernel
     parameters and u0 through the discrete RK4 adjoint (checkpoints every C steps)."""
@@ -627,6 +761,10 @@ def run_ours(args, rank, world, local_rank):
         line["models"] = run_models(args, dev, wl, x32, q32, u0)
     if not args.no_geometries:
         line["geometries"] = run_geometries(dev)
+    if not args.no_periodic:
+        line["periodic"] = run_periodic(dev)
+    if args.convergence:
+        line["convergence"] = run_convergence(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], acc = cpu_baseline(wl, q32.double().cpu().numpy(), args.cpu_seconds, first_sums)
         for p, e in acc.items():
