@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-models", action="store_true", help="skip the §5 models section (depression, AB5)")
     ap.add_argument("--no-geometries", action="store_true", help="skip the curved-geometry weights section")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-square section")
+    ap.add_argument("--no-configs", action="store_true", help="skip the flat and sphere configurations")
     ap.add_argument("--convergence", action="store_true",
                     help="run the manufactured-solution convergence studies on the periodic square and the torus")
     ap.add_argument("--batched-scale", type=float, default=1.0,
@@ -555,6 +556,71 @@ def run_convergence(dev):
     return out
 
 
+def run_configs(dev):
+    """The small configurations: the flat square (n = 1,500, 100 RK4 steps, the whole run
+    as one call; L2-resident, latency bound) on every single-trajectory path, and the unit
+    sphere with the manufactured forcing (n = 20,000, 200 steps) with its error against u*."""
+    import torch
+
+    import paper_2504_13379_gb300 as nf
+    from nodesets import workloads as W
+
+    stream = torch.cuda.current_stream(dev)
+
+    def whole_run(op, u0, wl, forcing=None):
+        u = u0.clone()
+        nf.nf_rk4_advance(op, u, 0.0, wl.dt, 1, float(wl.beta[0]), float(wl.theta[0]), forcing=forcing)
+        u = u0.clone()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nf.nf_rk4_advance(op, u, 0.0, wl.dt, wl.nsteps, float(wl.beta[0]), float(wl.theta[0]), forcing=forcing)
+        b.record(stream)
+        b.synchronize()
+        op.check()
+        return a.elapsed_time(b), u
+
+    out = {}
+    wl = W.flat()
+    X2 = torch.as_tensor(wl.ns.coords(), device=dev)
+    tris = torch.as_tensor(wl.ns.tris, device=dev)
+    q = nf.nf_quad_weights(X2, tris, nf.nf_build_stencils(X2, tris, wl.k), wl.deg).to(torch.float32)
+    x32 = torch.as_tensor(wl.ns.nodes.astype(np.float32), device=dev)
+    u0 = torch.as_tensor(wl.u0.astype(np.float32), device=dev)
+    flat = {"workload": f"flat square n={wl.n} k={wl.k} deg={wl.deg}, {wl.nsteps} RK4 steps dt={wl.dt}, "
+                        "one call (graph replay)"}
+    for pname, path in PATHS.items():
+        op = nf.Operator(x32, q, wl.kernel, path)
+        ms, _ = whole_run(op, u0, wl)
+        flat[pname] = {"run_ms": ms, "rk4_steps_per_s": wl.nsteps * 1e3 / ms}
+        op.close()
+    out["flat"] = flat
+    wl = W.sphere()
+    nodes = torch.as_tensor(wl.ns.nodes, device=dev)
+    tris = torch.as_tensor(wl.ns.tris, device=dev)
+    st = nf.nf_build_stencils(nodes, tris, wl.k)
+    q = nf.nf_quad_weights(nodes, tris, st, wl.deg, normals=torch.as_tensor(wl.ns.normals, device=dev))
+    X = wl.ns.nodes
+    x32 = torch.as_tensor(X.astype(np.float32), device=dev)
+    Y1 = torch.as_tensor((0.5 * X[:, 2]).astype(np.float32), device=dev)
+    Y2 = torch.as_tensor((X[:, 0] * X[:, 1]).astype(np.float32), device=dev)
+    c, a0 = wl.forcing["c"], wl.forcing["a0"]
+    F = nf.Forcing(nf.FORCE_MMS_EIGEN, Y1, Y2, c, a0, nf.nf_mms_sphere_eigs(wl.kernel))
+    op = nf.Operator(x32, q.to(torch.float32), wl.kernel, nf.MATRIX_FREE)
+    u0 = torch.as_tensor(wl.u0.astype(np.float32), device=dev)
+    ms, u = whole_run(op, u0, wl, forcing=F)
+    op.close()
+    T = wl.dt * wl.nsteps
+    z = c + a0 * math.cos(T) * (0.5 * X[:, 2] + X[:, 0] * X[:, 1])
+    exact = wl.theta[0] + np.log(z / (1.0 - z)) / wl.beta[0]
+    err = u.double().cpu().numpy().ravel() - exact
+    out["sphere"] = {"workload": f"unit sphere n={wl.n} k={wl.k} deg={wl.deg}, manufactured forcing, "
+                                 f"{wl.nsteps} RK4 steps dt={wl.dt}, matrix-free",
+                     "run_ms": ms, "rk4_steps_per_s": wl.nsteps * 1e3 / ms,
+                     "pair_evals_per_s": 4.0 * wl.n * wl.n * wl.nsteps / (ms * 1e-3),
+                     "rel_max_err_vs_u_star": float(np.abs(err).max() / np.abs(exact).max())}
+    return out
+
+
 def run_adjoint(args, dev):
     """Differentiation workload: gradient of L = |u(T) - u_target|^2 w.r.t. the kernel
     parameters and u0 through the discrete RK4 adjoint (checkpoints every C steps)."""
@@ -763,6 +829,8 @@ def run_ours(args, rank, world, local_rank):
         line["geometries"] = run_geometries(dev)
     if not args.no_periodic:
         line["periodic"] = run_periodic(dev)
+    if not args.no_configs:
+        line["configs"] = run_configs(dev)
     if args.convergence:
         line["convergence"] = run_convergence(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -171,6 +171,17 @@ NF_API nf_status nf_operator_kernel_ms(nf_operator *op, float *ms);
  * column splits (host ints; -1 for other paths). */
 NF_API nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, int *tile_cols, int *splits);
 
+/* Schedule of a matrix-free operator's single-trajectory sums (Eq. (2.9) with B = 1):
+ *   NF_MF_AUTO       the symmetric block-pair kernel (each unordered pair once, w radial)
+ *                    when its block pairs give every SM a CTA, else the packed kernel
+ *                    (default; the switch is at about 17,400 nodes on 152 SMs);
+ *   NF_MF_SYMMETRIC  always the symmetric kernel;
+ *   NF_MF_PACKED     always the packed row-block x column-split kernel (ordered pairs).
+ * Results agree to FP32 rounding (summation order differs).  Multi-trajectory sums and
+ * nf_adjoint are unaffected.  Errors: NF_ERR_ARG (not matrix-free, unknown value). */
+enum { NF_MF_AUTO = 0, NF_MF_SYMMETRIC = 1, NF_MF_PACKED = 2 };
+NF_API nf_status nf_operator_mf_schedule(nf_operator *op, int schedule);
+
 /* Failure-path self-test (no paper counterpart): launches a one-warp kernel whose
  * mbarrier wait can never complete, with a short poll limit.  The wait gives up, the
  * kernel records a timeout and returns; the call synchronises `stream` and returns

@@ -16,6 +16,7 @@ Entry points (same names as the C ABI):
 * :func:`nf_nonlocal_apply`  I = sum_j w(x_i, x_j) q_j f(u_j)
 * :func:`nf_rk4_advance`     RK4 on Eq. (2.9)
 * :func:`nf_adjoint`         discrete adjoint of the RK4 map
+* :class:`NeuralFieldRK4`    autograd Function: RK4 forward, adjoint backward
 * :func:`nf_mms_sphere_eigs` Funk-Hecke eigenvalues for manufactured forcing
 """
 from __future__ import annotations
@@ -31,11 +32,13 @@ __all__ = [
     "NFError", "lib", "build", "nf_build_stencils", "nf_quad_weights", "Operator", "nf_nonlocal_apply",
     "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
     "DENSE_BF16X2", "DENSE_SYM_FP32", "STATUS", "nf_field_advance", "MODEL_FIELD", "MODEL_DEPRESSION",
-    "RATE_SIGMOID", "RATE_SMOOTHSTEP", "FORCE_NONE", "FORCE_MMS_EIGEN", "FORCE_MMS_FLAT",
+    "RATE_SIGMOID", "RATE_SMOOTHSTEP", "FORCE_NONE", "FORCE_MMS_EIGEN", "FORCE_MMS_FLAT", "NeuralFieldRK4",
+    "MF_AUTO", "MF_SYMMETRIC", "MF_PACKED",
 ]
 
 MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32 = 0, 1, 2, 4
 FORCE_NONE, FORCE_MMS_EIGEN, FORCE_MMS_FLAT = 0, 1, 2
+MF_AUTO, MF_SYMMETRIC, MF_PACKED = 0, 1, 2
 STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINITE", 4: "NF_ERR_TIMEOUT",
           5: "NF_ERR_NOMEM", 6: "NF_ERR_CUDA", 7: "NF_ERR_UNSUPPORTED"}
 
@@ -43,7 +46,7 @@ STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINIT
 EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights", "nf_operator_create",
            "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
            "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms",
-           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout",
+           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout", "nf_operator_mf_schedule",
            "nf_field_advance"]
 
 
@@ -101,6 +104,7 @@ def lib(path: str | None = None):
     L.nf_operator_profile.argtypes = [_vp, C.c_int]
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
     L.nf_operator_launch_shape.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nf_operator_mf_schedule.argtypes = [_vp, C.c_int]
     L.nf_selftest_timeout.argtypes = [_vp]
     L.nf_nonlocal_apply.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]
     L.nf_nonlocal_apply_noalloc.argtypes = [_vp, _vp, _i64, _Kernel, _vp, C.c_float, C.c_float, _vp, _vp]
@@ -229,6 +233,11 @@ class Operator:
         r, t, s = C.c_int(), C.c_int(), C.c_int()
         _check(lib().nf_operator_launch_shape(self.handle, C.byref(r), C.byref(t), C.byref(s)))
         return {"rows_per_warp": r.value, "tile_cols": t.value, "splits": s.value}
+
+    def mf_schedule(self, schedule: int):
+        """Single-trajectory matrix-free schedule: MF_AUTO, MF_SYMMETRIC or MF_PACKED."""
+        _check(lib().nf_operator_mf_schedule(self.handle, int(schedule)))
+        return self
 
     def check(self):
         _check(lib().nf_operator_check(self.handle, _stream()))
@@ -367,6 +376,45 @@ def nf_adjoint(op: Operator, ckpt: torch.Tensor, C_every: int, t0: float, dt: fl
                             _dptr(gk, torch.float32, "grad_kernel"), _stream(lam)))
     op._keep = (be, th, forcing)
     return gu, gk
+
+
+class NeuralFieldRK4(torch.autograd.Function):
+    """u(T) after ``nsteps`` classical RK4 steps of Eq. (2.9) from ``u0``, differentiable in u0
+    and in the kernel parameters (A1, s1, A2, s2).
+
+    ``NeuralFieldRK4.apply(u0, kernel_params, x, q, beta, theta, t0, dt, nsteps[, C_every[,
+    forcing[, period]]])`` (positional; defaults 10, None, 0.0): forward builds a matrix-free operator from the values of
+    ``kernel_params`` (a 4-element tensor) and runs :func:`nf_rk4_advance` with a checkpoint
+    every ``C_every`` steps; backward runs :func:`nf_adjoint` from the incoming gradient of
+    u(T) and returns dL/du0 and dL/d(kernel_params) (summed over trajectories).  u0: n or
+    B x n float32 CUDA; x: n x 3, q: n float32 CUDA (constants)."""
+
+    @staticmethod
+    def forward(ctx, u0, kernel_params, x, q, beta, theta, t0, dt, nsteps, C_every=10, forcing=None, period=0.0):
+        kp = [float(v) for v in kernel_params.detach().reshape(-1).cpu().tolist()]
+        if len(kp) != 4:
+            raise ValueError("kernel_params must hold (A1, s1, A2, s2)")
+        op = Operator(x, q, kp + [float(period)], MATRIX_FREE)
+        squeeze = u0.dim() == 1
+        u = u0.detach().to(torch.float32).reshape(1 if squeeze else u0.shape[0], -1).contiguous().clone()
+        B, n = u.shape
+        C_every = max(1, int(C_every))
+        ck = torch.empty((int(nsteps) // C_every + 1, B, n), dtype=torch.float32, device=u.device)
+        nf_rk4_advance(op, u, t0, dt, int(nsteps), beta, theta, forcing=forcing, ckpt=ck, C_every=C_every)
+        ctx.save_for_backward(ck)
+        ctx.op = op
+        ctx.args = (C_every, float(t0), float(dt), int(nsteps), beta, theta, forcing, squeeze, kernel_params)
+        return u.view(-1) if squeeze else u
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (ck,) = ctx.saved_tensors
+        C_every, t0, dt, nsteps, beta, theta, forcing, squeeze, kparams = ctx.args
+        lam = grad_out.detach().to(torch.float32).reshape(ck.shape[1], ck.shape[2]).contiguous()
+        gu, gk = nf_adjoint(ctx.op, ck, C_every, t0, dt, nsteps, beta, theta, lam, forcing=forcing)
+        g_kernel = gk.sum(0).to(dtype=kparams.dtype, device=kparams.device).reshape(kparams.shape)
+        g_u0 = gu.view(-1) if squeeze else gu
+        return (g_u0, g_kernel) + (None,) * 10
 
 
 def nf_mms_sphere_eigs(kernel):

@@ -464,6 +464,17 @@ nf_status nf_selftest_timeout(void *stream) {
     return fail(NF_ERR_CUDA, "self-test wait did not report a timeout (flag %d)", h);
 }
 
+nf_status nf_operator_mf_schedule(nf_operator *op, int schedule) {
+    clear_error();
+    NF_ARG(op, "op is NULL");
+    NF_ARG(op->path == NF_MATRIX_FREE, "the schedule applies to matrix-free operators");
+    NF_ARG(schedule == NF_MF_AUTO || schedule == NF_MF_SYMMETRIC || schedule == NF_MF_PACKED,
+           "unknown schedule %d", schedule);
+    if (op->mf_sched != schedule) destroy_graphs(op);  // captured steps bake in the launch shape
+    op->mf_sched = schedule;
+    return NF_OK;
+}
+
 nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, int *tile_cols, int *splits) {
     clear_error();
     NF_ARG(op && rows_per_warp && tile_cols && splits, "arguments must be non-NULL");

@@ -173,6 +173,7 @@ struct nf_operator {
     float *xyz = nullptr;    // 3 x n_pad: coordinates times sqrt(log2 e)/s1, structure of arrays
     int mf_variant = -1;     // launch shape of the packed pair kernel
     int mf_sym_r = 8;        // rows per warp of the symmetric single-trajectory kernel (autotuned)
+    int mf_sched = 0;        // NF_MF_AUTO / NF_MF_SYMMETRIC / NF_MF_PACKED
     int *rowperm = nullptr;  // n_pad: row order of the packed pair kernel (Morton order of the nodes)
     float *q = nullptr;      // n_pad, zero padded
     // dense planes (row-major, leading dimension ld = n_pad)
@@ -227,6 +228,7 @@ nf_status mf_build_row_order(nf_operator *op, cudaStream_t s);
 SplitPlan mf_plan(nf_operator *op);     // column splits of the multi-trajectory matrix-free launches
 int mf_splits(nf_operator *op, int B);  // partial-sum slots of a matrix-free launch over B trajectories
 int64_t sym_pair_count(const nf_operator *op);  // block pairs of the symmetric kernels
+int sym_slots(const nf_operator *op);   // node blocks of the symmetric schedule (W nu slots)
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
                          float *r2_phys, cudaStream_t s);
 nf_status mf_autotune(nf_operator *op, cudaStream_t s);

@@ -1191,6 +1191,17 @@ static nf_status launch_sym(nf_operator *op, int B, int b_base, cudaStream_t s) 
 // into wpart [n_pad / MS_BLK][B][n_pad], parameter sums into gpart [B][pairs][4] with r^2 in
 // exponent units; *r2_phys receives the factor to physical r^2.
 int64_t sym_pair_count(const nf_operator *op) { return sym_pairs(op); }
+int sym_slots(const nf_operator *op) { return (int)(op->n_pad / MS_BLK); }
+
+// One trajectory takes the symmetric kernel when its block pairs give every SM at least one
+// CTA; smaller node sets (fewer than ~17,400 nodes on 152 SMs) have too few block pairs to
+// fill the GPU and take the packed row-block x column-split kernel instead, which evaluates
+// ordered pairs but spreads them over many more CTAs.
+static bool use_sym(const nf_operator *op) {
+    if (op->mf_sched == NF_MF_SYMMETRIC) return true;
+    if (op->mf_sched == NF_MF_PACKED) return false;
+    return sym_pairs(op) >= (int64_t)num_sms();
+}
 
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
                          float *r2_phys, cudaStream_t s) {
@@ -1214,7 +1225,7 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
 }
 
 int mf_splits(nf_operator *op, int B) {
-    return B == 1 ? (int)(op->n_pad / MS_BLK) : mf_plan(op).splits;
+    return (B == 1 && use_sym(op)) ? sym_slots(op) : mf_plan(op).splits;
 }
 
 static SplitPlan variant_plan(int64_t n_pad, int v) {
@@ -1228,9 +1239,16 @@ SplitPlan mf_plan(nf_operator *op) {
 
 // Shape of the single-trajectory (symmetric) launch: rows per warp, block width, slots.
 void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits) {
+    if (!use_sym(op)) {
+        const SplitPlan pl = mf_plan(op);
+        *R = kMfVariants[op->mf_variant].R;
+        *TJ = kMfVariants[op->mf_variant].TJ;
+        *splits = pl.splits;
+        return;
+    }
     *R = op->mf_sym_r;
     *TJ = MS_BLK;
-    *splits = (int)(op->n_pad / MS_BLK);
+    *splits = sym_slots(op);
 }
 
 // Rows per warp of the scalar multi-trajectory kernel (2 or 4 are instantiated).
@@ -1243,6 +1261,7 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     static std::mutex mu;
     static std::map<std::tuple<int, int64_t, int>, int> cache;
     op->mf_variant = default_variant(op->n_pad);
+    if (sym_pairs(op) < (int64_t)num_sms()) return NF_OK;  // too small to time: keep 8 rows per warp
     const auto key = std::make_tuple(op->device, op->n_pad, mf_width_ratio(op->kp));
     {
         std::lock_guard<std::mutex> lock(mu);
@@ -1282,9 +1301,15 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
 }
 
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
-    if (B == 1) {  // one trajectory: symmetric kernel, one partial slot per node block
+    if (B == 1 && use_sym(op)) {  // one trajectory: symmetric kernel, one partial slot per node block
         NF_TRY(launch_sym(op, 1, 0, s));
-        *splits_out = (int)(op->n_pad / MS_BLK);
+        *splits_out = sym_slots(op);
+        return NF_OK;
+    }
+    if (B == 1) {  // a small node set: the packed kernel over (row block, column split) items
+        const SplitPlan pl = mf_plan(op);
+        NF_TRY(launch_mf_packed(op, 1, 0, 1, pl, s));
+        *splits_out = pl.splits;
         return NF_OK;
     }
     // the column splits (and so the partial-sum layout) come from the packed kernel's

@@ -68,3 +68,33 @@ def test_adjoint_rejects_dense_operator(nf):
     with pytest.raises(nf.NFError) as ei:
         nf.nf_adjoint(op, ck, 1, 0.0, 0.1, 1, 20.0, 0.2, torch.zeros((1, 64), device="cuda"))
     assert ei.value.name == "NF_ERR_UNSUPPORTED"
+
+
+def test_autograd_function_matches_adjoint_and_oracle(nf):
+    """NeuralFieldRK4 (forward nf_rk4_advance, backward nf_adjoint) inside a torch loss:
+    its gradients equal the oracle's discrete adjoint (trajectory gradients summed for the
+    shared kernel parameters)."""
+    ns = nodesets.torus_lattice(1200, seed=3)
+    n = ns.n
+    X = ns.nodes.astype(np.float32)
+    q = np.full(n, ns.area / n, dtype=np.float32)
+    u0 = np.stack([nodesets.spiral_bumps_u0(ns, count=3 + b) for b in range(2)]).astype(np.float32)
+    beta = np.array([20.0, 12.0], dtype=np.float32)
+    theta = np.array([0.2, 0.25], dtype=np.float32)
+    dt, nsteps, C = 0.02, 9, 4
+    target = (0.9 * u0).astype(np.float32)
+    kp = torch.tensor(M4, dtype=torch.float64, requires_grad=True)
+    u0t = dev(u0).requires_grad_(True)
+    uT = nf.NeuralFieldRK4.apply(u0t, kp, dev(X), dev(q), dev(beta), dev(theta), 0.0, dt, nsteps, C)
+    loss = ((uT - dev(target)) ** 2).sum()
+    loss.backward()
+    uN = oracle.rk4(f32(X), f32(q), f32(u0), f32(M4), f32(beta), f32(theta), 0.0, dt, nsteps)
+    np.testing.assert_allclose(uT.detach().cpu().numpy(), uN, rtol=0, atol=1e-5 * np.abs(uN).max())
+    gu_o, gk_o = oracle.adjoint(f32(X), f32(q), f32(u0), f32(M4), f32(beta), f32(theta), 0.0, dt, nsteps,
+                                2.0 * (uN - f32(target)))
+    gu = u0t.grad.cpu().numpy()
+    for b in range(2):
+        assert np.linalg.norm(gu[b] - gu_o[b]) / np.linalg.norm(gu_o[b]) < 1e-5
+    gk = kp.grad.numpy()
+    want = gk_o.sum(0)
+    np.testing.assert_allclose(gk, want, rtol=1e-4, atol=1e-6 * np.abs(want).max())

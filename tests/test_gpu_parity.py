@@ -157,7 +157,7 @@ def test_nonlocal_apply_row_order_forms(nf, s1):
     q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
     u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
     kern = (1.0, s1, 0.5, 2 * s1)
-    op = _op(nf, X, q, kern, 0)
+    op = _op(nf, X, q, kern, 0).mf_schedule(nf.MF_SYMMETRIC)
     got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), 20.0, 0.2).cpu().numpy()
     op.check()
     want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
@@ -165,18 +165,20 @@ def test_nonlocal_apply_row_order_forms(nf, s1):
     assert np.abs(got - want).max() / np.abs(want).max() < REL_L2
 
 
+@pytest.mark.parametrize("sched", [1, 2])
 @pytest.mark.parametrize("ratio,n", [(2.0, 2048), (2 ** 0.5, 1024), (3 ** 0.5, 1025), (1.7, 3073), (2.0, 1023)])
-def test_nonlocal_apply_width_ratios_and_blocks(nf, ratio, n):
-    """One trajectory: the symmetric kernel's forms for s2^2 / s1^2 = 4, 2, 3 (e1 = e2^m
-    by squaring) and a non-integer ratio (two exponentials), on node counts at and just
-    past the 1024-node block boundaries (one block, a ragged second block, exact blocks)."""
+def test_nonlocal_apply_width_ratios_and_blocks(nf, ratio, n, sched):
+    """One trajectory, both schedules (symmetric block pairs; packed row blocks x column
+    splits): the forms for s2^2 / s1^2 = 4, 2, 3 (e1 = e2^m by squaring) and a non-integer
+    ratio (two exponentials), on node counts at and just past the 1024-node block
+    boundaries (one block, a ragged second block, exact blocks)."""
     rng = np.random.default_rng(int(ratio * 1000) + n)
     X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
     q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
     u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
     s1 = 0.15
     kern = (1.0, s1, 0.5, float(np.float32(s1) * np.float32(ratio)))
-    op = _op(nf, X, q, kern, 0)
+    op = _op(nf, X, q, kern, 0).mf_schedule(sched)
     got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), 20.0, 0.2).cpu().numpy()
     op.check()
     want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
@@ -293,3 +295,30 @@ def test_rk4_checkpoints(nf):
     for c in (1, 2):
         want = oracle.rk4(f32(X), f32(q), f32(u0), (1.0, 0.3, 0.5, 0.6), 20.0, np.float32(0.2), 0.0, 0.05, 3 * c)
         assert rel_l2(ck[c], want) < REL_L2
+
+
+def test_mf_schedule_switch_and_auto(nf):
+    """The automatic schedule picks the packed kernel for a small node set and the
+    symmetric one at n = 20,000 (210 block pairs); switching schedules on a live operator
+    (also between captured RK4 steps) keeps the results."""
+    for n, want_tile in ((3000, None), (20000, 1024)):
+        rng = np.random.default_rng(n)
+        X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+        q = np.full(n, 1.0 / n, dtype=np.float32)
+        u0 = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
+        op = _op(nf, X, q, (1.0, 0.3, 0.5, 0.6), 0)
+        shape = op.launch_shape()
+        if want_tile is not None:
+            assert shape["tile_cols"] == want_tile and shape["splits"] == -(-n // 1024)
+        else:
+            assert shape["tile_cols"] in (512, 1024) and shape["splits"] <= 64
+        res = []
+        for sched in (0, 1, 2, 0):
+            op.mf_schedule(sched)
+            u = dev(u0, torch.float32)
+            nf.nf_rk4_advance(op, u, 0.0, 0.05, 3, 20.0, 0.2)
+            op.check()
+            res.append(u.cpu().numpy())
+        want = oracle.rk4(f32(X), f32(q), f32(u0), (1.0, 0.3, 0.5, 0.6), 20.0, float(np.float32(0.2)), 0.0, 0.05, 3)
+        for r in res:
+            assert rel_l2(r, want) < REL_L2

@@ -88,12 +88,27 @@ def test_periodic_forms_blobs(nf, kern):
     X = np.concatenate([np.mod(xy, L), np.zeros((n, 1))], 1).astype(np.float32)
     q = (rng.uniform(0.5, 1.5, n) / n).astype(np.float32)
     u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
-    op = nf.Operator(dev(X), dev(q), kern, 0)
+    op = nf.Operator(dev(X), dev(q), kern, 0).mf_schedule(nf.MF_SYMMETRIC)
     got = nf.nf_nonlocal_apply(op, dev(u), 20.0, 0.2).cpu().numpy()
     op.check()
     want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
     assert rel_l2(got, want) < REL_L2
     assert np.abs(got - want).max() / np.abs(want).max() < REL_L2
+
+
+@pytest.mark.parametrize("kname", sorted(KERNELS))
+@pytest.mark.parametrize("n", [3001, 1025])
+def test_periodic_symmetric_schedule(nf, kname, n):
+    """The symmetric kernel's periodic forms on small node sets (the automatic schedule
+    would take the packed kernel there)."""
+    kern = KERNELS[kname]
+    rng, X, q = _square(n, 40 + n)
+    u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
+    op = nf.Operator(dev(X), dev(q), kern, 0).mf_schedule(nf.MF_SYMMETRIC)
+    got = nf.nf_nonlocal_apply(op, dev(u), 20.0, 0.2).cpu().numpy()
+    op.check()
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
+    assert rel_l2(got, want) < REL_L2
 
 
 def test_periodic_z_is_not_wrapped(nf):
