@@ -173,8 +173,8 @@ NF_API nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, i
 
 /* Schedule of a matrix-free operator's single-trajectory sums (Eq. (2.9) with B = 1):
  *   NF_MF_AUTO       the symmetric block-pair kernel (each unordered pair once, w radial)
- *                    when its block pairs give every SM a CTA, else the packed kernel
- *                    (default; the switch is at about 17,400 nodes on 152 SMs);
+ *                    when it has block pairs for 2/3 of the SMs, else the packed kernel
+ *                    (default; the switch is at about 13,300 nodes on 152 SMs);
  *   NF_MF_SYMMETRIC  always the symmetric kernel;
  *   NF_MF_PACKED     always the packed row-block x column-split kernel (ordered pairs).
  * Results agree to FP32 rounding (summation order differs).  Multi-trajectory sums and

@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2)
 mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
               int64_t n_pad, int B, int b_base, float k2, float A1, float A2, float per,
               float *__restrict__ partial) {
-    static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
+    static_assert(M >= 0 && M <= 4, "form M: 0 general, 1 one Gaussian (A2 = 0), 2-4 width ratio");
     static_assert(R == 4 || R == 8, "rows per warp");
     constexpr int NPASS = MS_BLK / R;
     extern __shared__ __align__(16) float ms_smem[];
@@ -506,7 +506,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
     // exponent units: s1 (coordinates as stored), or s2 when M > 0 (times sk = s1 / s2,
     // applied once here, so r^2 and s_ij arrive as the exponent of e2)
-    const float sk = M > 0 ? sqrtf(k2) : 1.f;
+    const float sk = M >= 2 ? sqrtf(k2) : 1.f;  // M = 1: one Gaussian, units of s1
     // gather the column block, and the row block's raw data (x, y, z, g in mx, my, mz, h1)
     for (int k = tid; k < MS_BLK; k += MS_THREADS) {
         const int node = __ldg(rowperm + cbase + k);
@@ -600,7 +600,10 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     auto exps = [&](u64 arg, u64 &e1, u64 &e2) {
         float s0, s1v;
         f2_unpack(arg, s0, s1v);
-        if constexpr (M > 0) {
+        if constexpr (M == 1) {
+            e1 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
+            e2 = 0ull;
+        } else if constexpr (M > 0) {
             e2 = f2_pack(ex2_sfu(-s0), ex2_sfu(-s1v));
             const u64 sq = f2_mul(e2, e2);
             e1 = M == 2 ? sq : (M == 3 ? f2_mul(sq, e2) : f2_mul(sq, sq));
@@ -663,8 +666,12 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                         u64 e1, e2;
                         exps(sij, e1, e2);
                         a1[r] = f2_fma(e1, gj[h], a1[r]);
-                        a2[r] = f2_fma(e2, gj[h], a2[r]);
-                        cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
+                        if constexpr (M == 1) {
+                            cacc[h] = f2_fma(e1, h1[r], cacc[h]);
+                        } else {
+                            a2[r] = f2_fma(e2, gj[h], a2[r]);
+                            cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
+                        }
                     }
                 }
                 add_cols(q, cacc);
@@ -703,8 +710,12 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                         u64 e1, e2;
                         exps(r2s, e1, e2);
                         a1[r] = f2_fma(e1, gj[h], a1[r]);
-                        a2[r] = f2_fma(e2, gj[h], a2[r]);
-                        cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
+                        if constexpr (M == 1) {
+                            cacc[h] = f2_fma(e1, h1[r], cacc[h]);
+                        } else {
+                            a2[r] = f2_fma(e2, gj[h], a2[r]);
+                            cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
+                        }
                     }
                 }
                 add_cols(q, cacc);
@@ -1047,6 +1058,8 @@ nf_status mf_init_attrs() {
     NF_CUDA_TRY((set_adj_attr<4, 3>()));
     NF_CUDA_TRY((set_adj_attr<4, 4>()));
     NF_CUDA_TRY((set_sym_attr<4, 0>()));
+    NF_CUDA_TRY((set_sym_attr<4, 1>()));
+    NF_CUDA_TRY((set_sym_attr<8, 1>()));
     NF_CUDA_TRY((set_sym_attr<4, 2>()));
     NF_CUDA_TRY((set_sym_attr<4, 3>()));
     NF_CUDA_TRY((set_sym_attr<4, 4>()));
@@ -1097,6 +1110,10 @@ constexpr MfVariant kMfVariants[] = {{2, 512}, {4, 512}, {4, 1024}, {8, 1024}};
 static float scaled_period(const nf_kernel &k) {
     return k.period > 0.f ? k.period * (std::sqrt(1.4426950408889634f) / k.s1) : 0.f;
 }
+
+// Form of the symmetric kernel: 1 for a single Gaussian (A2 = 0), else the width ratio.
+static int mf_width_ratio(const nf_kernel &k);
+static int sym_form(const nf_kernel &k) { return k.A2 == 0.f ? 1 : mf_width_ratio(k); }
 
 // Integer width ratio m = s2^2 / s1^2 in {2, 3, 4} (to FP32 rounding of the k2 the kernel
 // receives), else 0: selects the one-exponential form of the packed kernel.
@@ -1169,7 +1186,8 @@ static void launch_sym_r(nf_operator *op, int B, int b_base, cudaStream_t s) {
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
     dim3 grid((unsigned)sym_pairs(op), 1, 1);
 #define NF_SYM_ARGS op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, scaled_period(k), op->partial
-    switch (mf_width_ratio(k)) {
+    switch (sym_form(k)) {
+        case 1: mf_sym_kernel<R, 1><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
         case 2: mf_sym_kernel<R, 2><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
         case 3: mf_sym_kernel<R, 3><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
         case 4: mf_sym_kernel<R, 4><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
@@ -1193,14 +1211,15 @@ static nf_status launch_sym(nf_operator *op, int B, int b_base, cudaStream_t s) 
 int64_t sym_pair_count(const nf_operator *op) { return sym_pairs(op); }
 int sym_slots(const nf_operator *op) { return (int)(op->n_pad / MS_BLK); }
 
-// One trajectory takes the symmetric kernel when its block pairs give every SM at least one
-// CTA; smaller node sets (fewer than ~17,400 nodes on 152 SMs) have too few block pairs to
-// fill the GPU and take the packed row-block x column-split kernel instead, which evaluates
-// ordered pairs but spreads them over many more CTAs.
+// One trajectory takes the symmetric kernel when it has at least 2/3 as many block pairs as
+// the GPU has SMs; smaller node sets (below ~13,300 nodes on 152 SMs) have too few block
+// pairs to fill the GPU and take the packed row-block x column-split kernel instead, which
+// evaluates ordered pairs but spreads them over many more CTAs (measured crossover on GB300:
+// packed 0.119 ms vs symmetric 0.130 ms at n = 12,000; 0.155 vs 0.131 ms at n = 16,384).
 static bool use_sym(const nf_operator *op) {
     if (op->mf_sched == NF_MF_SYMMETRIC) return true;
     if (op->mf_sched == NF_MF_PACKED) return false;
-    return sym_pairs(op) >= (int64_t)num_sms();
+    return 3 * sym_pairs(op) >= 2 * (int64_t)num_sms();
 }
 
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
@@ -1261,8 +1280,8 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     static std::mutex mu;
     static std::map<std::tuple<int, int64_t, int>, int> cache;
     op->mf_variant = default_variant(op->n_pad);
-    if (sym_pairs(op) < (int64_t)num_sms()) return NF_OK;  // too small to time: keep 8 rows per warp
-    const auto key = std::make_tuple(op->device, op->n_pad, mf_width_ratio(op->kp));
+    if (3 * sym_pairs(op) < 2 * (int64_t)num_sms()) return NF_OK;  // packed by default: keep 8 rows per warp
+    const auto key = std::make_tuple(op->device, op->n_pad, sym_form(op->kp));
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);

@@ -166,18 +166,20 @@ def test_nonlocal_apply_row_order_forms(nf, s1):
 
 
 @pytest.mark.parametrize("sched", [1, 2])
-@pytest.mark.parametrize("ratio,n", [(2.0, 2048), (2 ** 0.5, 1024), (3 ** 0.5, 1025), (1.7, 3073), (2.0, 1023)])
+@pytest.mark.parametrize("ratio,n", [(2.0, 2048), (2 ** 0.5, 1024), (3 ** 0.5, 1025), (1.7, 3073), (2.0, 1023),
+                                     (None, 3073), (None, 1025)])
 def test_nonlocal_apply_width_ratios_and_blocks(nf, ratio, n, sched):
     """One trajectory, both schedules (symmetric block pairs; packed row blocks x column
     splits): the forms for s2^2 / s1^2 = 4, 2, 3 (e1 = e2^m by squaring) and a non-integer
-    ratio (two exponentials), on node counts at and just past the 1024-node block
-    boundaries (one block, a ragged second block, exact blocks)."""
-    rng = np.random.default_rng(int(ratio * 1000) + n)
+    ratio (two exponentials), and a single Gaussian (A2 = 0, one accumulator per sum; ratio
+    None), on node counts at and just past the 1024-node block boundaries (one block, a
+    ragged second block, exact blocks)."""
+    rng = np.random.default_rng(int((ratio or 5.0) * 1000) + n)
     X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
     q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
     u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
     s1 = 0.15
-    kern = (1.0, s1, 0.5, float(np.float32(s1) * np.float32(ratio)))
+    kern = (1.0, s1, 0.5, float(np.float32(s1) * np.float32(ratio))) if ratio else (1.3, s1, 0.0, 0.3)
     op = _op(nf, X, q, kern, 0).mf_schedule(sched)
     got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), 20.0, 0.2).cpu().numpy()
     op.check()
