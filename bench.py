@@ -469,9 +469,10 @@ def mms_case(geometry, n):
             "h": 1.0 / math.sqrt(ns.n)}
 
 
-def mms_run(dev, geometry, n, degs):
+def mms_run(dev, geometry, n, degs, cull=True):
     """One node set: GPU stencils and weights per degree, then RK4 on the matrix-free
-    periodic path with the flat manufactured forcing; errors at T against u*."""
+    periodic path with the flat manufactured forcing; errors at T against u*.  cull: skip
+    the block pairs whose contributions are exactly zero (bit-identical sums)."""
     import torch
 
     import paper_2504_13379_gb300 as nf
@@ -496,6 +497,7 @@ def mms_run(dev, geometry, n, degs):
             continue
         qd = q.cpu().numpy() * cs["qscale"]
         op = nf.Operator(x32, torch.as_tensor(qd.astype(np.float32), device=dev), mms_kernel(), nf.MATRIX_FREE)
+        live, total = op.mf_cull(cull)
         F = nf.Forcing.flat(MMS_C, MMS_RADIUS, MMS_SIGMA, cs["scale"])
         u = u0.clone()
         nf.nf_rk4_advance(op, u, 0.0, MMS_DT, 1, MMS_GAIN, MMS_THRESH, forcing=F)  # graph capture
@@ -512,7 +514,8 @@ def mms_run(dev, geometry, n, degs):
         rows.append({"deg": deg, "n": cs["n"], "h": cs["h"],
                      "rel_max_err": float(np.abs(err).max() / np.abs(exact).max()),
                      "rel_l2_err": float(math.sqrt((w * err ** 2).sum() / (w * exact ** 2).sum())),
-                     "rk4_ms": a.elapsed_time(b), "ms_per_nonlocal_sum": a.elapsed_time(b) / (4 * nsteps)})
+                     "rk4_ms": a.elapsed_time(b), "ms_per_nonlocal_sum": a.elapsed_time(b) / (4 * nsteps),
+                     "live_block_pairs": live, "block_pairs": total, "culled": bool(cull)})
         op.close()
     return rows
 
@@ -532,13 +535,16 @@ def observed_orders(rows):
 
 def run_periodic(dev):
     """The periodic-square path at one size: §4.3's manufactured problem on 2^17 Halton
-    nodes (degree 3), error at T and the time per nonlocal sum."""
-    r = mms_run(dev, "flat", 1 << 17, [3])[0]
-    r["workload"] = ("§4.3 manufactured solution on the periodic square of side 2 pi, Gauss(1/40) kernel, "
-                     "matrix-free periodic path, RK4 dt=0.01 to T=0.1")
-    n = r["n"]
-    r["pair_evals_per_s"] = n * n / (r["ms_per_nonlocal_sum"] * 1e-3)
-    return r
+    nodes (degree 3), error at T and the time per nonlocal sum, without and with block-pair
+    culling (whose sums are bit-identical)."""
+    out = {"workload": "§4.3 manufactured solution on the periodic square of side 2 pi, Gauss(1/40) kernel, "
+                       "matrix-free periodic path (one-Gaussian form), RK4 dt=0.01 to T=0.1"}
+    for key, cull in (("all_pairs", False), ("culled", True)):
+        r = mms_run(dev, "flat", 1 << 17, [3], cull=cull)[0]
+        n = r["n"]
+        r["pair_evals_per_s"] = n * n / (r["ms_per_nonlocal_sum"] * 1e-3)
+        out[key] = r
+    return out
 
 
 def run_convergence(dev):
@@ -619,6 +625,39 @@ def run_configs(dev):
                      "pair_evals_per_s": 4.0 * wl.n * wl.n * wl.nsteps / (ms * 1e-3),
                      "rel_max_err_vs_u_star": float(np.abs(err).max() / np.abs(exact).max())}
     return out
+
+
+def run_culling(args, dev, wl, x32, q32, u0):
+    """Block-pair culling on the precision workload: RK4 steps with the culled symmetric
+    kernel, the live fraction, and a bitwise comparison with the full sum after one step.
+    Not part of the headline value (which counts every pair evaluated)."""
+    import torch
+
+    import paper_2504_13379_gb300 as nf
+
+    beta, theta = float(wl.beta[0]), float(wl.theta[0])
+    full = nf.Operator(x32, q32, wl.kernel, nf.MATRIX_FREE)
+    op = nf.Operator(x32, q32, wl.kernel, nf.MATRIX_FREE)
+    live, total = op.mf_cull(True)
+    ua, ub = u0.clone().view(1, -1), u0.clone().view(1, -1)
+    nf.nf_rk4_advance(full, ua, 0.0, wl.dt, 1, beta, theta)
+    nf.nf_rk4_advance(op, ub, 0.0, wl.dt, 1, beta, theta)
+    identical = bool(torch.equal(ua, ub))
+    full.close()
+    stream = torch.cuda.current_stream(dev)
+    K = max(4, min(args.steps, 40))
+    u = u0.clone().view(1, -1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    nf.nf_rk4_advance(op, u, 0.0, wl.dt, K, beta, theta)
+    b.record(stream)
+    b.synchronize()
+    op.check()
+    op.close()
+    ms = a.elapsed_time(b) / K
+    return {"workload": f"precision torus n={wl.n}, matrix-free symmetric kernel with block-pair culling",
+            "ms_per_step": ms, "rk4_steps_per_s": 1e3 / ms, "live_block_pairs": live, "block_pairs": total,
+            "bit_identical_to_full_sum": identical, "steps_timed": K}
 
 
 def run_adjoint(args, dev):
@@ -829,6 +868,7 @@ def run_ours(args, rank, world, local_rank):
         line["geometries"] = run_geometries(dev)
     if not args.no_periodic:
         line["periodic"] = run_periodic(dev)
+        line["culling"] = run_culling(args, dev, wl, x32, q32, u0)
     if not args.no_configs:
         line["configs"] = run_configs(dev)
     if args.convergence:

@@ -182,6 +182,22 @@ NF_API nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, i
 enum { NF_MF_AUTO = 0, NF_MF_SYMMETRIC = 1, NF_MF_PACKED = 2 };
 NF_API nf_status nf_operator_mf_schedule(nf_operator *op, int schedule);
 
+/* Block-pair culling for the symmetric single-trajectory schedule (opt-in; off at creation).
+ * A pair of 1024-node blocks whose bounding boxes lie so far apart that the wider Gaussian
+ * has an exponent above 160 (base 2) for every node pair in it contributes exactly zero in
+ * FP32 (the exponential flushes to 0 below 2^-126), so it is skipped: the kernel runs over
+ * the remaining block pairs only, and each node adds its block's live partial sums in the
+ * same order as the full sum.  Results are bit-identical to the unculled sum; narrow
+ * kernels on large domains (the Gauss(1/40) kernel of §4.3-4.4 on the 2 pi square) skip
+ * almost every pair.  The distance bound respects the kernel's period.
+ *   enable       1 to build the live-pair lists (host work over all block pairs; copies
+ *                the coordinates to the host and synchronises `stream`), 0 to switch off
+ *   live_pairs, block_pairs   host int64 outputs (may be NULL): live and total block pairs
+ * Multi-trajectory sums, the packed schedule and nf_adjoint do not cull.
+ * Errors: NF_ERR_ARG (not matrix-free), NF_ERR_NOMEM/NF_ERR_CUDA. */
+NF_API nf_status nf_operator_mf_cull(nf_operator *op, int enable, int64_t *live_pairs, int64_t *block_pairs,
+                                     void *stream);
+
 /* Failure-path self-test (no paper counterpart): launches a one-warp kernel whose
  * mbarrier wait can never complete, with a short poll limit.  The wait gives up, the
  * kernel records a timeout and returns; the call synchronises `stream` and returns

@@ -46,8 +46,8 @@ STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINIT
 EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights", "nf_operator_create",
            "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
            "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms",
-           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout", "nf_operator_mf_schedule",
-           "nf_field_advance"]
+           "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout",
+           "nf_operator_mf_schedule", "nf_operator_mf_cull", "nf_field_advance"]
 
 
 class NFError(RuntimeError):
@@ -105,6 +105,7 @@ def lib(path: str | None = None):
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
     L.nf_operator_launch_shape.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.nf_operator_mf_schedule.argtypes = [_vp, C.c_int]
+    L.nf_operator_mf_cull.argtypes = [_vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]
     L.nf_selftest_timeout.argtypes = [_vp]
     L.nf_nonlocal_apply.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]
     L.nf_nonlocal_apply_noalloc.argtypes = [_vp, _vp, _i64, _Kernel, _vp, C.c_float, C.c_float, _vp, _vp]
@@ -238,6 +239,13 @@ class Operator:
         """Single-trajectory matrix-free schedule: MF_AUTO, MF_SYMMETRIC or MF_PACKED."""
         _check(lib().nf_operator_mf_schedule(self.handle, int(schedule)))
         return self
+
+    def mf_cull(self, enable: bool = True):
+        """Skip block pairs whose every pair contributes exactly zero in FP32 (bit-identical
+        results); returns (live block pairs, total block pairs)."""
+        live, tot = C.c_int64(), C.c_int64()
+        _check(lib().nf_operator_mf_cull(self.handle, int(enable), C.byref(live), C.byref(tot), _stream()))
+        return live.value, tot.value
 
     def check(self):
         _check(lib().nf_operator_check(self.handle, _stream()))

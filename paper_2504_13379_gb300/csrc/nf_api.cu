@@ -347,6 +347,10 @@ nf_status nf_operator_destroy(nf_operator *op) {
     cudaFree(op->x4);
     cudaFree(op->xyz);
     cudaFree(op->rowperm);
+    cudaFree(op->cull_pairs);
+    cudaFree(op->cull_ptr);
+    cudaFree(op->cull_slots);
+    cudaFree(op->node_blk);
     cudaFree(op->q);
     cudaFree(op->W32);
     cudaFree(op->Whi);
@@ -462,6 +466,14 @@ nf_status nf_selftest_timeout(void *stream) {
     NF_CUDA_TRY(cudaStreamSynchronize(s));
     if (h == DEV_TIMEOUT) return fail(NF_ERR_TIMEOUT, "bounded wait gave up as expected (self-test)");
     return fail(NF_ERR_CUDA, "self-test wait did not report a timeout (flag %d)", h);
+}
+
+nf_status nf_operator_mf_cull(nf_operator *op, int enable, int64_t *live_pairs, int64_t *block_pairs,
+                              void *stream) {
+    clear_error();
+    NF_ARG(op, "op is NULL");
+    NF_ARG(op->path == NF_MATRIX_FREE, "culling applies to matrix-free operators");
+    return mf_set_cull(op, enable, live_pairs, block_pairs, as_stream(stream));
 }
 
 nf_status nf_operator_mf_schedule(nf_operator *op, int schedule) {

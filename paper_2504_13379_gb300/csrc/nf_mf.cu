@@ -20,6 +20,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 namespace nfi {
 
@@ -484,7 +485,7 @@ template <int R, int M>
 __global__ void __launch_bounds__(MS_THREADS, 2)
 mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
               int64_t n_pad, int B, int b_base, float k2, float A1, float A2, float per,
-              float *__restrict__ partial) {
+              float *__restrict__ partial, const int *__restrict__ pairs) {
     static_assert(M >= 0 && M <= 4, "form M: 0 general, 1 one Gaussian (A2 = 0), 2-4 width ratio");
     static_assert(R == 4 || R == 8, "rows per warp");
     constexpr int NPASS = MS_BLK / R;
@@ -498,7 +499,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     float *colacc = reinterpret_cast<float *>(pc + MS_BLK / 4);  // [MS_WARPS][MS_BLK]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int I, J;
-    sym_pair(blockIdx.x, I, J);
+    sym_pair(pairs ? (int64_t)__ldg(pairs + blockIdx.x) : (int64_t)blockIdx.x, I, J);  // pairs: live list
     const bool diag = I == J;
     const int b = b_base + blockIdx.z;
     const float *g = g_all + (int64_t)b * n_pad;
@@ -1184,8 +1185,10 @@ template <int R>
 static void launch_sym_r(nf_operator *op, int B, int b_base, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
-    dim3 grid((unsigned)sym_pairs(op), 1, 1);
-#define NF_SYM_ARGS op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, scaled_period(k), op->partial
+    dim3 grid((unsigned)(op->mf_cull ? op->cull_live : sym_pairs(op)), 1, 1);
+#define NF_SYM_ARGS                                                                                       \
+    op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, scaled_period(k), op->partial, \
+        (op->mf_cull ? op->cull_pairs : nullptr)
     switch (sym_form(k)) {
         case 1: mf_sym_kernel<R, 1><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
         case 2: mf_sym_kernel<R, 2><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
@@ -1319,10 +1322,125 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     return NF_OK;
 }
 
+// ---- block-pair culling (opt-in).  A block pair whose bounding boxes are so far apart that
+// the wider Gaussian's exponent exceeds 160 (log2 units) for every pair in it contributes
+// exactly zero in FP32: ex2 flushes results below 2^-126 to 0, e1 = e2^m then is 0 too, and
+// adding those zeros leaves every row and column sum unchanged.  Culling skips such pairs:
+// the symmetric kernel runs over the live pairs only, and each node then adds the slots of
+// its block's live pairs, in ascending slot order, into slot 0 -- the same nonzero terms in
+// the same order as the full sum, so results are bit-identical to it.
+__global__ void cull_reduce_kernel(float *__restrict__ partial, int64_t n_pad, const int *__restrict__ node_blk,
+                                   const int *__restrict__ ptr, const int *__restrict__ slots) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    const int K = node_blk[i];
+    float acc = 0.f;
+    for (int p = ptr[K]; p < ptr[K + 1]; ++p) acc += partial[(int64_t)slots[p] * n_pad + i];
+    partial[i] = acc;
+}
+
+nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live_out, int64_t *total_out, cudaStream_t s) {
+    const int64_t n = op->n, n_pad = op->n_pad, nb = n_pad / MS_BLK, npairs = nb * (nb + 1) / 2;
+    if (total_out) *total_out = npairs;
+    if (live_out) *live_out = npairs;
+    if (!enable) {
+        if (op->mf_cull) destroy_graphs(op);
+        op->mf_cull = 0;
+        return NF_OK;
+    }
+    // boxes of the Morton blocks over their real nodes, in the kernel's coordinate units
+    std::vector<float> xyz((size_t)3 * n_pad);
+    std::vector<int> perm((size_t)n_pad);
+    NF_CUDA_TRY(cudaMemcpyAsync(xyz.data(), op->xyz, sizeof(float) * 3 * n_pad, cudaMemcpyDeviceToHost, s));
+    NF_CUDA_TRY(cudaMemcpyAsync(perm.data(), op->rowperm, sizeof(int) * n_pad, cudaMemcpyDeviceToHost, s));
+    NF_CUDA_TRY(cudaStreamSynchronize(s));
+    const nf_kernel &k = op->kp;
+    const int form = sym_form(k);
+    const double k2 = ((double)k.s1 * k.s1) / ((double)k.s2 * k.s2);
+    const double sk = form >= 2 ? std::sqrt(k2) : 1.0;
+    const double wide = form > 0 ? 1.0 : std::min(1.0, k2);
+    const double per = (double)scaled_period(k);
+    std::vector<double> lo((size_t)3 * nb, 1e300), hi((size_t)3 * nb, -1e300);
+    std::vector<char> empty((size_t)nb, 1);
+    std::vector<int> node_blk((size_t)n_pad);
+    for (int64_t p = 0; p < n_pad; ++p) {
+        const int node = perm[(size_t)p];
+        const int64_t K = p / MS_BLK;
+        node_blk[(size_t)node] = (int)K;
+        if (node >= n) continue;
+        empty[(size_t)K] = 0;
+        for (int d = 0; d < 3; ++d) {
+            const double v = (double)xyz[(size_t)d * n_pad + node] * sk;
+            lo[(size_t)(3 * K + d)] = std::min(lo[(size_t)(3 * K + d)], v);
+            hi[(size_t)(3 * K + d)] = std::max(hi[(size_t)(3 * K + d)], v);
+        }
+    }
+    const double pers = per * sk;
+    auto live = [&](int64_t I, int64_t J) {
+        if (I == J) return true;
+        if (empty[(size_t)I] || empty[(size_t)J]) return false;  // no real node: all g are 0
+        double d2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double cI = 0.5 * (lo[(size_t)(3 * I + d)] + hi[(size_t)(3 * I + d)]);
+            const double cJ = 0.5 * (lo[(size_t)(3 * J + d)] + hi[(size_t)(3 * J + d)]);
+            const double H = 0.5 * (hi[(size_t)(3 * I + d)] - lo[(size_t)(3 * I + d)]) +
+                             0.5 * (hi[(size_t)(3 * J + d)] - lo[(size_t)(3 * J + d)]);
+            double D = cJ - cI;
+            if (pers > 0.0 && d < 2) D -= pers * std::nearbyint(D / pers);  // nearest image
+            const double gap = std::max(0.0, std::fabs(D) - H);
+            d2 += gap * gap;
+        }
+        return wide * d2 < 160.0 * (1.0 + 1e-4);
+    };
+    std::vector<int> pairs;
+    std::vector<int> ptr((size_t)nb + 1, 0), slots;
+    std::vector<char> lv((size_t)npairs);
+    for (int64_t J = 0; J < nb; ++J)
+        for (int64_t I = 0; I <= J; ++I) {
+            const int64_t t = J * (J + 1) / 2 + I;
+            lv[(size_t)t] = live(I, J) ? 1 : 0;
+            if (lv[(size_t)t]) pairs.push_back((int)t);
+        }
+    for (int64_t K = 0; K < nb; ++K) {
+        for (int64_t S = 0; S < nb; ++S) {
+            const int64_t a = std::min(K, S), b = std::max(K, S);
+            if (lv[(size_t)(b * (b + 1) / 2 + a)]) slots.push_back((int)S);
+        }
+        ptr[(size_t)K + 1] = (int)slots.size();
+    }
+    cudaFree(op->cull_pairs);
+    cudaFree(op->cull_ptr);
+    cudaFree(op->cull_slots);
+    cudaFree(op->node_blk);
+    op->cull_pairs = op->cull_ptr = op->cull_slots = op->node_blk = nullptr;
+    op->mf_cull = 0;
+    NF_CUDA_TRY(cudaMalloc(&op->cull_pairs, sizeof(int) * pairs.size()));
+    NF_CUDA_TRY(cudaMalloc(&op->cull_ptr, sizeof(int) * ptr.size()));
+    NF_CUDA_TRY(cudaMalloc(&op->cull_slots, sizeof(int) * slots.size()));
+    NF_CUDA_TRY(cudaMalloc(&op->node_blk, sizeof(int) * node_blk.size()));
+    NF_CUDA_TRY(cudaMemcpyAsync(op->cull_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, s));
+    NF_CUDA_TRY(cudaMemcpyAsync(op->cull_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, s));
+    NF_CUDA_TRY(cudaMemcpyAsync(op->cull_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, s));
+    NF_CUDA_TRY(cudaMemcpyAsync(op->node_blk, node_blk.data(), sizeof(int) * node_blk.size(), cudaMemcpyHostToDevice,
+                                s));
+    NF_CUDA_TRY(cudaStreamSynchronize(s));
+    op->cull_live = (int64_t)pairs.size();
+    op->mf_cull = 1;
+    destroy_graphs(op);
+    if (live_out) *live_out = op->cull_live;
+    return NF_OK;
+}
+
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
     if (B == 1 && use_sym(op)) {  // one trajectory: symmetric kernel, one partial slot per node block
         NF_TRY(launch_sym(op, 1, 0, s));
         *splits_out = sym_slots(op);
+        if (op->mf_cull) {  // only live pairs ran: add each node's live slots into slot 0
+            cull_reduce_kernel<<<(unsigned)ceil_div(op->n_pad, 256), 256, 0, s>>>(
+                op->partial, op->n_pad, op->node_blk, op->cull_ptr, op->cull_slots);
+            NF_CUDA_TRY(cudaGetLastError());
+            *splits_out = 1;
+        }
         return NF_OK;
     }
     if (B == 1) {  // a small node set: the packed kernel over (row block, column split) items
