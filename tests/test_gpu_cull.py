@@ -52,7 +52,7 @@ def _square(n, seed):
 
 CASES = {
     # narrow Mexican hat on the torus (R = 1, r = 0.4): far blocks cull
-    "torus_narrow": ("torus", (1.0, 0.05, 0.5, 0.1)),
+    "torus_narrow": ("torus", (1.0, 0.02, 0.5, 0.04)),
     # the §4.3 kernel Gauss(1/40) on the periodic square: almost every block pair culls
     "square_paper": ("square", (1.0 / (2 * math.pi / 40 ** 2), math.sqrt(2) / 40, 0.0, 0.1, L)),
     # general width ratio, periodic, moderate width
