@@ -176,10 +176,13 @@ NF_API nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, i
  *                    when it has block pairs for 2/3 of the SMs, else the packed kernel
  *                    (default; the switch is at about 13,300 nodes on 152 SMs);
  *   NF_MF_SYMMETRIC  always the symmetric kernel;
- *   NF_MF_PACKED     always the packed row-block x column-split kernel (ordered pairs).
+ *   NF_MF_PACKED     always the packed row-block x column-split kernel (ordered pairs);
+ *   NF_MF_SYMMETRIC_512, NF_MF_SYMMETRIC_1024   the symmetric kernel with that node-block
+ *                    size (by default the operator's autotuner picks 1,024, or 512 where
+ *                    that measured faster); a change of block size switches culling off.
  * Results agree to FP32 rounding (summation order differs).  Multi-trajectory sums and
  * nf_adjoint are unaffected.  Errors: NF_ERR_ARG (not matrix-free, unknown value). */
-enum { NF_MF_AUTO = 0, NF_MF_SYMMETRIC = 1, NF_MF_PACKED = 2 };
+enum { NF_MF_AUTO = 0, NF_MF_SYMMETRIC = 1, NF_MF_PACKED = 2, NF_MF_SYMMETRIC_512 = 3, NF_MF_SYMMETRIC_1024 = 4 };
 NF_API nf_status nf_operator_mf_schedule(nf_operator *op, int schedule);
 
 /* Block-pair culling for the symmetric single-trajectory schedule (opt-in; off at creation).

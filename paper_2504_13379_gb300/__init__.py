@@ -33,12 +33,12 @@ __all__ = [
     "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
     "DENSE_BF16X2", "DENSE_SYM_FP32", "STATUS", "nf_field_advance", "MODEL_FIELD", "MODEL_DEPRESSION",
     "RATE_SIGMOID", "RATE_SMOOTHSTEP", "FORCE_NONE", "FORCE_MMS_EIGEN", "FORCE_MMS_FLAT", "NeuralFieldRK4",
-    "MF_AUTO", "MF_SYMMETRIC", "MF_PACKED",
+    "MF_AUTO", "MF_SYMMETRIC", "MF_PACKED", "MF_SYMMETRIC_512", "MF_SYMMETRIC_1024",
 ]
 
 MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32 = 0, 1, 2, 4
 FORCE_NONE, FORCE_MMS_EIGEN, FORCE_MMS_FLAT = 0, 1, 2
-MF_AUTO, MF_SYMMETRIC, MF_PACKED = 0, 1, 2
+MF_AUTO, MF_SYMMETRIC, MF_PACKED, MF_SYMMETRIC_512, MF_SYMMETRIC_1024 = 0, 1, 2, 3, 4
 STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINITE", 4: "NF_ERR_TIMEOUT",
           5: "NF_ERR_NOMEM", 6: "NF_ERR_CUDA", 7: "NF_ERR_UNSUPPORTED"}
 
@@ -236,7 +236,8 @@ class Operator:
         return {"rows_per_warp": r.value, "tile_cols": t.value, "splits": s.value}
 
     def mf_schedule(self, schedule: int):
-        """Single-trajectory matrix-free schedule: MF_AUTO, MF_SYMMETRIC or MF_PACKED."""
+        """Single-trajectory matrix-free schedule: MF_AUTO, MF_SYMMETRIC, MF_PACKED, or the
+        symmetric kernel with a fixed node block (MF_SYMMETRIC_512 / MF_SYMMETRIC_1024)."""
         _check(lib().nf_operator_mf_schedule(self.handle, int(schedule)))
         return self
 

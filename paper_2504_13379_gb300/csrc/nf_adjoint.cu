@@ -126,7 +126,7 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     const int64_t n = op->n, n_pad = op->n_pad;
     const size_t BN = (size_t)B * n;
     NF_TRY(ensure_workspace(op, B, mf_splits(op, B)));
-    const int slots = sym_slots(op);  // one W nu slot per node block
+    const int slots = adj_slots(op);  // one W nu slot per 1,024-node block
     const int64_t ncta = sym_pair_count(op);
     const int Cseg = std::min(C, std::max(nsteps, 1));
     float *stages = nullptr, *lam = nullptr, *acc = nullptr, *ubuf = nullptr, *wpart = nullptr, *gpart = nullptr;

@@ -480,10 +480,13 @@ nf_status nf_operator_mf_schedule(nf_operator *op, int schedule) {
     clear_error();
     NF_ARG(op, "op is NULL");
     NF_ARG(op->path == NF_MATRIX_FREE, "the schedule applies to matrix-free operators");
-    NF_ARG(schedule == NF_MF_AUTO || schedule == NF_MF_SYMMETRIC || schedule == NF_MF_PACKED,
-           "unknown schedule %d", schedule);
-    if (op->mf_sched != schedule) destroy_graphs(op);  // captured steps bake in the launch shape
-    op->mf_sched = schedule;
+    NF_ARG(schedule >= NF_MF_AUTO && schedule <= NF_MF_SYMMETRIC_1024, "unknown schedule %d", schedule);
+    const int blk = schedule == NF_MF_SYMMETRIC_512 ? 512 : (schedule == NF_MF_SYMMETRIC_1024 ? 1024 : op->sym_blk);
+    const int sched = schedule >= NF_MF_SYMMETRIC_512 ? NF_MF_SYMMETRIC : schedule;
+    destroy_graphs(op);  // captured steps bake in the launch shape
+    if (blk != op->sym_blk) op->mf_cull = 0;  // the live-pair lists belong to the old blocks
+    op->sym_blk = blk;
+    op->mf_sched = sched;
     return NF_OK;
 }
 

@@ -174,6 +174,7 @@ struct nf_operator {
     int mf_variant = -1;     // launch shape of the packed pair kernel
     int mf_sym_r = 8;        // rows per warp of the symmetric single-trajectory kernel (autotuned)
     int mf_sched = 0;        // NF_MF_AUTO / NF_MF_SYMMETRIC / NF_MF_PACKED
+    int sym_blk = 1024;      // node block of the symmetric kernel (1024, or 512 when autotuned faster)
     // block-pair culling of the symmetric kernel (opt-in, nf_operator_mf_cull)
     int mf_cull = 0;
     int *cull_pairs = nullptr;   // live block-pair indices (ascending)
@@ -236,6 +237,7 @@ SplitPlan mf_plan(nf_operator *op);     // column splits of the multi-trajectory
 int mf_splits(nf_operator *op, int B);  // partial-sum slots of a matrix-free launch over B trajectories
 int64_t sym_pair_count(const nf_operator *op);  // block pairs of the symmetric kernels
 int sym_slots(const nf_operator *op);   // node blocks of the symmetric schedule (W nu slots)
+int adj_slots(const nf_operator *op);   // node blocks of the adjoint kernel (1,024 nodes)
 nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live, int64_t *total, cudaStream_t s);
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
                          float *r2_phys, cudaStream_t s);

@@ -424,23 +424,25 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
 // ----------------------------------------------------------------------------
 // Symmetric single-trajectory kernel.  w(x_i, x_j) = w(x_j, x_i), so every unordered pair
 // is evaluated once and feeds both sums: I_i += w_ij g_j and I_j += w_ij g_i.  Nodes are
-// taken in Morton order (rowperm) and cut into blocks of MS_BLK; one CTA takes a block
+// taken in Morton order (rowperm) and cut into blocks of BLK = MS_BLK (1,024) nodes, or 512
+// where the operator's autotuner measured the smaller blocks faster (mid-size node sets,
+// whose 1,024-node block pairs give too few CTAs); one CTA takes a block
 // pair (I <= J): it gathers block J's coordinates and g into shared memory, its warps
 // sweep block I's rows R at a time (the packed forms above: expanded about the warp's
 // centre when its rows are close, coordinate differences otherwise), accumulate the row
 // sums in registers and the column sums per warp in shared memory.  Row sums of pair
 // (I, J) go to partial slot J, column sums to slot I; a diagonal pair (I = I) sweeps all
 // ordered pairs of the block and writes rows only.  Every (slot, node) entry is written
-// exactly once, and the stage kernel adds the n_pad / MS_BLK slots in a fixed order, so
+// exactly once, and the stage kernel adds the n_pad / BLK slots in a fixed order, so
 // results are deterministic.  Per unordered pair (expanded form, M > 0) this costs one
 // exponential and 9 FMA-pipe lane operations for two ordered pairs.
 constexpr int MS_BLK = 1024;
 constexpr int MS_THREADS = 256;
 constexpr int MS_WARPS = MS_THREADS / 32;
-// shared memory (4-byte words): column block x, y, z, g, node (5 MS_BLK); row block node and
-// precomputed row operands mx, my, mz, h1, h2, f1, f2 (8 MS_BLK); per-pass centre and form
-// (MS_BLK: up to MS_BLK / 4 passes x 4); per-warp column sums (MS_WARPS MS_BLK)
-constexpr size_t MS_SMEM = sizeof(float) * ((5 + 8 + 1 + MS_WARPS) * (size_t)MS_BLK);
+// shared memory (4-byte words): column block x, y, z, g, node (5 BLK); row block node and
+// precomputed row operands mx, my, mz, h1, h2, f1, f2 (8 BLK); per-pass centre and form
+// (BLK: up to BLK / 4 passes x 4); per-warp column sums (MS_WARPS BLK)
+constexpr size_t ms_smem(int blk) { return sizeof(float) * ((5 + 8 + 1 + MS_WARPS) * (size_t)blk); }
 
 // Block pair of CTA t over nb blocks, enumerated as (0,0), (0,1), (1,1), (0,2), ...
 __device__ __forceinline__ void sym_pair(int64_t t, int &I, int &J) {
@@ -481,22 +483,23 @@ __device__ __forceinline__ float warp_reduce_rows(float (&v)[R], int lane, int &
     return v[0];
 }
 
-template <int R, int M>
+template <int R, int M, int BLK>
 __global__ void __launch_bounds__(MS_THREADS, 2)
 mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
               int64_t n_pad, int B, int b_base, float k2, float A1, float A2, float per,
               float *__restrict__ partial, const int *__restrict__ pairs) {
     static_assert(M >= 0 && M <= 4, "form M: 0 general, 1 one Gaussian (A2 = 0), 2-4 width ratio");
     static_assert(R == 4 || R == 8, "rows per warp");
-    constexpr int NPASS = MS_BLK / R;
+    static_assert(BLK == 512 || BLK == 1024, "block size");
+    constexpr int NPASS = BLK / R;
     extern __shared__ __align__(16) float ms_smem[];
-    float *xs = ms_smem, *ys = xs + MS_BLK, *zs = ys + MS_BLK, *gs = zs + MS_BLK;
-    int *cnode = reinterpret_cast<int *>(gs + MS_BLK);
-    int *rnode = cnode + MS_BLK;
-    float *rmx = reinterpret_cast<float *>(rnode + MS_BLK), *rmy = rmx + MS_BLK, *rmz = rmy + MS_BLK;
-    float *rh1 = rmz + MS_BLK, *rh2 = rh1 + MS_BLK, *rf1 = rh2 + MS_BLK, *rf2 = rf1 + MS_BLK;
-    float4 *pc = reinterpret_cast<float4 *>(rf2 + MS_BLK);  // per pass: centre, form (w = 1: expanded)
-    float *colacc = reinterpret_cast<float *>(pc + MS_BLK / 4);  // [MS_WARPS][MS_BLK]
+    float *xs = ms_smem, *ys = xs + BLK, *zs = ys + BLK, *gs = zs + BLK;
+    int *cnode = reinterpret_cast<int *>(gs + BLK);
+    int *rnode = cnode + BLK;
+    float *rmx = reinterpret_cast<float *>(rnode + BLK), *rmy = rmx + BLK, *rmz = rmy + BLK;
+    float *rh1 = rmz + BLK, *rh2 = rh1 + BLK, *rf1 = rh2 + BLK, *rf2 = rf1 + BLK;
+    float4 *pc = reinterpret_cast<float4 *>(rf2 + BLK);  // per pass: centre, form (w = 1: expanded)
+    float *colacc = reinterpret_cast<float *>(pc + BLK / 4);  // [MS_WARPS][BLK]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int I, J;
     sym_pair(pairs ? (int64_t)__ldg(pairs + blockIdx.x) : (int64_t)blockIdx.x, I, J);  // pairs: live list
@@ -504,12 +507,12 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     const int b = b_base + blockIdx.z;
     const float *g = g_all + (int64_t)b * n_pad;
     const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
-    const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
+    const int64_t cbase = (int64_t)J * BLK, rbase = (int64_t)I * BLK;
     // exponent units: s1 (coordinates as stored), or s2 when M > 0 (times sk = s1 / s2,
     // applied once here, so r^2 and s_ij arrive as the exponent of e2)
     const float sk = M >= 2 ? sqrtf(k2) : 1.f;  // M = 1: one Gaussian, units of s1
     // gather the column block, and the row block's raw data (x, y, z, g in mx, my, mz, h1)
-    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+    for (int k = tid; k < BLK; k += MS_THREADS) {
         const int node = __ldg(rowperm + cbase + k);
         cnode[k] = node;
         xs[k] = X[node] * sk;
@@ -523,7 +526,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         rmz[k] = Z[rn] * sk;
         rh1[k] = g[rn];
     }
-    for (int k = tid; k < MS_WARPS * MS_BLK; k += MS_THREADS) colacc[k] = 0.f;
+    for (int k = tid; k < MS_WARPS * BLK; k += MS_THREADS) colacc[k] = 0.f;
     __syncthreads();
     // period in the units of the gathered coordinates (times sk)
     const float pers = per * sk, ipers = per > 0.f ? 1.f / pers : 0.f;
@@ -593,7 +596,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     const u64 ipp = f2_pack(ipers, ipers), npp = f2_pack(-pers, -pers), mgp = f2_pack(kRintMagic, kRintMagic);
     const float4 *xs4 = reinterpret_cast<const float4 *>(xs), *ys4 = reinterpret_cast<const float4 *>(ys);
     const float4 *zs4 = reinterpret_cast<const float4 *>(zs), *gs4 = reinterpret_cast<const float4 *>(gs);
-    float4 *cw4 = reinterpret_cast<float4 *>(colacc + warp * MS_BLK);
+    float4 *cw4 = reinterpret_cast<float4 *>(colacc + warp * BLK);
     float *out_rows = partial + ((int64_t)J * B + b) * n_pad;
     auto lo2 = [](float4 v) { return f2_pack(v.x, v.y); };
     auto hi2 = [](float4 v) { return f2_pack(v.z, v.w); };
@@ -643,7 +646,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         auto sweep_local = [&](auto tag) {
             constexpr bool P = decltype(tag)::value;
 #pragma unroll 1
-            for (int q = lane; q < MS_BLK / 4; q += 32) {
+            for (int q = lane; q < BLK / 4; q += 32) {
                 const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
                 u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
                 u64 yt[2] = {f2_sub(lo2(y4), cyp), f2_sub(hi2(y4), cyp)};
@@ -684,7 +687,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         auto sweep_diff = [&](auto tag_c, auto tag_w) {
             constexpr bool CEN = decltype(tag_c)::value, PW = decltype(tag_w)::value;
 #pragma unroll 1
-            for (int q = lane; q < MS_BLK / 4; q += 32) {
+            for (int q = lane; q < BLK / 4; q += 32) {
                 const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
                 u64 xj[2] = {lo2(x4), hi2(x4)}, yj[2] = {lo2(y4), hi2(y4)};
                 const u64 zj[2] = {lo2(z4), hi2(z4)};
@@ -750,10 +753,10 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     if (diag) return;
     __syncthreads();
     float *out_cols = partial + ((int64_t)I * B + b) * n_pad;
-    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+    for (int k = tid; k < BLK; k += MS_THREADS) {
         float v = 0.f;
 #pragma unroll
-        for (int w = 0; w < MS_WARPS; ++w) v += colacc[w * MS_BLK + k];
+        for (int w = 0; w < MS_WARPS; ++w) v += colacc[w * BLK + k];
         out_cols[cnode[k]] = v;
     }
 }
@@ -1042,9 +1045,10 @@ static cudaError_t set_mf_attr() {
 }
 
 // Opt every pair-kernel instance into its shared-memory size (outside any capture).
-template <int R, int M>
+template <int R, int M, int BLK = 1024>
 static cudaError_t set_sym_attr() {
-    return cudaFuncSetAttribute(mf_sym_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MS_SMEM);
+    return cudaFuncSetAttribute(mf_sym_kernel<R, M, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ms_smem(BLK));
 }
 
 template <int R, int M>
@@ -1068,6 +1072,11 @@ nf_status mf_init_attrs() {
     NF_CUDA_TRY((set_sym_attr<8, 2>()));
     NF_CUDA_TRY((set_sym_attr<8, 3>()));
     NF_CUDA_TRY((set_sym_attr<8, 4>()));
+    NF_CUDA_TRY((set_sym_attr<8, 0, 512>()));
+    NF_CUDA_TRY((set_sym_attr<8, 1, 512>()));
+    NF_CUDA_TRY((set_sym_attr<8, 2, 512>()));
+    NF_CUDA_TRY((set_sym_attr<8, 3, 512>()));
+    NF_CUDA_TRY((set_sym_attr<8, 4, 512>()));
     NF_CUDA_TRY((set_mf_attr<1, 2>()));
     NF_CUDA_TRY((set_mf_attr<2, 2>()));
     NF_CUDA_TRY((set_mf_attr<4, 2>()));
@@ -1176,43 +1185,54 @@ static nf_status launch_mf_packed(nf_operator *op, int B, int b_base, int groups
 static int default_variant(int64_t n_pad) { return n_pad >= 16384 ? 3 : 0; }
 
 // ---- symmetric kernel launch (B = 1)
+// Block pairs and slots of the forward symmetric kernel at the operator's block size
+// (1,024 nodes, or 512 where the autotuner found the smaller blocks faster: more CTAs for
+// mid-size node sets).
 static int64_t sym_pairs(const nf_operator *op) {
+    const int64_t nb = op->n_pad / op->sym_blk;
+    return nb * (nb + 1) / 2;
+}
+static int64_t sym_pairs_1024(const nf_operator *op) {
     const int64_t nb = op->n_pad / MS_BLK;
     return nb * (nb + 1) / 2;
 }
 
-template <int R>
-static void launch_sym_r(nf_operator *op, int B, int b_base, cudaStream_t s) {
+template <int R, int BLK>
+static void launch_sym_rb(nf_operator *op, int B, int b_base, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
     dim3 grid((unsigned)(op->mf_cull ? op->cull_live : sym_pairs(op)), 1, 1);
+    const size_t smem = ms_smem(BLK);
 #define NF_SYM_ARGS                                                                                       \
     op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, scaled_period(k), op->partial, \
         (op->mf_cull ? op->cull_pairs : nullptr)
     switch (sym_form(k)) {
-        case 1: mf_sym_kernel<R, 1><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
-        case 2: mf_sym_kernel<R, 2><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
-        case 3: mf_sym_kernel<R, 3><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
-        case 4: mf_sym_kernel<R, 4><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
-        default: mf_sym_kernel<R, 0><<<grid, MS_THREADS, MS_SMEM, s>>>(NF_SYM_ARGS); break;
+        case 1: mf_sym_kernel<R, 1, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        case 2: mf_sym_kernel<R, 2, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        case 3: mf_sym_kernel<R, 3, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        case 4: mf_sym_kernel<R, 4, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        default: mf_sym_kernel<R, 0, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
     }
 #undef NF_SYM_ARGS
 }
 
 static nf_status launch_sym(nf_operator *op, int B, int b_base, cudaStream_t s) {
-    if (op->mf_sym_r == 4)
-        launch_sym_r<4>(op, B, b_base, s);
+    if (op->sym_blk == 512)
+        launch_sym_rb<8, 512>(op, B, b_base, s);
+    else if (op->mf_sym_r == 4)
+        launch_sym_rb<4, 1024>(op, B, b_base, s);
     else
-        launch_sym_r<8>(op, B, b_base, s);
+        launch_sym_rb<8, 1024>(op, B, b_base, s);
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
 }
 
-// Adjoint pair sums of trajectory b over all block pairs (see adj_sym_kernel): W nu slots
-// into wpart [n_pad / MS_BLK][B][n_pad], parameter sums into gpart [B][pairs][4] with r^2 in
-// exponent units; *r2_phys receives the factor to physical r^2.
-int64_t sym_pair_count(const nf_operator *op) { return sym_pairs(op); }
-int sym_slots(const nf_operator *op) { return (int)(op->n_pad / MS_BLK); }
+// Adjoint pair sums of trajectory b over all 1,024-node block pairs (see adj_sym_kernel):
+// W nu slots into wpart [n_pad / 1024][B][n_pad], parameter sums into gpart [B][pairs][4]
+// with r^2 in exponent units; *r2_phys receives the factor to physical r^2.
+int64_t sym_pair_count(const nf_operator *op) { return sym_pairs_1024(op); }
+int adj_slots(const nf_operator *op) { return (int)(op->n_pad / MS_BLK); }
+int sym_slots(const nf_operator *op) { return (int)(op->n_pad / op->sym_blk); }
 
 // One trajectory takes the symmetric kernel when it has at least 2/3 as many block pairs as
 // the GPU has SMs; smaller node sets (below ~13,300 nodes on 152 SMs) have too few block
@@ -1222,7 +1242,7 @@ int sym_slots(const nf_operator *op) { return (int)(op->n_pad / MS_BLK); }
 static bool use_sym(const nf_operator *op) {
     if (op->mf_sched == NF_MF_SYMMETRIC) return true;
     if (op->mf_sched == NF_MF_PACKED) return false;
-    return 3 * sym_pairs(op) >= 2 * (int64_t)num_sms();
+    return 3 * sym_pairs_1024(op) >= 2 * (int64_t)num_sms();
 }
 
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
@@ -1232,7 +1252,7 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
     const int m = mf_width_ratio(k);
     const double L2E = 1.4426950408889634;
     *r2_phys = (float)((m > 0 ? (double)k.s2 * k.s2 : (double)k.s1 * k.s1) / L2E);
-    dim3 grid((unsigned)sym_pairs(op), 1, 1);
+    dim3 grid((unsigned)sym_pairs_1024(op), 1, 1);
     const size_t smem = AS_SMEM_FLOATS * sizeof(float);
 #define NF_ADJ_ARGS op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, scaled_period(k), wpart, gpart
     switch (m) {
@@ -1269,7 +1289,7 @@ void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits) {
         return;
     }
     *R = op->mf_sym_r;
-    *TJ = MS_BLK;
+    *TJ = op->sym_blk;
     *splits = sym_slots(op);
 }
 
@@ -1281,27 +1301,35 @@ static int mf_rows_per_warp(int64_t n_pad) { return n_pad >= 16384 ? 4 : 2; }
 // outside any stream capture.
 nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int64_t, int>, int> cache;
+    static std::map<std::tuple<int, int64_t, int>, std::pair<int, int>> cache;
     op->mf_variant = default_variant(op->n_pad);
-    if (3 * sym_pairs(op) < 2 * (int64_t)num_sms()) return NF_OK;  // packed by default: keep 8 rows per warp
+    if (3 * sym_pairs_1024(op) < 2 * (int64_t)num_sms()) return NF_OK;  // packed by default
     const auto key = std::make_tuple(op->device, op->n_pad, sym_form(op->kp));
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            op->mf_sym_r = it->second;
+            op->mf_sym_r = it->second.first;
+            op->sym_blk = it->second.second;
             return NF_OK;
         }
     }
-    NF_TRY(ensure_workspace(op, 1, mf_splits(op, 1)));
+    NF_TRY(ensure_workspace(op, 1, (int)(op->n_pad / 512)));  // room for either block size
     NF_CUDA_TRY(cudaMemsetAsync(op->g, 0, sizeof(float) * op->n_pad, s));
     cudaEvent_t e0, e1;
     NF_CUDA_TRY(cudaEventCreate(&e0));
     NF_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_r = 8;
-    for (int r : {4, 8}) {
-        op->mf_sym_r = r;
+    int best_r = 8, best_blk = 1024;
+    // (rows per warp, block size): 512-node blocks only where 1,024-node pairs fill fewer than
+    // two waves of two CTAs per SM (n below ~35,000); measured on GB300 they win there (n =
+    // 20,000: 0.177 vs 0.198 ms) and lose badly on large sets (n = 1e5: 7.2 vs 1.8 ms)
+    const bool try512 = sym_pairs_1024(op) < 4 * (int64_t)num_sms();
+    const std::pair<int, int> shapes[3] = {{4, 1024}, {8, 1024}, {8, 512}};
+    for (const auto &sh : shapes) {
+        if (sh.second == 512 && !try512) continue;
+        op->mf_sym_r = sh.first;
+        op->sym_blk = sh.second;
         NF_TRY(launch_sym(op, 1, 0, s));  // warm-up
         NF_CUDA_TRY(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 2; ++rep) NF_TRY(launch_sym(op, 1, 0, s));
@@ -1311,14 +1339,16 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
         NF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) {
             best = ms;
-            best_r = r;
+            best_r = sh.first;
+            best_blk = sh.second;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     op->mf_sym_r = best_r;
+    op->sym_blk = best_blk;
     std::lock_guard<std::mutex> lock(mu);
-    cache[key] = best_r;
+    cache[key] = {best_r, best_blk};
     return NF_OK;
 }
 
@@ -1340,7 +1370,7 @@ __global__ void cull_reduce_kernel(float *__restrict__ partial, int64_t n_pad, c
 }
 
 nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live_out, int64_t *total_out, cudaStream_t s) {
-    const int64_t n = op->n, n_pad = op->n_pad, nb = n_pad / MS_BLK, npairs = nb * (nb + 1) / 2;
+    const int64_t n = op->n, n_pad = op->n_pad, blk = op->sym_blk, nb = n_pad / blk, npairs = nb * (nb + 1) / 2;
     if (total_out) *total_out = npairs;
     if (live_out) *live_out = npairs;
     if (!enable) {
@@ -1365,7 +1395,7 @@ nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live_out, int64_t *t
     std::vector<int> node_blk((size_t)n_pad);
     for (int64_t p = 0; p < n_pad; ++p) {
         const int node = perm[(size_t)p];
-        const int64_t K = p / MS_BLK;
+        const int64_t K = p / blk;
         node_blk[(size_t)node] = (int)K;
         if (node >= n) continue;
         empty[(size_t)K] = 0;

@@ -99,6 +99,28 @@ def test_cull_bit_identical_and_oracle(nf, case):
     np.testing.assert_array_equal(a, c)
 
 
+@pytest.mark.parametrize("case", ["square_paper", "torus_narrow"])
+def test_cull_512_blocks(nf, case):
+    """Culling over 512-node blocks: bit-identical to the unculled 512-node sum."""
+    geom, kern = CASES[case]
+    n = 20000
+    if geom == "torus":
+        X, q, ns = _torus(n, 5)
+    else:
+        X, q = _square(n, 6)
+    u = np.random.default_rng(9).normal(0.3, 0.4, size=(1, len(q))).astype(np.float32)
+    full = nf.Operator(dev(X), dev(q), kern, 0).mf_schedule(nf.MF_SYMMETRIC_512)
+    cull = nf.Operator(dev(X), dev(q), kern, 0).mf_schedule(nf.MF_SYMMETRIC_512)
+    live, total = cull.mf_cull(True)
+    assert live < total and total == (-(-len(q) // 1024) * 2) * ((-(-len(q) // 1024) * 2) + 1) // 2
+    a = nf.nf_nonlocal_apply(full, dev(u), 20.0, 0.2).cpu().numpy()
+    b = nf.nf_nonlocal_apply(cull, dev(u), 20.0, 0.2).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    rows = np.sort(np.random.default_rng(8).choice(len(q), 300, replace=False))
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)), rows=rows)
+    assert rel_l2(b[:, rows], want) < REL_L2
+
+
 def test_cull_separated_clusters(nf):
     """Two clusters far apart: every cross pair culls and each cluster sums only itself."""
     rng = np.random.default_rng(3)

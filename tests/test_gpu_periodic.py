@@ -96,15 +96,16 @@ def test_periodic_forms_blobs(nf, kern):
     assert np.abs(got - want).max() / np.abs(want).max() < REL_L2
 
 
+@pytest.mark.parametrize("sched", [4, 3])
 @pytest.mark.parametrize("kname", sorted(KERNELS))
 @pytest.mark.parametrize("n", [3001, 1025])
-def test_periodic_symmetric_schedule(nf, kname, n):
+def test_periodic_symmetric_schedule(nf, kname, n, sched):
     """The symmetric kernel's periodic forms on small node sets (the automatic schedule
-    would take the packed kernel there)."""
+    would take the packed kernel there), with 1,024- and 512-node blocks."""
     kern = KERNELS[kname]
     rng, X, q = _square(n, 40 + n)
     u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
-    op = nf.Operator(dev(X), dev(q), kern, 0).mf_schedule(nf.MF_SYMMETRIC)
+    op = nf.Operator(dev(X), dev(q), kern, 0).mf_schedule(sched)
     got = nf.nf_nonlocal_apply(op, dev(u), 20.0, 0.2).cpu().numpy()
     op.check()
     want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
