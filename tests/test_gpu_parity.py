@@ -324,3 +324,35 @@ def test_mf_schedule_switch_and_auto(nf):
         want = oracle.rk4(f32(X), f32(q), f32(u0), (1.0, 0.3, 0.5, 0.6), 20.0, float(np.float32(0.2)), 0.0, 0.05, 3)
         for r in res:
             assert rel_l2(r, want) < REL_L2
+
+
+@pytest.mark.parametrize("B", [2, 3])
+def test_symmetric_kernel_several_trajectories(nf, B):
+    """Up to three trajectories share one symmetric launch (a grid z per trajectory); their
+    sums and RK4 steps match the oracle, with and without block-pair culling."""
+    rng = np.random.default_rng(B)
+    ns = nodesets.torus_lattice(16000, seed=B)
+    X = ns.nodes.astype(np.float32)
+    n = ns.n
+    q = np.full(n, ns.area / n, dtype=np.float32)
+    u = rng.normal(0.3, 0.4, size=(B, n)).astype(np.float32)
+    beta = rng.uniform(10, 40, B).astype(np.float32)
+    theta = rng.uniform(0.1, 0.3, B).astype(np.float32)
+    kern = (1.0, 0.02, 0.5, 0.04)  # narrow enough that far block pairs cull on this torus
+    rows = np.sort(rng.choice(n, 300, replace=False))
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), f32(beta), f32(theta), rows=rows)
+    op = _op(nf, X, q, kern, 0).mf_schedule(nf.MF_SYMMETRIC)
+    got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), dev(beta, torch.float32), dev(theta, torch.float32))
+    op.check()
+    got = got.cpu().numpy()
+    assert rel_l2(got[:, rows], want) < REL_L2
+    live, total = op.mf_cull(True)
+    assert live < total
+    got_c = nf.nf_nonlocal_apply(op, dev(u, torch.float32), dev(beta, torch.float32), dev(theta, torch.float32))
+    np.testing.assert_array_equal(got_c.cpu().numpy(), got)
+    ua, ub = dev(u, torch.float32), dev(u, torch.float32)
+    nf.nf_rk4_advance(op, ua, 0.0, 0.02, 2, dev(beta, torch.float32), dev(theta, torch.float32))
+    op.mf_cull(False)
+    nf.nf_rk4_advance(op, ub, 0.0, 0.02, 2, dev(beta, torch.float32), dev(theta, torch.float32))
+    op.check()
+    np.testing.assert_array_equal(ua.cpu().numpy(), ub.cpu().numpy())
