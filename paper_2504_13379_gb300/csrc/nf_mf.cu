@@ -1085,6 +1085,8 @@ nf_status mf_init_attrs() {
     NF_CUDA_TRY((set_mf_attr<2, 4>()));
     NF_CUDA_TRY((set_mf_attr<4, 4>()));
     NF_CUDA_TRY((set_mf_attr<8, 4>()));
+    NF_CUDA_TRY((set_mf_attr<16, 2>()));
+    NF_CUDA_TRY((set_mf_attr<16, 4>()));
     return NF_OK;
 }
 
@@ -1504,12 +1506,14 @@ nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out
             st = launch_mf_packed(op, B, b, groups, pl, s);
         } else if (R == 4) {
             switch (nb) {
+                case 16: st = launch_mf_group<16, 4>(op, B, b, groups, spl, s); break;
                 case 8: st = launch_mf_group<8, 4>(op, B, b, groups, spl, s); break;
                 case 4: st = launch_mf_group<4, 4>(op, B, b, groups, spl, s); break;
                 default: st = launch_mf_group<2, 4>(op, B, b, groups, spl, s); break;
             }
         } else {
             switch (nb) {
+                case 16: st = launch_mf_group<16, 2>(op, B, b, groups, spl, s); break;
                 case 8: st = launch_mf_group<8, 2>(op, B, b, groups, spl, s); break;
                 case 4: st = launch_mf_group<4, 2>(op, B, b, groups, spl, s); break;
                 default: st = launch_mf_group<2, 2>(op, B, b, groups, spl, s); break;
@@ -1518,6 +1522,7 @@ nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out
         b += groups * nb;
         return st;
     };
+    NF_TRY(run(16));
     NF_TRY(run(8));
     NF_TRY(run(4));
     NF_TRY(run(2));

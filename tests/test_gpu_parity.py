@@ -127,7 +127,7 @@ def _op(nf, X, q, kernel, path):
 
 
 @pytest.mark.parametrize("path", [0, 1, 2, 4])
-@pytest.mark.parametrize("n,B", [(3001, 1), (2500, 3), (1100, 7), (5, 2), (1, 1), (2048, 2)])
+@pytest.mark.parametrize("n,B", [(3001, 1), (2500, 3), (1100, 7), (5, 2), (1, 1), (2048, 2), (1500, 19), (1100, 35)])
 def test_nonlocal_apply_matches_oracle(nf, path, n, B):
     rng = np.random.default_rng(n + B)
     X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
