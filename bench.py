@@ -221,8 +221,34 @@ def cpu_baseline(wl, q32, seconds, gpu_sums):
     want = np.asarray(oracle.nonlocal_sum(x, q32, u, kern, beta, theta, rows=sel)).ravel()
     dt = time.perf_counter() - t
     acc = {p: float(np.linalg.norm(got[sel] - want) / np.linalg.norm(want)) for p, got in gpu_sums.items()}
-    return {"value": rows * wl.n / dt, "unit": "pair-evals/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one nonlocal stage on {rows} random rows x {wl.n} columns (FP64, {dt:.1f} s)"}, acc
+    cores = oracle.num_threads()
+    # the same sum on one thread, on a tenth of the sample
+    oracle.set_threads(1)
+    try:
+        sel1 = sel[: max(16, rows // (10 * max(1, cores // 16)))]
+        t = time.perf_counter()
+        oracle.nonlocal_sum(x, q32, u, kern, beta, theta, rows=sel1)
+        dt1 = time.perf_counter() - t
+    finally:
+        oracle.set_threads(0)
+    # setup (stencils + weights) on a sample of elements, all cores
+    ns = wl.ns
+    esel = np.random.default_rng(2).choice(ns.m, 2000, replace=False)
+    t = time.perf_counter()
+    st = oracle.knn(ns.nodes, ns.tris, wl.k, elems=esel)
+    nbr = oracle.tri_neighbors(ns.tris)
+    for e, sten in zip(esel, st):
+        oracle.surface_element_weights(ns.nodes, ns.normals, ns.tris, nbr, int(e), sten, wl.deg)
+    dts = time.perf_counter() - t
+    return {"value": rows * wl.n / dt, "unit": "pair-evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"one nonlocal stage on {rows} random rows x {wl.n} columns (FP64, {dt:.1f} s)",
+            "single_thread": {"value": len(sel1) * wl.n / dt1, "unit": "pair-evals/s", "cores": 1,
+                              "sample": f"{len(sel1)} rows x {wl.n} columns ({dt1:.1f} s)"},
+            "setup": {"elements_per_s": len(esel) / dts, "elements": int(ns.m),
+                      "extrapolated_full_setup_s": ns.m / (len(esel) / dts),
+                      "sample": f"stencils (k = {wl.k}) and surface weights (deg {wl.deg}) of 2000 random "
+                                f"elements, one element after another ({dts:.1f} s); the per-element weights "
+                                "run serially in this sample"}}, acc
 
 
 def batched_accuracy(wls, xs, qs, u0, beta, theta, got, rows_per_group=8):

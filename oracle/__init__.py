@@ -66,6 +66,8 @@ def lib():
         L.or_mms_sphere_solution.argtypes = [_dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_double, _dp]
         L.or_num_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_set_threads.restype = None
         L.or_mms_flat_solution.argtypes = [_dp, C.c_int64, C.c_double, _dp, C.c_double, C.c_double, C.c_double,
                                            C.c_double, C.c_double, _dp]
         L.or_mms_flat_solution.restype = None
@@ -98,6 +100,11 @@ def _i64(a):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_threads(n: int = 0) -> None:
+    """Thread count of the oracle's OpenMP loops (0: the default); results do not depend on it."""
+    lib().or_set_threads(int(n))
 
 
 # ---------------------------------------------------------------------------- §3.1

@@ -43,6 +43,18 @@
 #define OR_MAXK 128
 #define OR_MAXP 28  /* (deg+1)(deg+2)/2 for deg <= 6 */
 
+/* Threads of the OpenMP loops (timing only: every result is the same for any count,
+ * each output being reduced in a fixed order).  n <= 0 restores the default. */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    static int dflt = 0;
+    if (!dflt) dflt = omp_get_max_threads();
+    omp_set_num_threads(n > 0 ? n : dflt);
+#else
+    (void)n;
+#endif
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -494,3 +494,19 @@ def test_adjoint_matches_central_differences(rng):
         fd = (oracle.loss(X, q, up, kp, beta, theta, 0.0, dt, N, target)
               - oracle.loss(X, q, um, kp, beta, theta, 0.0, dt, N, target)) / (2 * h)
         assert gu[b, i] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_oracle_thread_count_does_not_change_results():
+    """The oracle's OpenMP loops reduce every output in a fixed order: one thread and all
+    threads give bit-identical sums (the bench times both)."""
+    rng = np.random.default_rng(12)
+    x = rng.uniform(-1, 1, (700, 3))
+    q = rng.uniform(0.5, 1.5, 700)
+    u = rng.normal(size=(2, 700))
+    a = oracle.nonlocal_sum(x, q, u, (1.0, 0.3, 0.5, 0.6), [10.0, 20.0], [0.1, 0.2])
+    oracle.set_threads(1)
+    try:
+        b = oracle.nonlocal_sum(x, q, u, (1.0, 0.3, 0.5, 0.6), [10.0, 20.0], [0.1, 0.2])
+    finally:
+        oracle.set_threads(0)
+    np.testing.assert_array_equal(a, b)
