@@ -587,9 +587,13 @@ __global__ void __launch_bounds__(QW_THREADS) quad_element_kernel(QwArgs a) {
     }
     __syncthreads();
 
-    // assemble the saddle system of Eq. (3.4) and its right-hand side
+    // assemble the saddle system of Eq. (3.4) and its right-hand side; the matrix is
+    // symmetric, so each entry of the upper triangle is computed once and mirrored (the
+    // kernel is bound by the FP64 pipe, and the r^3 entries' square roots dominate the
+    // assembly)
     for (int idx = tid; idx < N * N; idx += blockDim.x) {
         const int r = idx / N, c = idx % N;
+        if (c < r) continue;
         double v;
         if (r < k && c < k) {
             const double dx = xi[2 * r] - xi[2 * c], dy = xi[2 * r + 1] - xi[2 * c + 1];
@@ -603,6 +607,7 @@ __global__ void __launch_bounds__(QW_THREADS) quad_element_kernel(QwArgs a) {
             v = 0.0;
         }
         M[r * ld + c] = v;
+        M[c * ld + r] = v;
     }
     for (int r = tid; r < N; r += blockDim.x)
         z[r] = (r < k) ? tri_r3_integral(xi[2 * r], xi[2 * r + 1], tv)
