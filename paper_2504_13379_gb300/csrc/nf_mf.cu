@@ -442,7 +442,7 @@ constexpr int MS_WARPS = MS_THREADS / 32;
 // shared memory (4-byte words): column block x, y, z, g, node (5 BLK); row block node and
 // precomputed row operands mx, my, mz, h1, h2, f1, f2 (8 BLK); per-pass centre and form
 // (BLK: up to BLK / 4 passes x 4); per-warp column sums (MS_WARPS BLK)
-constexpr size_t ms_smem(int blk) { return sizeof(float) * ((5 + 8 + 1 + MS_WARPS) * (size_t)blk); }
+constexpr size_t ms_smem_bytes(int blk) { return sizeof(float) * ((5 + 8 + 1 + MS_WARPS) * (size_t)blk); }
 
 // Block pair of CTA t over nb blocks, enumerated as (0,0), (0,1), (1,1), (0,2), ...
 __device__ __forceinline__ void sym_pair(int64_t t, int &I, int &J) {
@@ -1048,7 +1048,7 @@ static cudaError_t set_mf_attr() {
 template <int R, int M, int BLK = 1024>
 static cudaError_t set_sym_attr() {
     return cudaFuncSetAttribute(mf_sym_kernel<R, M, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ms_smem(BLK));
+                                (int)ms_smem_bytes(BLK));
 }
 
 template <int R, int M>
@@ -1205,7 +1205,7 @@ static void launch_sym_rb(nf_operator *op, int B, int b_base, cudaStream_t s) {
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
     // blockIdx.z: trajectory b_base + z of the B in the partial-sum layout
     dim3 grid((unsigned)(op->mf_cull ? op->cull_live : sym_pairs(op)), 1, (unsigned)(B - b_base));
-    const size_t smem = ms_smem(BLK);
+    const size_t smem = ms_smem_bytes(BLK);
 #define NF_SYM_ARGS                                                                                       \
     op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, scaled_period(k), op->partial, \
         (op->mf_cull ? op->cull_pairs : nullptr)
