@@ -24,7 +24,6 @@ paper passage it follows:
 from __future__ import annotations
 
 import ctypes as C
-import os
 
 import numpy as np
 

@@ -5,7 +5,6 @@ Bars: stencil indices bit-exact; quadrature weights within 1e-12 relative
 (max-norm); FP32 nonlocal sums and trajectories within 1e-5 relative L2 per
 trajectory.  The oracle always receives the FP32-rounded values the GPU sees.
 """
-import math
 
 import numpy as np
 import pytest

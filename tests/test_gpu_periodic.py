@@ -9,7 +9,6 @@ import numpy as np
 import pytest
 import torch
 
-import nodesets
 import oracle
 
 pytestmark = pytest.mark.gpu

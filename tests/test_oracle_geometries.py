@@ -5,7 +5,6 @@ order of the appended polynomials in n^{-1/2}.  References come from high-accura
 parameter-space quadrature of the exact surfaces (nodesets), independent of the oracle."""
 import math
 
-import numpy as np
 import pytest
 
 import nodesets
