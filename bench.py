@@ -883,21 +883,23 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches_total,
     }
-    if not args.no_batched:
+    # the further sections are measured on rank 0 only (they are not part of `value`)
+    extra = rank == 0
+    if extra and not args.no_batched:
         line["batched"] = run_batched(args, dev, args.steps)
         line["gpu_launches"] += 4 * args.steps  # tensor-core path: one grouped GEMM per stage
-    if not args.no_adjoint:
+    if extra and not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, dev)
-    if not args.no_models:
+    if extra and not args.no_models:
         line["models"] = run_models(args, dev, wl, x32, q32, u0)
-    if not args.no_geometries:
+    if extra and not args.no_geometries:
         line["geometries"] = run_geometries(dev)
-    if not args.no_periodic:
+    if extra and not args.no_periodic:
         line["periodic"] = run_periodic(dev)
         line["culling"] = run_culling(args, dev, wl, x32, q32, u0)
-    if not args.no_configs:
+    if extra and not args.no_configs:
         line["configs"] = run_configs(dev)
-    if args.convergence:
+    if extra and args.convergence:
         line["convergence"] = run_convergence(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], acc = cpu_baseline(wl, q32.double().cpu().numpy(), args.cpu_seconds, first_sums)
