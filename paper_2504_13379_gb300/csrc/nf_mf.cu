@@ -850,7 +850,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             spread = fmaxf(spread, dx * dx + dy * dy + dz * dz);
         }
         // the threshold in units of s1; periodic distances take the difference form
-        const bool local = spread <= kMfLocalSpread * sk * sk && !(per > 0.f);
+        const bool local = spread <= kSymLocalSpread * sk * sk && !(per > 0.f);
         pc[ps] = make_float4(cx, cy, cz, local ? 1.f : 0.f);
         const float lsc = -2.f;
 #pragma unroll
