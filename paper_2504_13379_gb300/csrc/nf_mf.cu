@@ -1257,10 +1257,23 @@ constexpr int kSymMaxB = 3;
 // pairs to fill the GPU and take the packed row-block x column-split kernel instead, which
 // evaluates ordered pairs but spreads them over many more CTAs (measured crossover on GB300:
 // packed 0.119 ms vs symmetric 0.130 ms at n = 12,000; 0.155 vs 0.131 ms at n = 16,384).
+// The automatic schedule also keeps the symmetric partial sums (one slot of n_pad floats per
+// 1,024-node block, growing as n^2) within an eighth of the device memory: beyond that (n
+// above about 3 million on a GB300) the packed kernel, whose layout grows with its column
+// splits only, takes over.
+static bool sym_layout_fits(const nf_operator *op) {
+    static size_t budget = 0;
+    if (!budget) {
+        size_t freeb = 0, total = 0;
+        budget = (cudaMemGetInfo(&freeb, &total) == cudaSuccess && total > 0) ? total / 8 : ((size_t)8 << 30);
+    }
+    return (double)(op->n_pad / MS_BLK) * (double)op->n_pad * sizeof(float) <= (double)budget;
+}
+
 static bool use_sym(const nf_operator *op) {
     if (op->mf_sched == NF_MF_SYMMETRIC) return true;
     if (op->mf_sched == NF_MF_PACKED) return false;
-    return 3 * sym_pairs_1024(op) >= 2 * (int64_t)num_sms();
+    return 3 * sym_pairs_1024(op) >= 2 * (int64_t)num_sms() && sym_layout_fits(op);
 }
 
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
@@ -1321,7 +1334,8 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     static std::mutex mu;
     static std::map<std::tuple<int, int64_t, int>, std::pair<int, int>> cache;
     op->mf_variant = default_variant(op->n_pad);
-    if (3 * sym_pairs_1024(op) < 2 * (int64_t)num_sms()) return NF_OK;  // packed by default
+    if (3 * sym_pairs_1024(op) < 2 * (int64_t)num_sms() || !sym_layout_fits(op))
+        return NF_OK;  // packed by default
     const auto key = std::make_tuple(op->device, op->n_pad, sym_form(op->kp));
     {
         std::lock_guard<std::mutex> lock(mu);
@@ -1332,8 +1346,6 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
             return NF_OK;
         }
     }
-    NF_TRY(ensure_workspace(op, 1, (int)(op->n_pad / 512)));  // room for either block size
-    NF_CUDA_TRY(cudaMemsetAsync(op->g, 0, sizeof(float) * op->n_pad, s));
     cudaEvent_t e0, e1;
     NF_CUDA_TRY(cudaEventCreate(&e0));
     NF_CUDA_TRY(cudaEventCreate(&e1));
@@ -1343,6 +1355,8 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     // two waves of two CTAs per SM (n below ~35,000); measured on GB300 they win there (n =
     // 20,000: 0.177 vs 0.198 ms) and lose badly on large sets (n = 1e5: 7.2 vs 1.8 ms)
     const bool try512 = sym_pairs_1024(op) < 4 * (int64_t)num_sms();
+    NF_TRY(ensure_workspace(op, 1, (int)(op->n_pad / (try512 ? 512 : MS_BLK))));
+    NF_CUDA_TRY(cudaMemsetAsync(op->g, 0, sizeof(float) * op->n_pad, s));
     const std::pair<int, int> shapes[3] = {{4, 1024}, {8, 1024}, {8, 512}};
     for (const auto &sh : shapes) {
         if (sh.second == 512 && !try512) continue;
