@@ -171,22 +171,26 @@ NF_API nf_status nf_operator_kernel_ms(nf_operator *op, float *ms);
  * column splits (host ints; -1 for other paths). */
 NF_API nf_status nf_operator_launch_shape(nf_operator *op, int *rows_per_warp, int *tile_cols, int *splits);
 
-/* Schedule of a matrix-free operator's single-trajectory sums (Eq. (2.9) with B = 1):
+/* Schedule of a matrix-free operator's sums for up to three trajectories (Eq. (2.9); from
+ * four trajectories on the multi-trajectory kernels share each pair's exponentials):
  *   NF_MF_AUTO       the symmetric block-pair kernel (each unordered pair once, w radial)
- *                    when it has block pairs for 2/3 of the SMs, else the packed kernel
- *                    (default; the switch is at about 13,300 nodes on 152 SMs);
+ *                    when it has block pairs for 2/3 of the SMs and its partial sums
+ *                    (4 n^2 / 1024 bytes per trajectory) fit an eighth of the device
+ *                    memory, else the packed kernel (default; the switch is at about
+ *                    13,300 nodes on 152 SMs, and again at about 3 million);
  *   NF_MF_SYMMETRIC  always the symmetric kernel;
  *   NF_MF_PACKED     always the packed row-block x column-split kernel (ordered pairs);
  *   NF_MF_SYMMETRIC_512, NF_MF_SYMMETRIC_1024   the symmetric kernel with that node-block
  *                    size (by default the operator's autotuner picks 1,024, or 512 where
  *                    that measured faster); a change of block size switches culling off.
- * Results agree to FP32 rounding (summation order differs).  Multi-trajectory sums and
- * nf_adjoint are unaffected.  Errors: NF_ERR_ARG (not matrix-free, unknown value). */
+ * Results agree to FP32 rounding (summation order differs).  Sums of four or more
+ * trajectories and nf_adjoint are unaffected.  Errors: NF_ERR_ARG (not matrix-free, unknown
+ * value). */
 enum { NF_MF_AUTO = 0, NF_MF_SYMMETRIC = 1, NF_MF_PACKED = 2, NF_MF_SYMMETRIC_512 = 3, NF_MF_SYMMETRIC_1024 = 4 };
 NF_API nf_status nf_operator_mf_schedule(nf_operator *op, int schedule);
 
-/* Block-pair culling for the symmetric single-trajectory schedule (opt-in; off at creation).
- * A pair of 1024-node blocks whose bounding boxes lie so far apart that the wider Gaussian
+/* Block-pair culling for the symmetric schedule (opt-in; off at creation).
+ * A pair of node blocks whose bounding boxes lie so far apart that the wider Gaussian
  * has an exponent above 160 (base 2) for every node pair in it contributes exactly zero in
  * FP32 (the exponential flushes to 0 below 2^-126), so it is skipped: the kernel runs over
  * the remaining block pairs only, and each node adds its block's live partial sums in the
@@ -196,7 +200,7 @@ NF_API nf_status nf_operator_mf_schedule(nf_operator *op, int schedule);
  *   enable       1 to build the live-pair lists (host work over all block pairs; copies
  *                the coordinates to the host and synchronises `stream`), 0 to switch off
  *   live_pairs, block_pairs   host int64 outputs (may be NULL): live and total block pairs
- * Multi-trajectory sums, the packed schedule and nf_adjoint do not cull.
+ * Sums of four or more trajectories, the packed schedule and nf_adjoint do not cull.
  * Errors: NF_ERR_ARG (not matrix-free), NF_ERR_NOMEM/NF_ERR_CUDA. */
 NF_API nf_status nf_operator_mf_cull(nf_operator *op, int enable, int64_t *live_pairs, int64_t *block_pairs,
                                      void *stream);
