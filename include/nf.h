@@ -200,7 +200,9 @@ NF_API nf_status nf_operator_mf_schedule(nf_operator *op, int schedule);
  *   enable       1 to build the live-pair lists (host work over all block pairs; copies
  *                the coordinates to the host and synchronises `stream`), 0 to switch off
  *   live_pairs, block_pairs   host int64 outputs (may be NULL): live and total block pairs
- * Sums of four or more trajectories, the packed schedule and nf_adjoint do not cull.
+ * nf_adjoint culls its adjoint pass as well (lists built from both Gaussians, so that the
+ * A2 and s2 gradients stay exact); gradients are bit-identical to the unculled ones.  Sums
+ * of four or more trajectories and the packed schedule do not cull.
  * Errors: NF_ERR_ARG (not matrix-free), NF_ERR_NOMEM/NF_ERR_CUDA. */
 NF_API nf_status nf_operator_mf_cull(nf_operator *op, int enable, int64_t *live_pairs, int64_t *block_pairs,
                                      void *stream);

@@ -128,6 +128,10 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     NF_TRY(ensure_workspace(op, B, mf_splits(op, B)));
     const int slots = adj_slots(op);  // one W nu slot per 1,024-node block
     const int64_t ncta = sym_pair_count(op);
+    // block-pair culling (nf_operator_mf_cull): the adjoint kernel runs over its own live
+    // pairs, and each node's live W nu slots are added into slot 0 before the epilogue
+    const bool cull = op->mf_cull && op->adj_pairs;
+    const int64_t ncta_run = cull ? op->adj_live : ncta;
     const int Cseg = std::min(C, std::max(nsteps, 1));
     float *stages = nullptr, *lam = nullptr, *acc = nullptr, *ubuf = nullptr, *wpart = nullptr, *gpart = nullptr;
     float2 *vg = nullptr;
@@ -186,10 +190,13 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
         for (int j = cnt - 1; j >= 0; --j) {
             for (int stg = 3; stg >= 0; --stg) {
                 float r2phys = 1.f;
-                for (int b = 0; b < B; ++b) NF_TRY(launch_adj_sym(op, vg, B, b, wpart, gpart, &r2phys, s));
+                for (int b = 0; b < B; ++b) {
+                    NF_TRY(launch_adj_sym(op, vg, B, b, wpart, gpart, &r2phys, s));
+                    if (cull) NF_TRY(launch_adj_cull_reduce(op, wpart, B, b, s));
+                }
                 AdjEpiArgs ea{};
                 ea.wpart = wpart;
-                ea.slots = slots;
+                ea.slots = cull ? 1 : slots;
                 ea.n = n;
                 ea.n_pad = n_pad;
                 ea.B = B;
@@ -206,7 +213,7 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
                 ea.dt = (float)dt;
                 AdjScale sc{{1.0, 2.0 * kp.A1 / ((double)kp.s1 * kp.s1 * kp.s1) * r2phys, -1.0,
                              -2.0 * kp.A2 / ((double)kp.s2 * kp.s2 * kp.s2) * r2phys}};
-                adj_reduce_kernel<<<(unsigned)(4 * B), 256, 0, s>>>(gpart, ncta, sc, gk);
+                adj_reduce_kernel<<<(unsigned)(4 * B), 256, 0, s>>>(gpart, ncta_run, sc, gk);
                 adj_epilogue_kernel<<<eg, T, 0, s>>>(ea);
                 NF_CUDA_TRY(cudaGetLastError());
             }

@@ -351,6 +351,10 @@ nf_status nf_operator_destroy(nf_operator *op) {
     cudaFree(op->cull_ptr);
     cudaFree(op->cull_slots);
     cudaFree(op->node_blk);
+    cudaFree(op->adj_pairs);
+    cudaFree(op->adj_ptr);
+    cudaFree(op->adj_slots);
+    cudaFree(op->adj_node_blk);
     cudaFree(op->q);
     cudaFree(op->W32);
     cudaFree(op->Whi);

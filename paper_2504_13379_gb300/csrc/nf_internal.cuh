@@ -182,6 +182,9 @@ struct nf_operator {
     int *cull_ptr = nullptr;     // nb + 1: each node block's live slots in cull_slots
     int *cull_slots = nullptr;   // ascending per block
     int *node_blk = nullptr;     // n_pad: Morton block of each node
+    int *adj_pairs = nullptr;    // the adjoint kernel's live pairs of 1,024-node blocks (both Gaussians)
+    int64_t adj_live = 0;
+    int *adj_ptr = nullptr, *adj_slots = nullptr, *adj_node_blk = nullptr;
     int *rowperm = nullptr;  // n_pad: row order of the packed pair kernel (Morton order of the nodes)
     float *q = nullptr;      // n_pad, zero padded
     // dense planes (row-major, leading dimension ld = n_pad)
@@ -239,6 +242,7 @@ int64_t sym_pair_count(const nf_operator *op);  // block pairs of the symmetric 
 int sym_slots(const nf_operator *op);   // node blocks of the symmetric schedule (W nu slots)
 int adj_slots(const nf_operator *op);   // node blocks of the adjoint kernel (1,024 nodes)
 nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live, int64_t *total, cudaStream_t s);
+nf_status launch_adj_cull_reduce(nf_operator *op, float *wpart, int B, int b, cudaStream_t s);
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
                          float *r2_phys, cudaStream_t s);
 nf_status mf_autotune(nf_operator *op, cudaStream_t s);

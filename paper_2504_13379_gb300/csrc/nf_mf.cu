@@ -789,7 +789,7 @@ template <int R, int M>
 __global__ void __launch_bounds__(MS_THREADS, 2)
 adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all, const int *__restrict__ rowperm,
                int64_t n_pad, int B, int b, float k2, float A1, float A2, float per, float *__restrict__ wpart,
-               float *__restrict__ gpart) {
+               float *__restrict__ gpart, const int *__restrict__ pairs) {
     static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
     static_assert(R == 2 || R == 4, "rows per warp");
     constexpr int NPASS = MS_BLK / R;
@@ -806,7 +806,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     __shared__ float gred[MS_WARPS][4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int I, J;
-    sym_pair(blockIdx.x, I, J);
+    sym_pair(pairs ? (int64_t)__ldg(pairs + blockIdx.x) : (int64_t)blockIdx.x, I, J);  // pairs: live list
     const bool diag = I == J;
     const float2 *vg = vg_all + (int64_t)b * n_pad;
     const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
@@ -1283,9 +1283,12 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
     const int m = mf_width_ratio(k);
     const double L2E = 1.4426950408889634;
     *r2_phys = (float)((m > 0 ? (double)k.s2 * k.s2 : (double)k.s1 * k.s1) / L2E);
-    dim3 grid((unsigned)sym_pairs_1024(op), 1, 1);
+    const bool cull = op->mf_cull && op->adj_pairs;
+    dim3 grid((unsigned)(cull ? op->adj_live : sym_pairs_1024(op)), 1, 1);
     const size_t smem = AS_SMEM_FLOATS * sizeof(float);
-#define NF_ADJ_ARGS op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, scaled_period(k), wpart, gpart
+#define NF_ADJ_ARGS                                                                                       \
+    op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, scaled_period(k), wpart, gpart, \
+        (cull ? op->adj_pairs : nullptr)
     switch (m) {
         case 2: adj_sym_kernel<4, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
         case 3: adj_sym_kernel<4, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
@@ -1391,10 +1394,11 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
 // the symmetric kernel runs over the live pairs only, and each node then adds the slots of
 // its block's live pairs, in ascending slot order, into slot 0 -- the same nonzero terms in
 // the same order as the full sum, so results are bit-identical to it.
-__global__ void cull_reduce_kernel(float *__restrict__ partial, int64_t n_pad, int B, const int *__restrict__ node_blk,
-                                   const int *__restrict__ ptr, const int *__restrict__ slots) {
+__global__ void cull_reduce_kernel(float *__restrict__ partial, int64_t n_pad, int B, int b0,
+                                   const int *__restrict__ node_blk, const int *__restrict__ ptr,
+                                   const int *__restrict__ slots) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;  // trajectory
+    const int b = b0 + blockIdx.y;  // trajectory
     if (i >= n_pad) return;
     const int K = node_blk[i];
     float acc = 0.f;
@@ -1402,34 +1406,33 @@ __global__ void cull_reduce_kernel(float *__restrict__ partial, int64_t n_pad, i
     partial[(int64_t)b * n_pad + i] = acc;
 }
 
-nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live_out, int64_t *total_out, cudaStream_t s) {
-    const int64_t n = op->n, n_pad = op->n_pad, blk = op->sym_blk, nb = n_pad / blk, npairs = nb * (nb + 1) / 2;
-    if (total_out) *total_out = npairs;
-    if (live_out) *live_out = npairs;
-    if (!enable) {
-        if (op->mf_cull) destroy_graphs(op);
-        op->mf_cull = 0;
-        return NF_OK;
-    }
-    // boxes of the Morton blocks over their real nodes, in the kernel's coordinate units
-    std::vector<float> xyz((size_t)3 * n_pad);
-    std::vector<int> perm((size_t)n_pad);
-    NF_CUDA_TRY(cudaMemcpyAsync(xyz.data(), op->xyz, sizeof(float) * 3 * n_pad, cudaMemcpyDeviceToHost, s));
-    NF_CUDA_TRY(cudaMemcpyAsync(perm.data(), op->rowperm, sizeof(int) * n_pad, cudaMemcpyDeviceToHost, s));
-    NF_CUDA_TRY(cudaStreamSynchronize(s));
-    const nf_kernel &k = op->kp;
-    const int form = sym_form(k);
-    const double k2 = ((double)k.s1 * k.s1) / ((double)k.s2 * k.s2);
-    const double sk = form >= 2 ? std::sqrt(k2) : 1.0;
-    const double wide = form > 0 ? 1.0 : std::min(1.0, k2);
-    const double per = (double)scaled_period(k);
+// The adjoint pass over culled pairs: each node adds its 1,024-node block's live W nu slots
+// of trajectory b into slot 0 (the epilogue then reads one slot).
+nf_status launch_adj_cull_reduce(nf_operator *op, float *wpart, int B, int b, cudaStream_t s) {
+    cull_reduce_kernel<<<dim3((unsigned)ceil_div(op->n_pad, 256), 1), 256, 0, s>>>(
+        wpart, op->n_pad, B, b, op->adj_node_blk, op->adj_ptr, op->adj_slots);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+// Live block pairs of the node blocks of size blk (Morton order), in coordinates scaled by sk
+// from the stored s1 units, for a kernel whose wider exponential has exponent wide * r^2
+// there; per: the period in s1 units (0: none).  Also each block's live slots (CSR) and each
+// node's block.
+struct CullLists {
+    std::vector<int> pairs, ptr, slots, node_blk;
+};
+
+static void build_cull_lists(const std::vector<float> &xyz, const std::vector<int> &perm, int64_t n, int64_t n_pad,
+                             int64_t blk, double sk, double wide, double per, CullLists &L) {
+    const int64_t nb = n_pad / blk, npairs = nb * (nb + 1) / 2;
     std::vector<double> lo((size_t)3 * nb, 1e300), hi((size_t)3 * nb, -1e300);
     std::vector<char> empty((size_t)nb, 1);
-    std::vector<int> node_blk((size_t)n_pad);
+    L.node_blk.assign((size_t)n_pad, 0);
     for (int64_t p = 0; p < n_pad; ++p) {
         const int node = perm[(size_t)p];
         const int64_t K = p / blk;
-        node_blk[(size_t)node] = (int)K;
+        L.node_blk[(size_t)node] = (int)K;
         if (node >= n) continue;
         empty[(size_t)K] = 0;
         for (int d = 0; d < 3; ++d) {
@@ -1455,41 +1458,70 @@ nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live_out, int64_t *t
         }
         return wide * d2 < 160.0 * (1.0 + 1e-4);
     };
-    std::vector<int> pairs;
-    std::vector<int> ptr((size_t)nb + 1, 0), slots;
     std::vector<char> lv((size_t)npairs);
+    L.pairs.clear();
     for (int64_t J = 0; J < nb; ++J)
         for (int64_t I = 0; I <= J; ++I) {
             const int64_t t = J * (J + 1) / 2 + I;
             lv[(size_t)t] = live(I, J) ? 1 : 0;
-            if (lv[(size_t)t]) pairs.push_back((int)t);
+            if (lv[(size_t)t]) L.pairs.push_back((int)t);
         }
+    L.ptr.assign((size_t)nb + 1, 0);
+    L.slots.clear();
     for (int64_t K = 0; K < nb; ++K) {
         for (int64_t S = 0; S < nb; ++S) {
             const int64_t a = std::min(K, S), b = std::max(K, S);
-            if (lv[(size_t)(b * (b + 1) / 2 + a)]) slots.push_back((int)S);
+            if (lv[(size_t)(b * (b + 1) / 2 + a)]) L.slots.push_back((int)S);
         }
-        ptr[(size_t)K + 1] = (int)slots.size();
+        L.ptr[(size_t)K + 1] = (int)L.slots.size();
     }
-    cudaFree(op->cull_pairs);
-    cudaFree(op->cull_ptr);
-    cudaFree(op->cull_slots);
-    cudaFree(op->node_blk);
-    op->cull_pairs = op->cull_ptr = op->cull_slots = op->node_blk = nullptr;
+}
+
+static nf_status upload_int(const std::vector<int> &v, int **dst, cudaStream_t s) {
+    cudaFree(*dst);
+    *dst = nullptr;
+    NF_CUDA_TRY(cudaMalloc(dst, sizeof(int) * std::max<size_t>(1, v.size())));
+    NF_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+    return NF_OK;
+}
+
+nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live_out, int64_t *total_out, cudaStream_t s) {
+    const int64_t n = op->n, n_pad = op->n_pad, blk = op->sym_blk, nb = n_pad / blk, npairs = nb * (nb + 1) / 2;
+    if (total_out) *total_out = npairs;
+    if (live_out) *live_out = npairs;
+    if (op->mf_cull) destroy_graphs(op);
     op->mf_cull = 0;
-    NF_CUDA_TRY(cudaMalloc(&op->cull_pairs, sizeof(int) * pairs.size()));
-    NF_CUDA_TRY(cudaMalloc(&op->cull_ptr, sizeof(int) * ptr.size()));
-    NF_CUDA_TRY(cudaMalloc(&op->cull_slots, sizeof(int) * slots.size()));
-    NF_CUDA_TRY(cudaMalloc(&op->node_blk, sizeof(int) * node_blk.size()));
-    NF_CUDA_TRY(cudaMemcpyAsync(op->cull_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, s));
-    NF_CUDA_TRY(cudaMemcpyAsync(op->cull_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, s));
-    NF_CUDA_TRY(cudaMemcpyAsync(op->cull_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, s));
-    NF_CUDA_TRY(cudaMemcpyAsync(op->node_blk, node_blk.data(), sizeof(int) * node_blk.size(), cudaMemcpyHostToDevice,
-                                s));
+    if (!enable) return NF_OK;
+    // boxes of the Morton blocks over their real nodes, in the kernels' coordinate units
+    std::vector<float> xyz((size_t)3 * n_pad);
+    std::vector<int> perm((size_t)n_pad);
+    NF_CUDA_TRY(cudaMemcpyAsync(xyz.data(), op->xyz, sizeof(float) * 3 * n_pad, cudaMemcpyDeviceToHost, s));
+    NF_CUDA_TRY(cudaMemcpyAsync(perm.data(), op->rowperm, sizeof(int) * n_pad, cudaMemcpyDeviceToHost, s));
     NF_CUDA_TRY(cudaStreamSynchronize(s));
-    op->cull_live = (int64_t)pairs.size();
+    const nf_kernel &k = op->kp;
+    const int form = sym_form(k);
+    const double k2 = ((double)k.s1 * k.s1) / ((double)k.s2 * k.s2);
+    const double per = (double)scaled_period(k);
+    // forward: the symmetric kernel's units (s2 when m >= 2) and its wider exponential
+    // (the second Gaussian is not evaluated when A2 = 0)
+    CullLists fw, ad;
+    build_cull_lists(xyz, perm, n, n_pad, blk, form >= 2 ? std::sqrt(k2) : 1.0,
+                     form > 0 ? 1.0 : std::min(1.0, k2), per, fw);
+    // adjoint: 1,024-node blocks, and both Gaussians always (the parameter sums of A2 and s2
+    // need e2 even when A2 = 0)
+    build_cull_lists(xyz, perm, n, n_pad, MS_BLK, 1.0, std::min(1.0, k2), per, ad);
+    NF_TRY(upload_int(fw.pairs, &op->cull_pairs, s));
+    NF_TRY(upload_int(fw.ptr, &op->cull_ptr, s));
+    NF_TRY(upload_int(fw.slots, &op->cull_slots, s));
+    NF_TRY(upload_int(fw.node_blk, &op->node_blk, s));
+    NF_TRY(upload_int(ad.pairs, &op->adj_pairs, s));
+    NF_TRY(upload_int(ad.ptr, &op->adj_ptr, s));
+    NF_TRY(upload_int(ad.slots, &op->adj_slots, s));
+    NF_TRY(upload_int(ad.node_blk, &op->adj_node_blk, s));
+    NF_CUDA_TRY(cudaStreamSynchronize(s));
+    op->cull_live = (int64_t)fw.pairs.size();
+    op->adj_live = (int64_t)ad.pairs.size();
     op->mf_cull = 1;
-    destroy_graphs(op);
     if (live_out) *live_out = op->cull_live;
     return NF_OK;
 }
@@ -1500,7 +1532,7 @@ nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out
         *splits_out = sym_slots(op);
         if (op->mf_cull) {  // only live pairs ran: add each node's live slots into slot 0
             cull_reduce_kernel<<<dim3((unsigned)ceil_div(op->n_pad, 256), (unsigned)B), 256, 0, s>>>(
-                op->partial, op->n_pad, B, op->node_blk, op->cull_ptr, op->cull_slots);
+                op->partial, op->n_pad, B, 0, op->node_blk, op->cull_ptr, op->cull_slots);
             NF_CUDA_TRY(cudaGetLastError());
             *splits_out = 1;
         }

@@ -136,3 +136,28 @@ def test_cull_separated_clusters(nf):
     a = nf.nf_nonlocal_apply(full, dev(u), 20.0, 0.2).cpu().numpy()
     b = nf.nf_nonlocal_apply(cull, dev(u), 20.0, 0.2).cpu().numpy()
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("kern", [(1.0, 0.02, 0.5, 0.04), (3.0, 0.02, 0.0, 0.05)])
+def test_cull_adjoint_bit_identical(nf, kern):
+    """The adjoint pass culls with its own live pairs (both Gaussians count: the A2 and s2
+    parameter sums need e2 even when A2 = 0): gradients bit-identical to the unculled ones."""
+    n, B, nsteps, C, dt = 20000, 1, 4, 2, 0.02
+    X, q, ns = _torus(n, 11)
+    u0 = (0.8 * nodesets.spiral_bumps_u0(ns))[None, :].astype(np.float32)
+    target = (0.9 * u0).astype(np.float32)
+    res = []
+    for cull in (False, True):
+        op = nf.Operator(dev(X), dev(q), kern, 0).mf_schedule(nf.MF_SYMMETRIC_1024)
+        if cull:
+            live, total = op.mf_cull(True)
+            assert live < total
+        u = dev(u0)
+        ck = torch.zeros((nsteps // C + 1, B, n), dtype=torch.float32, device="cuda")
+        nf.nf_rk4_advance(op, u, 0.0, dt, nsteps, 20.0, 0.2, ckpt=ck, C_every=C)
+        gu, gk = nf.nf_adjoint(op, ck, C, 0.0, dt, nsteps, 20.0, 0.2, 2.0 * (u - dev(target)))
+        op.check()
+        res.append((u.cpu().numpy(), gu.cpu().numpy(), gk.cpu().numpy()))
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, b)
+    assert np.abs(res[1][2]).max() > 0
