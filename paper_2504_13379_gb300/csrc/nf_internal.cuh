@@ -175,6 +175,7 @@ struct nf_operator {
     int mf_sym_r = 8;        // rows per warp of the symmetric single-trajectory kernel (autotuned)
     int mf_sched = 0;        // NF_MF_AUTO / NF_MF_SYMMETRIC / NF_MF_PACKED
     int sym_blk = 1024;      // node block of the symmetric kernel (1024, or 512 when autotuned faster)
+    int planar = 0;          // every node has the same z: the symmetric kernel drops the z terms
     // block-pair culling of the symmetric kernel (opt-in, nf_operator_mf_cull)
     int mf_cull = 0;
     int *cull_pairs = nullptr;   // live block-pair indices (ascending)

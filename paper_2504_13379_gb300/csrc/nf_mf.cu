@@ -491,7 +491,9 @@ __device__ __forceinline__ float warp_reduce_rows(float (&v)[R], int lane, int &
     return v[0];
 }
 
-template <int R, int M, int BLK>
+// D2: every node has the same z (flat domains), so the z terms of the distance vanish
+// identically and are left out (bit-identical sums, one FMA fewer per pair).
+template <int R, int M, int BLK, bool D2 = false>
 __global__ void __launch_bounds__(MS_THREADS, 2)
 mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, const int *__restrict__ rowperm,
               int64_t n_pad, int B, int b_base, float k2, float A1, float A2, float per,
@@ -655,7 +657,8 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
             constexpr bool P = decltype(tag)::value;
 #pragma unroll 1
             for (int q = lane; q < BLK / 4; q += 32) {
-                const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
+                const float4 x4 = xs4[q], y4 = ys4[q], g4 = gs4[q];
+                const float4 z4 = D2 ? make_float4(0.f, 0.f, 0.f, 0.f) : zs4[q];
                 u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
                 u64 yt[2] = {f2_sub(lo2(y4), cyp), f2_sub(hi2(y4), cyp)};
                 const u64 zt[2] = {f2_sub(lo2(z4), czp), f2_sub(hi2(z4), czp)};
@@ -669,12 +672,16 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                 const u64 gj[2] = {lo2(g4), hi2(g4)};
                 u64 nj[2], cacc[2] = {0ull, 0ull};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) nj[h] = f2_fma(zt[h], zt[h], f2_fma(yt[h], yt[h], f2_mul(xt[h], xt[h])));
+                for (int h = 0; h < 2; ++h) {
+                    nj[h] = f2_fma(yt[h], yt[h], f2_mul(xt[h], xt[h]));
+                    if constexpr (!D2) nj[h] = f2_fma(zt[h], zt[h], nj[h]);
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const u64 sij = f2_fma(xi[r], xt[h], f2_fma(yi[r], yt[h], f2_fma(zi[r], zt[h], nj[h])));
+                        const u64 zz = D2 ? nj[h] : f2_fma(zi[r], zt[h], nj[h]);
+                        const u64 sij = f2_fma(xi[r], xt[h], f2_fma(yi[r], yt[h], zz));
                         u64 e1, e2;
                         exps(sij, e1, e2);
                         a1[r] = f2_fma(e1, gj[h], a1[r]);
@@ -696,7 +703,8 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
             constexpr bool CEN = decltype(tag_c)::value, PW = decltype(tag_w)::value;
 #pragma unroll 1
             for (int q = lane; q < BLK / 4; q += 32) {
-                const float4 x4 = xs4[q], y4 = ys4[q], z4 = zs4[q], g4 = gs4[q];
+                const float4 x4 = xs4[q], y4 = ys4[q], g4 = gs4[q];
+                const float4 z4 = D2 ? make_float4(0.f, 0.f, 0.f, 0.f) : zs4[q];
                 u64 xj[2] = {lo2(x4), hi2(x4)}, yj[2] = {lo2(y4), hi2(y4)};
                 const u64 zj[2] = {lo2(z4), hi2(z4)};
                 if constexpr (CEN) {
@@ -718,7 +726,8 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                             dx = f2_wrap(dx, ipp, npp, mgp);
                             dy = f2_wrap(dy, ipp, npp, mgp);
                         }
-                        const u64 r2s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                        const u64 r2xy = f2_fma(dy, dy, f2_mul(dx, dx));
+                        const u64 r2s = D2 ? r2xy : f2_fma(dz, dz, r2xy);
                         u64 e1, e2;
                         exps(r2s, e1, e2);
                         a1[r] = f2_fma(e1, gj[h], a1[r]);
@@ -1053,9 +1062,9 @@ static cudaError_t set_mf_attr() {
 }
 
 // Opt every pair-kernel instance into its shared-memory size (outside any capture).
-template <int R, int M, int BLK = 1024>
+template <int R, int M, int BLK = 1024, bool D2 = false>
 static cudaError_t set_sym_attr() {
-    return cudaFuncSetAttribute(mf_sym_kernel<R, M, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(mf_sym_kernel<R, M, BLK, D2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ms_smem_bytes(BLK));
 }
 
@@ -1085,6 +1094,11 @@ nf_status mf_init_attrs() {
     NF_CUDA_TRY((set_sym_attr<8, 2, 512>()));
     NF_CUDA_TRY((set_sym_attr<8, 3, 512>()));
     NF_CUDA_TRY((set_sym_attr<8, 4, 512>()));
+    NF_CUDA_TRY((set_sym_attr<8, 0, 1024, true>()));
+    NF_CUDA_TRY((set_sym_attr<8, 1, 1024, true>()));
+    NF_CUDA_TRY((set_sym_attr<8, 2, 1024, true>()));
+    NF_CUDA_TRY((set_sym_attr<8, 3, 1024, true>()));
+    NF_CUDA_TRY((set_sym_attr<8, 4, 1024, true>()));
     NF_CUDA_TRY((set_mf_attr<1, 2>()));
     NF_CUDA_TRY((set_mf_attr<2, 2>()));
     NF_CUDA_TRY((set_mf_attr<4, 2>()));
@@ -1207,7 +1221,7 @@ static int64_t sym_pairs_1024(const nf_operator *op) {
     return nb * (nb + 1) / 2;
 }
 
-template <int R, int BLK>
+template <int R, int BLK, bool D2 = false>
 static void launch_sym_rb(nf_operator *op, int B, int b_base, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
@@ -1218,11 +1232,11 @@ static void launch_sym_rb(nf_operator *op, int B, int b_base, cudaStream_t s) {
     op->xyz, op->g, op->rowperm, op->n_pad, B, b_base, k2, k.A1, k.A2, scaled_period(k), op->partial, \
         (op->mf_cull ? op->cull_pairs : nullptr)
     switch (sym_form(k)) {
-        case 1: mf_sym_kernel<R, 1, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
-        case 2: mf_sym_kernel<R, 2, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
-        case 3: mf_sym_kernel<R, 3, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
-        case 4: mf_sym_kernel<R, 4, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
-        default: mf_sym_kernel<R, 0, BLK><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        case 1: mf_sym_kernel<R, 1, BLK, D2><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        case 2: mf_sym_kernel<R, 2, BLK, D2><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        case 3: mf_sym_kernel<R, 3, BLK, D2><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        case 4: mf_sym_kernel<R, 4, BLK, D2><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
+        default: mf_sym_kernel<R, 0, BLK, D2><<<grid, MS_THREADS, smem, s>>>(NF_SYM_ARGS); break;
     }
 #undef NF_SYM_ARGS
 }
@@ -1232,6 +1246,8 @@ static nf_status launch_sym(nf_operator *op, int B, int b_base, cudaStream_t s) 
         launch_sym_rb<8, 512>(op, B, b_base, s);
     else if (op->mf_sym_r == 4)
         launch_sym_rb<4, 1024>(op, B, b_base, s);
+    else if (op->planar)
+        launch_sym_rb<8, 1024, true>(op, B, b_base, s);
     else
         launch_sym_rb<8, 1024>(op, B, b_base, s);
     NF_CUDA_TRY(cudaGetLastError());
@@ -1709,8 +1725,11 @@ nf_status mf_build_row_order(nf_operator *op, cudaStream_t s) {
         for (int64_t jj = kk >> 1; jj > 0; jj >>= 1)
             row_bitonic_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(keys, m, jj, kk);
     row_perm_kernel<<<(unsigned)ceil_div(n_pad, 256), 256, 0, s>>>(keys, n, n_pad, op->rowperm);
+    float hbox[6] = {0, 0, 0, 0, 0, 0};
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hbox, box, sizeof(hbox), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    op->planar = (e == cudaSuccess && hbox[2] == hbox[5]) ? 1 : 0;  // one z for every node
     if (e != cudaSuccess) st = cuda_fail(e, "row order", __FILE__, __LINE__);
     cudaFree(keys);
     return st;
