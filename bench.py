@@ -156,7 +156,7 @@ LANE_OPS_PER_PAIR = 9.875 / 2.0
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels:
 # mf_sym_kernel<8, 4> on the n = 100,000 torus; tc_grouped_kernel on the batched workload at
 # half node counts, scaled to full size by the W bytes a launch streams (4x)
-MF_TRAFFIC_BYTES = 2.181e6 + 0.239e6
+MF_TRAFFIC_BYTES = 2.181e6 + 0.245e6
 TC_TRAFFIC_BYTES = (2.956e9 + 0.104e9) * 4.0
 
 
