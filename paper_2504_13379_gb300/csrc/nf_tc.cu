@@ -612,7 +612,12 @@ static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
     std::vector<double> cost(ntiles);
     for (int k = 0; k < P.ngroups; ++k) {
         const TcGroup &G = P.grp[k];
-        const double c = (double)ceil_div(G.n, 32) * std::max(3.0 * G.n_mma, 760.0);
+        // time per K step: the MMAs (∝ N) or the W stream, whichever is longer.  Run alone on
+        // GB300, a 64-wide step takes 1.36 µs for N = 256 tiles and 0.84 µs for N = 64 tiles
+        // (HBM-bound); in the mixed launch the N = 256 tiles weigh more still (coefficient of
+        // N swept over 4.5 / 5.3 / 6.5 / 8: 2.101 / 2.112 / 2.087 / 2.084 ms per launch on
+        // the 448-trajectory workload, 2.154 ms with the former 3 / 760 model)
+        const double c = (double)ceil_div(G.n, 32) * std::max(8.0 * G.n_mma, 840.0);
         for (int t = P.tile_start[k]; t < P.tile_start[k + 1]; ++t) cost[t] = c;
     }
     std::vector<int> order(ntiles);
