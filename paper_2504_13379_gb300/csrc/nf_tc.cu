@@ -630,6 +630,10 @@ static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
         lists[c].push_back(t);
         load[c] += cost[t];
     }
+    // LPT leaves every cluster's list in decreasing cost order, so all clusters would run
+    // their tensor-bound (wide) tiles at the same time and their HBM-bound (narrow) tiles
+    // later; every other cluster runs its list backwards, so the two kinds overlap
+    for (int c = 1; c < nclust; c += 2) std::reverse(lists[c].begin(), lists[c].end());
     std::vector<int> host;
     host.reserve(nclust + 1 + ntiles);
     int off = 0;
