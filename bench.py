@@ -157,7 +157,7 @@ LANE_OPS_PER_PAIR = 9.875 / 2.0
 # mf_sym_kernel<8, 4> on the n = 100,000 torus; tc_grouped_kernel on the batched workload at
 # half node counts, scaled to full size by the W bytes a launch streams (4x)
 MF_TRAFFIC_BYTES = 2.181e6 + 0.245e6
-TC_TRAFFIC_BYTES = (2.956e9 + 0.104e9) * 4.0
+TC_TRAFFIC_BYTES = (2.949e9 + 0.028e9) * 4.0
 
 
 def run_reference(args, rank, world):
