@@ -19,7 +19,7 @@ captured around it inside the step graph.  With --gpus N under torchrun every ra
 runs an independent replica (the single-trajectory path does not shard without a
 per-stage all-gather), value = all ranks' pairs / max time ("weak" scaling).
 
---impl reference times the FP64 CPU oracle (the reference arm of this build) on a
+--impl reference times the FP64 CPU oracle (the reference arm of the measurement) on a
 bounded sample of the same workload: a step is one nonlocal stage over a row sample.
 """
 from __future__ import annotations

@@ -47,7 +47,7 @@ typedef enum {
     NF_ERR_TIMEOUT = 4,      /* a bounded device wait gave up; the kernel returned early */
     NF_ERR_NOMEM = 5,        /* device allocation failed */
     NF_ERR_CUDA = 6,         /* CUDA runtime / launch error */
-    NF_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+    NF_ERR_UNSUPPORTED = 7   /* valid request the library does not implement */
 } nf_status;
 
 /* Message describing the last failure on the calling thread ("" if none). */
