@@ -55,3 +55,43 @@ def test_cyclide_area_and_polynomial_convergence():
 def test_cyclide_reference_area_converged():
     """The periodic trapezoid reference is converged (600 vs 900 points per direction)."""
     assert abs(nodesets.cyclide_area(m=600) - nodesets.cyclide_area(m=900)) < 1e-9
+
+
+def _ellipsoid_grid(a, b, c, m=400):
+    """Nodes and weights on x = (a sin t cos p, b sin t sin p, c cos t): Gauss-Legendre in
+    t, the periodic trapezoid in p, times the surface element |x_t x x_p|."""
+    import numpy as np
+    xg, wg = np.polynomial.legendre.leggauss(m)
+    t = 0.5 * math.pi * (xg + 1.0)
+    p = np.arange(2 * m) * math.pi / m
+    T, P = np.meshgrid(t, p, indexing="ij")
+    X = np.stack([a * np.sin(T) * np.cos(P), b * np.sin(T) * np.sin(P), c * np.cos(T)], -1)
+    Xt = np.stack([a * np.cos(T) * np.cos(P), b * np.cos(T) * np.sin(P), -c * np.sin(T)], -1)
+    Xp = np.stack([-a * np.sin(T) * np.sin(P), b * np.sin(T) * np.cos(P), 0.0 * T], -1)
+    W = (0.5 * math.pi * wg)[:, None] * (math.pi / m) * np.linalg.norm(np.cross(Xt, Xp), axis=-1)
+    return X, W
+
+
+def test_ellipsoid_area_closed_form_and_convergence():
+    """The tri-axial ellipsoid (1, 0.8, 0.6) of the many-trajectory workload: its area is
+    4 pi a b c R_G(a^-2, b^-2, c^-2) with Carlson's symmetric integral R_G (scipy); the
+    parameter-space rule above agrees with it, then integrates e^x cos 2y + z^2.  The
+    oracle's weights approach both at least at the appended degree's order."""
+    import numpy as np
+    sp = pytest.importorskip("scipy.special")
+    a, b, c = 1.0, 0.8, 0.6
+    area = 4.0 * math.pi * a * b * c * float(sp.elliprg(a ** -2, b ** -2, c ** -2))
+    X, W = _ellipsoid_grid(a, b, c)
+    assert abs(W.sum() - area) < 1e-12 * area
+    f = lambda P: np.exp(P[..., 0]) * np.cos(2.0 * P[..., 1]) + P[..., 2] ** 2
+    ref = float((W * f(X)).sum())
+    ea, ef, ns_ = [], [], []
+    for n in (1000, 16000):
+        ns = nodesets.ellipsoid_fibonacci(n, axes=(a, b, c))
+        q = _weights(ns)
+        ea.append(abs(q.sum() - area) / area)
+        ef.append(abs((q * f(ns.nodes)).sum() - ref) / abs(ref))
+        ns_.append(ns.n)
+    assert _order(ea[0], ea[1], *ns_) > 3.0, ea
+    assert _order(ef[0], ef[1], *ns_) > 3.0, ef
+    assert ea[1] < 1e-6 and ef[1] < 1e-6

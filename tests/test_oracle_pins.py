@@ -325,10 +325,11 @@ def test_surface_jacobian_matches_area_ratio_on_sphere():
 
 def test_sphere_area_and_monomial_convergence():
     """Supplementary (sphere): sum of weights -> 4 pi and x^2 y^2 z^4 (closed form
-    2 G(3/2)^2 G(5/2) / G(11/2)) at least at the appended degree in n^{-1/2}."""
+    2 G(3/2)^2 G(5/2) / G(11/2)) at least at the appended degree in n^{-1/2}; the
+    integral of sin x cos 2y cos 3z is 0 (odd in x), and its error falls as fast."""
     exact_m = 2 * math.gamma(1.5) ** 2 * math.gamma(2.5) / math.gamma(5.5)
     ns_list = [1000, 4000, 16000]
-    e_area, e_mono = [], []
+    e_area, e_mono, e_odd = [], [], []
     for n in ns_list:
         ns = nodesets.sphere_fibonacci(n)
         q, _ = _surf(ns, 32, 3)
@@ -336,7 +337,9 @@ def test_sphere_area_and_monomial_convergence():
         e_area.append(abs(q.sum() - 4 * math.pi) / (4 * math.pi))
         e_mono.append(abs((q * (x ** 3 * y ** 2 * z ** 4 + 5)).sum() - 20 * math.pi) / (20 * math.pi))
         e_mono[-1] = max(e_mono[-1], abs((q * x ** 2 * y ** 2 * z ** 4).sum() - exact_m) / exact_m)
+        e_odd.append(abs((q * np.sin(x) * np.cos(2 * y) * np.cos(3 * z)).sum()))
     span = math.log(math.sqrt(ns_list[-1] / ns_list[0]))
+    assert math.log(e_odd[0] / e_odd[-1]) / span >= 3.0, e_odd
     assert math.log(e_area[0] / e_area[-1]) / span >= 3.0, e_area
     assert math.log(e_mono[0] / e_mono[-1]) / span >= 3.0, e_mono
     assert e_area[-1] < 1e-6
@@ -381,6 +384,22 @@ def test_nonlocal_sum_bruteforce(rng):
     np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15)
     rows = np.array([5, 0, 256])
     np.testing.assert_allclose(oracle.nonlocal_sum(X, q, u, kp, beta, theta, rows=rows), want[:, rows], rtol=1e-14)
+
+
+@pytest.mark.parametrize("period", [0.0, 1.0])
+def test_nonlocal_operator_is_symmetric(rng, period):
+    """w depends on the distance alone (§2.2), so W is symmetric: u.(Wv) = v.(Wu).  With
+    f = 1 (u far above theta) the oracle's sum with weights v is Wv; this catches an index
+    or a displacement taken the wrong way round, on the plain and the periodic distance."""
+    n = 301
+    X = rng.uniform(0, 1, size=(n, 3))
+    X[:, 2] = 0.0 if period else X[:, 2]
+    kp = (1.0, 0.15, 0.5, 0.3)
+    one = np.full((1, n), 50.0)
+    u, v = rng.normal(size=n), rng.normal(size=n)
+    Wu = oracle.nonlocal_sum(X, u, one, kp, np.ones(1), np.zeros(1), period=period)[0]
+    Wv = oracle.nonlocal_sum(X, v, one, kp, np.ones(1), np.zeros(1), period=period)[0]
+    assert abs(u @ Wv - v @ Wu) < 1e-12 * np.abs(u) @ np.abs(Wv)
 
 
 # ----------------------------------------------------------------------------------
