@@ -790,8 +790,11 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
 //         P1 = sum nu_i g_j e1, Q1 = sum nu_i g_j r^2 e1, P2 = sum nu_i g_j e2, Q2 = ... r^2 e2
 //     over ordered pairs: off the diagonal an unordered pair carries the weight
 //     nu_i g_j + nu_j g_i, on a diagonal block pair every ordered pair is swept with
-//     nu_i g_j.  Each CTA writes its four sums (r^2 in exponent units: of s2 when M > 0,
-//     else of s1) to gpart; a fixed-order FP64 reduction adds them.
+//     nu_i g_j.  The row's factor nu_i (or g_i) comes out of its sum over j, so per pair
+//     the lane only accumulates sum e g_j, sum arg e g_j and sum arg e nu_j per row
+//     (sum e nu_j is the W nu row sum), with arg = r^2 - n_i; the pass end forms the
+//     four sums from them.  Each CTA writes its four sums (r^2 in exponent units: of s2
+//     when M > 0, else of s1) to gpart; a fixed-order FP64 reduction adds them.
 constexpr size_t AS_SMEM_FLOATS = (size_t)(5 + 14 + 1 + MS_WARPS) * MS_BLK;
 
 template <int R, int M>
@@ -899,47 +902,43 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             e2 = f2_ex2(f2_mul(arg, nk2));
         }
     };
-    u64 P1 = 0ull, Q1 = 0ull, P2 = 0ull, Q2 = 0ull;  // per lane, over all its pairs
+    float P1 = 0.f, Q1 = 0.f, P2 = 0.f, Q2 = 0.f;  // per lane, over all its pairs
     for (int ps = warp; ps < NPASS; ps += MS_WARPS) {
         const int r0 = ps * R;
         const float4 c = pc[ps];
         const bool local = c.w != 0.f;
-        u64 xi[R], yi[R], zi[R], nir[R], h1[R], h2[R], v1[R], u1[R], v2[R], u2[R], a1[R], a2[R];
+        // per row, over the lane's columns j (e1, e2 without the row factors):
+        //   a = sum e nu_j, b = sum e g_j, c = sum arg e g_j, d = sum arg e nu_j
+        u64 xi[R], yi[R], zi[R], h1[R], h2[R], a1[R], a2[R], b1[R], b2[R], c1[R], c2[R], d1[R], d2[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float4 p = rgeo[r0 + r], w = rwn[r0 + r], q = rgw[r0 + r];
+            const float4 p = rgeo[r0 + r], w = rwn[r0 + r];
             xi[r] = f2_pack(p.x, p.x);
             yi[r] = f2_pack(p.y, p.y);
             zi[r] = f2_pack(p.z, p.z);
-            nir[r] = f2_pack(p.w, p.w);
             h1[r] = f2_pack(w.x, w.x);
             h2[r] = f2_pack(w.y, w.y);
-            v1[r] = f2_pack(q.x, q.x);
-            u1[r] = f2_pack(q.y, q.y);
-            v2[r] = f2_pack(q.z, q.z);
-            u2[r] = f2_pack(q.w, q.w);
-            a1[r] = 0ull;
-            a2[r] = 0ull;
+            a1[r] = a2[r] = b1[r] = b2[r] = c1[r] = c2[r] = d1[r] = d2[r] = 0ull;
         }
         const u64 cxp = f2_pack(c.x, c.x), cyp = f2_pack(c.y, c.y), czp = f2_pack(c.z, c.z);
         // per (row, column pair): e1, e2 from the exponent argument arg (r^2 - n_i in the
-        // expanded form, r^2 otherwise), then the W nu and parameter-sum updates
+        // expanded form, r^2 otherwise), then the W nu and row-sum updates
         auto pair = [&](int r, u64 arg, u64 vj, u64 gj, u64 &cacc) {
             u64 e1, e2;
             exps(arg, e1, e2);
             a1[r] = f2_fma(e1, vj, a1[r]);
             a2[r] = f2_fma(e2, vj, a2[r]);
             cacc = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc));
-            const u64 r2 = f2_add(arg, nir[r]);
-            const u64 t1 = f2_mul(e1, f2_fma(v1[r], gj, f2_mul(u1[r], vj)));
-            const u64 t2 = f2_mul(e2, f2_fma(v2[r], gj, f2_mul(u2[r], vj)));
-            P1 = f2_add(P1, t1);
-            Q1 = f2_fma(r2, t1, Q1);
-            P2 = f2_add(P2, t2);
-            Q2 = f2_fma(r2, t2, Q2);
+            b1[r] = f2_fma(e1, gj, b1[r]);
+            b2[r] = f2_fma(e2, gj, b2[r]);
+            const u64 s1e = f2_mul(arg, e1), s2e = f2_mul(arg, e2);
+            c1[r] = f2_fma(s1e, gj, c1[r]);
+            d1[r] = f2_fma(s1e, vj, d1[r]);
+            c2[r] = f2_fma(s2e, gj, c2[r]);
+            d2[r] = f2_fma(s2e, vj, d2[r]);
         };
         if (local) {
-#pragma unroll 2
+#pragma unroll 1
             for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
                 const u64 xt = f2_sub(xs2[jp], cxp), yt = f2_sub(ys2[jp], cyp), zt = f2_sub(zs2[jp], czp);
                 const u64 nj = f2_fma(zt, zt, f2_fma(yt, yt, f2_mul(xt, xt)));
@@ -953,7 +952,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         } else {
             auto sweep = [&](auto tag) {
                 constexpr bool P = decltype(tag)::value;
-#pragma unroll 2
+#pragma unroll 1
             for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
                 const u64 xj = xs2[jp], yj = ys2[jp], zj = zs2[jp], vj = vs2[jp], gj = gs2[jp];
                 u64 cacc = 0ull;
@@ -975,32 +974,31 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             else
                 sweep(PerTag<false>{});
         }
+        auto fold = [](u64 x) {
+            float lo, hi;
+            f2_unpack(x, lo, hi);
+            return lo + hi;
+        };
         float v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            float p0, p1, q0, q1;
-            f2_unpack(a1[r], p0, p1);
-            f2_unpack(a2[r], q0, q1);
-            const float4 w = rwn[r0 + r];
-            v[r] = w.z * (p0 + p1) + w.w * (q0 + q1);
+            const float A1s = fold(a1[r]), A2s = fold(a2[r]), B1s = fold(b1[r]), B2s = fold(b2[r]);
+            const float4 w = rwn[r0 + r], q = rgw[r0 + r];
+            const float ni = rgeo[r0 + r].w;
+            v[r] = w.z * A1s + w.w * A2s;
+            // pair weight e (nu_i g_j + g_i nu_j) with the row factors: q = (f1 nu_i, f1 g_i,
+            // f2 nu_i, f2 g_i), g_i = 0 on diagonal block pairs; r^2 = arg + n_i
+            P1 += q.x * B1s + q.y * A1s;
+            Q1 += q.x * (fold(c1[r]) + ni * B1s) + q.y * (fold(d1[r]) + ni * A1s);
+            P2 += q.z * B2s + q.w * A2s;
+            Q2 += q.z * (fold(c2[r]) + ni * B2s) + q.w * (fold(d2[r]) + ni * A2s);
         }
         int row;
         const float tot = warp_reduce_rows<R>(v, lane, row);
         if ((lane & (32 / R - 1)) == 0) out_rows[rnode[r0 + row]] = tot;
     }
     // the CTA's parameter sums: lanes, then warps, in a fixed order
-    float gs4[4];
-    {
-        float a, bq;
-        f2_unpack(P1, a, bq);
-        gs4[0] = a + bq;
-        f2_unpack(Q1, a, bq);
-        gs4[1] = a + bq;
-        f2_unpack(P2, a, bq);
-        gs4[2] = a + bq;
-        f2_unpack(Q2, a, bq);
-        gs4[3] = a + bq;
-    }
+    float gs4[4] = {P1, Q1, P2, Q2};
 #pragma unroll
     for (int k = 0; k < 4; ++k) gs4[k] = warp_sum(gs4[k]);
     if (lane == 0)
