@@ -135,6 +135,32 @@ def square_halton(n: int = 1500, seed: int = 0) -> NodeSet:
                    meta={"kind": "square_halton", "n_boundary": bnd.shape[0], "seed": seed})
 
 
+def square_repulsion(n: int = 2000, iters: int = 60, seed: int = 0) -> NodeSet:
+    """Unit square with the paper's second node family (§4): interior nodes spread by a
+    deterministic point-repulsion process, equispaced boundary nodes.  Starts from the
+    nodes of ``square_halton``; each iteration moves every interior node by a tenth of the
+    mean spacing s = n^-1/2 along the sum of the unit vectors away from its 8 nearest nodes,
+    weighted (s / d)^3 (the step shrinks where that sum is below 1), boundary nodes fixed,
+    and keeps it half a boundary spacing inside the square.  Delaunay triangulation."""
+    from scipy.spatial import Delaunay, cKDTree
+    base = square_halton(n, seed)
+    x2 = base.coords().copy()
+    nb = base.meta["n_boundary"]
+    h = 1.0 / int(math.isqrt(n))
+    s = math.sqrt(1.0 / n)
+    for _ in range(iters):
+        d, idx = cKDTree(x2).query(x2[nb:], 9)
+        d, idx = d[:, 1:], idx[:, 1:]
+        away = (x2[nb:, None, :] - x2[idx]) / d[..., None]
+        f = (away * ((s / d) ** 3)[..., None]).sum(1)
+        mag = np.linalg.norm(f, axis=1, keepdims=True)
+        x2[nb:] += 0.1 * s * f / np.maximum(mag, 1e-300) * np.minimum(1.0, mag)
+        x2[nb:] = np.clip(x2[nb:], 0.5 * h, 1.0 - 0.5 * h)
+    tris = _orient_flat(x2, Delaunay(x2).simplices)
+    return NodeSet(_pad3(x2), tris, None, 2, area=1.0,
+                   meta={"kind": "square_repulsion", "n_boundary": nb, "iters": iters, "seed": seed})
+
+
 def square_regular(rows: int = 24) -> NodeSet:
     """Unit square with interior nodes on an equilateral triangular lattice and
     equispaced boundary nodes (the paper's "regular grid", §4.1 and Supplementary).

@@ -252,3 +252,35 @@ def test_periodic_models(nf):
                                   beta_d=float(np.float32(0.6)), integrator="ab5")
     assert rel_l2(u.cpu().numpy(), wu) < REL_L2
     assert rel_l2(s.cpu().numpy(), ws) < REL_L2
+
+
+@pytest.mark.parametrize("path", [0, 1, 2, 4])
+def test_spatial_error_map_unit_square(nf, path):
+    """§4.2, Eq. (flat_spatial_error) on the unit square (period 1): the oracle's weights on
+    point-repulsion nodes (n = 2000, r^3, k = 21, deg 3), a 64 x 64 grid of centres x0
+    appended as nodes of weight 0, f = 1, so that row x0 of the sum is Q_n f_x0 for the
+    periodic Gaussian of sigma = 1/10.  Every path against the oracle on the grid rows, and
+    the mean of E(x0) = 1 - Q_n f_x0 / Q f_x0 near zero, as the exactness for constants
+    requires."""
+    import nodesets
+    from scipy.special import erf
+    ns = nodesets.square_repulsion(2000)
+    x2 = ns.coords()
+    q = oracle.quad_weights(x2, ns.tris, oracle.knn(x2, ns.tris, 21), 3)
+    m = 64
+    t = (np.arange(m) + 0.5) / m
+    c = np.stack(np.meshgrid(t, t, indexing="ij"), -1).reshape(-1, 2)
+    X = np.concatenate([ns.nodes, np.concatenate([c, np.zeros((m * m, 1))], 1)]).astype(np.float32)
+    qa = np.concatenate([q, np.zeros(m * m)]).astype(np.float32)
+    s = math.sqrt(2.0) * 0.1
+    kern = (1.0, s, 0.0, s, 1.0)
+    u = np.full((1, X.shape[0]), 50.0, dtype=np.float32)
+    op = nf.Operator(dev(X), dev(qa), kern, path)
+    got = nf.nf_nonlocal_apply(op, dev(u), 1.0, 0.0).cpu().numpy()[0, ns.n:].astype(np.float64)
+    op.check()
+    rows = np.arange(ns.n, X.shape[0])
+    want = oracle.nonlocal_sum(f32(X), f32(qa), f32(u), f32(kern[:4]), 1.0, 0.0, rows=rows, period=1.0)[0]
+    assert rel_l2(got, want) < REL_L2
+    Qf = (s * math.sqrt(math.pi) * erf(0.5 / s)) ** 2
+    rms = math.sqrt((((Qf - want) / Qf) ** 2).mean())
+    assert abs(((Qf - got) / Qf).mean()) < 0.1 * rms

@@ -174,3 +174,28 @@ def test_flat_mms_convergence():
         ex = oracle.mms_flat_solution(x, T, kern, L, BETA, THETA, C0, RAD, SIG)
         errs.append(np.abs(u[0] - ex).max())
     assert errs[1] < errs[0] / 3.5, errs
+
+
+def test_spatial_error_of_periodic_gaussians_averages_to_zero():
+    """§4.2, Eq. (flat_spatial_error): E(x0) = (Q f_x0 - Q_n f_x0) / Q f_x0 for the
+    doubly periodic Gaussians f_x0 = exp(-|x - x0|^2 / (2 sigma^2)), sigma = 1/10, on the
+    unit square (point-repulsion nodes, n = 2000, r^3, k = 21, deg 3).  Q f_x0 does not
+    depend on x0, so the mean of E over x0 is 1 - sum q = 0: here the mean over a 64 x 64
+    grid of centres (appended to the node set with weight 0, f = 1) against the closed form
+    Q f = (s sqrt(pi) erf(1 / (2 s)))^2 with s = sqrt(2) sigma (nearest image)."""
+    import nodesets
+    ns = nodesets.square_repulsion(2000)
+    x2 = ns.coords()
+    q = oracle.quad_weights(x2, ns.tris, oracle.knn(x2, ns.tris, 21), 3)
+    m = 64
+    t = (np.arange(m) + 0.5) / m
+    c = np.stack(np.meshgrid(t, t, indexing="ij"), -1).reshape(-1, 2)
+    x = np.concatenate([ns.nodes, np.concatenate([c, np.zeros((m * m, 1))], 1)])
+    s = math.sqrt(2.0) * 0.1
+    Qn = oracle.nonlocal_sum(x, np.concatenate([q, np.zeros(m * m)]), np.full((1, x.shape[0]), 50.0),
+                             (1.0, s, 0.0, s), 1.0, 0.0, rows=np.arange(ns.n, ns.n + m * m), period=1.0)[0]
+    Qf = (s * math.sqrt(math.pi) * erf(0.5 / s)) ** 2
+    E = (Qf - Qn) / Qf
+    rms = math.sqrt((E ** 2).mean())
+    assert 1e-8 < rms < 1e-3          # small, and not identically zero
+    assert abs(E.mean()) < 1e-4 * rms  # averages to zero (midpoint rule on the kink of the nearest image: < 1e-8)

@@ -224,6 +224,26 @@ def test_flat_histogram_mode_near_one_over_n():
     assert mode == pytest.approx(fact["mode"], rel=0.25)
 
 
+def test_flat_repulsion_nodes_weight_structure():
+    """§4.2 on the paper's random node family (point repulsion, equispaced boundary;
+    n = 2000, r^3, k = 21, deg 3): constants integrate exactly, the main histogram mode
+    lies near 1/n, boundary weights are smaller than interior ones, and negative weights
+    are few and small (the paper counts five)."""
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    fact = gold["flat_square_weight_mode"]
+    ns = nodesets.square_repulsion(fact["n"])
+    q = _flat(ns, fact["k"], fact["deg"])
+    assert abs(q.sum() - 1.0) < 1e-12
+    hist, edges = np.histogram(q, bins=60)
+    mode = 0.5 * (edges[hist.argmax()] + edges[hist.argmax() + 1])
+    assert mode == pytest.approx(fact["mode"], rel=0.25)
+    nb = ns.meta["n_boundary"]
+    assert np.median(q[:nb]) < 0.75 * np.median(q[nb:])
+    assert (q < 0).sum() <= 5
+    assert q.min() > -0.1 * np.median(q)
+
+
 def test_flat_convergence_chebyshev():
     """§4.3: T5(2x-1) T4(2y-1) + 1 on the unit square (integral 1).  Random node sets
     make single errors noisy (§4.3 says so), so the RMS over three seeded node sets is
