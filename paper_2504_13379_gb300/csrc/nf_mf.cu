@@ -15,6 +15,7 @@
 #include "nf_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <map>
@@ -1276,12 +1277,15 @@ constexpr int kSymMaxB = 3;
 // above about 3 million on a GB300) the packed kernel, whose layout grows with its column
 // splits only, takes over.
 static bool sym_layout_fits(const nf_operator *op) {
-    static size_t budget = 0;
-    if (!budget) {
+    static std::atomic<size_t> budget[64];  // per device, an eighth of its memory
+    const int d = device_id();
+    size_t b = (d >= 0 && d < 64) ? budget[d].load() : 0;
+    if (!b) {
         size_t freeb = 0, total = 0;
-        budget = (cudaMemGetInfo(&freeb, &total) == cudaSuccess && total > 0) ? total / 8 : ((size_t)8 << 30);
+        b = (cudaMemGetInfo(&freeb, &total) == cudaSuccess && total > 0) ? total / 8 : ((size_t)8 << 30);
+        if (d >= 0 && d < 64) budget[d].store(b);
     }
-    return (double)(op->n_pad / MS_BLK) * (double)op->n_pad * sizeof(float) <= (double)budget;
+    return (double)(op->n_pad / MS_BLK) * (double)op->n_pad * sizeof(float) <= (double)b;
 }
 
 static bool use_sym(const nf_operator *op) {

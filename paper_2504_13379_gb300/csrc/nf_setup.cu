@@ -748,11 +748,8 @@ extern "C" nf_status nf_quad_weights(const double *nodes, const double *normals,
     cudaStream_t s = as_stream(stream);
     const int N = k + P;
     const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + N + 3 * (size_t)k + 6 + 24);
-    static size_t smem_set = 0;
-    if (smem > smem_set) {
-        NF_CUDA_TRY(cudaFuncSetAttribute(quad_element_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-    }
+    // per call: the attribute belongs to the current device, and a call costs microseconds
+    NF_CUDA_TRY(cudaFuncSetAttribute(quad_element_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t *nbr = nullptr;
     unsigned long long *keys = nullptr;
     long long *v0 = nullptr, *v1 = nullptr;
