@@ -626,7 +626,8 @@ __global__ void __launch_bounds__(QW_THREADS) quad_element_kernel(QwArgs a) {
     __syncthreads();
     const double anorm = misc[17];
 
-    // LU with partial pivoting (first maximal pivot), explicitly rounded updates
+    // LU with partial pivoting (first maximal pivot); each elimination update is one fused
+    // multiply-add (the FP64 pipe bounds this kernel, and the fusion halves its updates)
     for (int c = 0; c < N; ++c) {
         if (tid < 32) {
             double best = -1.0;
@@ -681,16 +682,16 @@ __global__ void __launch_bounds__(QW_THREADS) quad_element_kernel(QwArgs a) {
             const int cc = c + 1 + idx % cols;
             const double l = M[r * ld + c];
             if (cc < N)
-                M[r * ld + cc] = __dsub_rn(M[r * ld + cc], __dmul_rn(l, M[c * ld + cc]));
+                M[r * ld + cc] = __fma_rn(-l, M[c * ld + cc], M[r * ld + cc]);
             else
-                z[r] = __dsub_rn(z[r], __dmul_rn(l, z[c]));
+                z[r] = __fma_rn(-l, z[c], z[r]);
         }
         __syncthreads();
     }
     if (tid == 0) {
         for (int r = N - 1; r >= 0; --r) {
             double sacc = z[r];
-            for (int cc = r + 1; cc < N; ++cc) sacc = __dsub_rn(sacc, __dmul_rn(M[r * ld + cc], z[cc]));
+            for (int cc = r + 1; cc < N; ++cc) sacc = __fma_rn(-M[r * ld + cc], z[cc], sacc);
             z[r] = __ddiv_rn(sacc, M[r * ld + r]);
         }
     }
