@@ -43,7 +43,7 @@ typedef enum {
     NF_OK = 0,
     NF_ERR_ARG = 1,          /* invalid argument (null pointer, size, alignment, rule of §3.1) */
     NF_ERR_SINGULAR = 2,     /* an element's interpolation system is singular (§3.1) */
-    NF_ERR_NONFINITE = 3,    /* non-finite input or result detected */
+    NF_ERR_NONFINITE = 3,    /* an RK4 step produced a non-finite state (see nf_operator_check) */
     NF_ERR_TIMEOUT = 4,      /* a bounded device wait gave up; the kernel returned early */
     NF_ERR_NOMEM = 5,        /* device allocation failed */
     NF_ERR_CUDA = 6,         /* CUDA runtime / launch error */
@@ -156,8 +156,11 @@ NF_API nf_status nf_operator_destroy(nf_operator *op);
 NF_API nf_status nf_operator_group(nf_operator *const *ops, const int *B_per_op, int count, void *stream,
                                    nf_operator **grouped);
 
-/* Synchronise `stream` and report device-side failures recorded on the operator
- * (NF_ERR_TIMEOUT when a bounded wait in a kernel gave up).  Clears nothing. */
+/* Synchronise `stream` and report device-side failures recorded on the operator:
+ * NF_ERR_TIMEOUT when a bounded wait in a kernel gave up; NF_ERR_NONFINITE when a step of
+ * nf_rk4_advance on the matrix-free or a dense path left a non-finite value (NaN or
+ * infinity, e.g. from a non-finite initial state) in the state.  The first failure stays
+ * recorded: clears nothing. */
 NF_API nf_status nf_operator_check(nf_operator *op, void *stream);
 
 /* Measurement helpers.  With profiling enabled, the captured RK4 step records CUDA
@@ -280,7 +283,8 @@ NF_API nf_status nf_mms_sphere_eigs(nf_kernel kp, double *lam);
  *   ckpt   ((nsteps / C) + 1) x B x n FP32 device, or NULL: receives u at steps
  *          0, C, 2C, ... (checkpoints for nf_adjoint)
  * The step sequence is captured once in a CUDA graph and replayed.
- * Errors: NF_ERR_ARG, NF_ERR_CUDA. */
+ * Errors: NF_ERR_ARG, NF_ERR_CUDA; a non-finite state is recorded on the operator and
+ * reported as NF_ERR_NONFINITE by nf_operator_check. */
 NF_API nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt, int nsteps,
                          const float *beta, const float *theta, const nf_forcing *g,
                          float *ckpt, int C, void *stream);

@@ -376,6 +376,7 @@ nf_status nf_operator_check(nf_operator *op, void *stream) {
     int flag = 0;
     NF_CUDA_TRY(cudaMemcpy(&flag, op->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag == DEV_TIMEOUT) return fail(NF_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (flag == DEV_NONFINITE) return fail(NF_ERR_NONFINITE, "an RK4 step produced a non-finite state");
     if (flag != 0) return fail(NF_ERR_CUDA, "device error flag %d", flag);
     return NF_OK;
 }

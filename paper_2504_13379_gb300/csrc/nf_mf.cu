@@ -1812,6 +1812,7 @@ struct StageKArgs {
     unsigned *done_ctr;
     float *ckpt;
     int C;
+    int *err;           // operator's device flag: DEV_NONFINITE on a non-finite new state
 };
 
 // Flat manufactured forcing (NF_FORCE_MMS_FLAT).  One factor of the convolution term:
@@ -1900,6 +1901,7 @@ __global__ void rk4_stage_kernel(StageKArgs a) {
             const float unew = fmaf(dt / 6.f, a.ks[idx] + k, uv);
             a.u[idx] = unew;
             Un = unew;
+            if (!isfinite(unew) && *a.err == DEV_OK) atomicCAS(a.err, DEV_OK, DEV_NONFINITE);
             if (a.ckpt && ((step + 1) % a.C) == 0)
                 a.ckpt[(int64_t)((step + 1) / a.C) * a.B * a.n + idx] = unew;
         }
@@ -1958,6 +1960,7 @@ nf_status launch_stage(nf_operator *op, int B, const StageParams &p, cudaStream_
     a.done_ctr = op->done_ctr;
     a.ckpt = p.ckpt;
     a.C = p.C;
+    a.err = op->err;
     const int64_t tot = (int64_t)B * op->n;
     const int T = 256;
     rk4_stage_kernel<<<(unsigned)ceil_div(tot, T), T, 0, s>>>(a);

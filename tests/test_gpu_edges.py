@@ -94,3 +94,24 @@ def test_collapsed_node_set_closed_form(nf, path, B):
     I = nf.nf_nonlocal_apply(op, dev(u), dev(beta), dev(theta)).cpu().numpy().astype(np.float64)
     op.check()
     np.testing.assert_allclose(I, np.repeat(want[:, None], n, 1), rtol=1e-5)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_nonfinite_state_is_reported(nf, path):
+    """A NaN in the initial state spreads through the sums; the RK4 step records it on the
+    operator and the check reports NF_ERR_NONFINITE (a finite run on another operator of
+    the same nodes reports nothing)."""
+    rng = np.random.default_rng(40 + path)
+    n = 1500
+    X = dev(rng.uniform(-1, 1, (n, 3)))
+    q = dev(np.full(n, 1.0 / n))
+    u0 = rng.normal(size=(1, n)).astype(np.float32)
+    ok = nf.Operator(X, q, (1.0, 0.2, 0.5, 0.4), path)
+    nf.nf_rk4_advance(ok, dev(u0), 0.0, 0.05, 2, 20.0, 0.2)
+    ok.check()
+    u0[0, 7] = np.nan
+    bad = nf.Operator(X, q, (1.0, 0.2, 0.5, 0.4), path)
+    nf.nf_rk4_advance(bad, dev(u0), 0.0, 0.05, 2, 20.0, 0.2)
+    with pytest.raises(nf.NFError) as ei:
+        bad.check()
+    assert ei.value.name == "NF_ERR_NONFINITE"
