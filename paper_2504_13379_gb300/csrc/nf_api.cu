@@ -245,7 +245,7 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
 }
 
 static nf_status check_forcing(const nf_operator *op, const nf_forcing *g, const nf_forcing **out) {
-    static const nf_forcing none{NF_FORCE_NONE, nullptr, nullptr, 0, 0, 0, 0, 0};
+    static const nf_forcing none{NF_FORCE_NONE, nullptr, nullptr, 0, 0, 0, 0, 0, 0, 0, 0};
     if (!g) {
         *out = &none;
         return NF_OK;
