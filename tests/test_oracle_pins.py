@@ -211,6 +211,27 @@ def test_flat_regular_grid_interior_weights_equal_cell_area():
         np.testing.assert_allclose(q[inner], math.sqrt(3) / 2 * s * s, rtol=1e-12)
 
 
+def test_regular_grid_supplement_polynomial_and_gaussian():
+    """Supplement (regular triangular grid, r^3, k = 30): x^3 - y^4 is integrated exactly
+    once degree-4 polynomials are appended (and not with degree 3), and the Gaussian
+    exp(-10 |x - (1/2, 1/2)|^2), whose integral is (sqrt(pi/10) erf(sqrt(10)/2))^2, converges
+    faster than the appended degree in n^-1/2."""
+    from scipy.special import erf
+    exact_g = (math.sqrt(math.pi / 10) * erf(math.sqrt(10) / 2)) ** 2
+    exact_p = 0.25 - 0.2
+    errs, ns_ = [], []
+    for rows in (12, 40):
+        ns = nodesets.square_regular(rows)
+        x, y = ns.nodes[:, 0], ns.nodes[:, 1]
+        q4 = _flat(ns, 30, 4)
+        assert abs((q4 * (x ** 3 - y ** 4)).sum() - exact_p) < 1e-13
+        q3 = _flat(ns, 30, 3)
+        assert abs((q3 * (x ** 3 - y ** 4)).sum() - exact_p) > 1e-9
+        errs.append(abs((q4 * np.exp(-10 * ((x - 0.5) ** 2 + (y - 0.5) ** 2))).sum() - exact_g) / exact_g)
+        ns_.append(ns.n)
+    assert math.log(errs[0] / errs[1]) / math.log(math.sqrt(ns_[1] / ns_[0])) > 4.0, errs
+
+
 def test_flat_histogram_mode_near_one_over_n():
     """Fig. 3B: n = 2000 nodes on the unit square, r^3, k = 21, deg 3: the main mode of
     the weight histogram sits near 1/n = 0.0005 (the value printed in the caption)."""
