@@ -528,31 +528,37 @@ def test_manufactured_sphere_solution_converges():
 # Discrete adjoint against FP64 central differences
 # ----------------------------------------------------------------------------------
 
-def test_adjoint_matches_central_differences(rng):
+@pytest.mark.parametrize("period", [0.0, 2.0])
+def test_adjoint_matches_central_differences(rng, period):
+    """FP64 central differences (h = 1e-4) of L = |u(T) - target|^2 in the four kernel
+    parameters and in entries of u0, on the plain and on the doubly periodic distance (nodes
+    of the square of side 2, where the kernel reaches across the edges)."""
     n, B = 120, 2
     X = rng.uniform(-1, 1, size=(n, 3))
+    if period:
+        X[:, :2] += 1.0
+        X[:, 2] = 0.0
     q = rng.uniform(0.01, 0.03, n)
     u0 = rng.normal(0.3, 0.3, size=(B, n))
     kp = np.array([1.0, 0.4, 0.5, 0.8])
     beta, theta = np.array([8.0, 12.0]), np.array([0.2, 0.3])
     dt, N = 0.05, 12
     target = rng.normal(0.1, 0.2, size=(B, n))
-    uN = oracle.rk4(X, q, u0, kp, beta, theta, 0.0, dt, N)
-    gu, gk = oracle.adjoint(X, q, u0, kp, beta, theta, 0.0, dt, N, 2 * (uN - target))
+    uN = oracle.rk4(X, q, u0, kp, beta, theta, 0.0, dt, N, period=period)
+    gu, gk = oracle.adjoint(X, q, u0, kp, beta, theta, 0.0, dt, N, 2 * (uN - target), period=period)
+    loss = lambda u_, k_: oracle.loss(X, q, u_, k_, beta, theta, 0.0, dt, N, target, period=period)
     h = 1e-4
     for p in range(4):
         kp1, kp2 = kp.copy(), kp.copy()
         kp1[p] += h
         kp2[p] -= h
-        fd = (oracle.loss(X, q, u0, kp1, beta, theta, 0.0, dt, N, target)
-              - oracle.loss(X, q, u0, kp2, beta, theta, 0.0, dt, N, target)) / (2 * h)
+        fd = (loss(u0, kp1) - loss(u0, kp2)) / (2 * h)
         assert gk[:, p].sum() == pytest.approx(fd, rel=1e-6, abs=1e-9)
     for (b, i) in [(0, 3), (1, 77), (0, 119)]:
         up, um = u0.copy(), u0.copy()
         up[b, i] += h
         um[b, i] -= h
-        fd = (oracle.loss(X, q, up, kp, beta, theta, 0.0, dt, N, target)
-              - oracle.loss(X, q, um, kp, beta, theta, 0.0, dt, N, target)) / (2 * h)
+        fd = (loss(up, kp) - loss(um, kp)) / (2 * h)
         assert gu[b, i] == pytest.approx(fd, rel=1e-6, abs=1e-9)
 
 
