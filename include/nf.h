@@ -330,8 +330,11 @@ NF_API nf_status nf_field_advance(nf_operator *op, const nf_model *model, int in
  *   grad_u0   B x n FP32   output dL/du_0
  *   grad_kernel B x 4 FP32 output dL/d(A1, s1, A2, s2), per trajectory
  * Stages are recomputed segment by segment from the checkpoints.  The transposed pair
- * sum uses the symmetry of the radial kernel (W^T = W).
- * Errors: NF_ERR_ARG, NF_ERR_UNSUPPORTED (dense operators), NF_ERR_CUDA. */
+ * sum uses the symmetry of the radial kernel (W^T = W).  A manufactured forcing on the
+ * sphere enters as given (its eigenvalues are inputs, not functions of the kernel
+ * parameters here).
+ * Errors: NF_ERR_ARG, NF_ERR_UNSUPPORTED (dense operators; the flat manufactured forcing,
+ * which depends on the kernel parameters), NF_ERR_CUDA. */
 NF_API nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B, double t0, double dt,
                      int nsteps, const float *beta, const float *theta, const nf_forcing *g,
                      const float *lambda_T, float *grad_u0, float *grad_kernel, void *stream);
