@@ -143,15 +143,18 @@ def peaks():
         return {}
 
 
-# FP32 FMA-pipe lane operations per clock per SM (f32x2 instructions count two), and the
-# lane operations per ordered pair of the symmetric matrix-free kernel in its expanded form
+# Lane operations per ordered pair of the symmetric matrix-free kernel in its expanded form
 # with s2^2 / s1^2 = 4 (the workload's kernel): per unordered pair 3 FMA (exponent) +
 # 2 MUL (e1 = e2^4) + 2 FMA (row sums) + 2 FMA (column sums), plus per column and 8-row
 # pass 3 SUB + 3 FMA (centred column and n_j) and 1 ADD (column sums into shared memory):
-# 9.875 per unordered pair, 4.9375 per ordered pair.  Diagonal block pairs evaluate their
-# ordered pairs one by one, a 1/nb share of the work.
-FMA_LANES_PER_CLK_SM = 128.0
+# 9.875 per unordered pair, 4.9375 per ordered pair; and one SFU exponential per unordered
+# pair.  Diagonal block pairs evaluate their ordered pairs one by one, a 1/nb share of the
+# work.  The rates these counts are divided by (FP32 FMA-pipe lane operations and SFU ex2
+# per clock per SM) are measured in the same run by nf_probe_pipe; the nominal figures
+# (128 FP32 lanes, 16 SFU operations per clock per SM) are kept only as a fallback.
+FMA_LANES_PER_CLK_SM_NOMINAL = 128.0
 LANE_OPS_PER_PAIR = 9.875 / 2.0
+EX2_PER_PAIR = 0.5
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels:
 # mf_sym_kernel<8, 4> on the n = 100,000 torus; tc_grouped_kernel on the batched workload at
@@ -272,9 +275,11 @@ def batched_accuracy(wls, xs, qs, u0, beta, theta, got, rows_per_group=8):
     return (err2 / ref2) ** 0.5
 
 
-def run_batched(args, dev, steps):
+def run_batched(args, dev, steps, pipes=None):
     """Batched workload: 448 trajectories on four node sets.  Tensor-core path (grouped
-    tcgen05 GEMM, bf16 x 3) against the plain FP32 matrix-free comparator."""
+    tcgen05 GEMM, bf16 x 3) against two plain FP32 comparators on the same node sets and
+    the same fused RK4 stage kernel: the dense FP32 operators with the SIMT FP32 GEMM
+    (W streamed from HBM, FFMA on the CUDA cores), and the matrix-free FP32 pair kernel."""
     import torch
 
     import paper_2504_13379_gb300 as nf
@@ -305,22 +310,22 @@ def run_batched(args, dev, steps):
                        f"x 64 traj, k=32 deg=3",
            "setup_ms": setup_ms, "pair_evals_per_stage": pairs_per_stage}
 
-    def timed(step_fn, nsteps, kernel_ms_fn=None):
+    def timed(step_fn, nsteps, history_fn=None):
+        """Mean step time over nsteps back-to-back steps (L2 flushed between them); with
+        history_fn, the mean nonlocal-kernel time per launch read after the loop."""
         for _ in range(3):
             step_fn()
         torch.cuda.synchronize(dev)
-        tot, kern = 0.0, 0.0
-        for _ in range(nsteps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        for a, b in evs:
             flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             step_fn()
             b.record(stream)
-            b.synchronize()
-            tot += a.elapsed_time(b)
-            if kernel_ms_fn:
-                kern += sum(kernel_ms_fn())
-        return tot / nsteps, (kern / (4 * nsteps) if kernel_ms_fn else None)
+        torch.cuda.synchronize(dev)
+        tot = sum(a.elapsed_time(b) for a, b in evs)
+        kern = float(sum(sum(st) for st in history_fn(nsteps))) if history_fn else None
+        return tot / nsteps, (kern / (4 * nsteps) if history_fn else None)
 
     # ---- tensor-core path
     t0 = time.perf_counter()
@@ -328,12 +333,12 @@ def run_batched(args, dev, steps):
     grp = nf.GroupedOperator(ops, [wl.B for wl in wls])
     torch.cuda.synchronize(dev)
     build_ms = 1e3 * (time.perf_counter() - t0)
-    grp.profile(True)
+    grp.profile(True, ring=steps)
     first_sums = nf.nf_nonlocal_apply(grp, u0.view(1, -1), beta, theta).double().cpu().numpy().ravel()
     u = u0.clone()
     sampler = ClockSampler(dev.index or 0)
     sampler.start()
-    ms, kms = timed(lambda: nf.nf_rk4_advance(grp, u, 0.0, 0.05, 1, beta, theta), steps, grp.kernel_ms)
+    ms, kms = timed(lambda: nf.nf_rk4_advance(grp, u, 0.0, 0.05, 1, beta, theta), steps, grp.kernel_ms_history)
     clocks = sampler.stop()
     grp.check()
     pk = peaks()
@@ -361,8 +366,6 @@ def run_batched(args, dev, steps):
         op.close()
     del grp, ops
     torch.cuda.empty_cache()
-    # ---- plain FP32 comparator: matrix-free pair kernel, B_g trajectories per node set
-    mops = [nf.Operator(x, q, wl.kernel, nf.MATRIX_FREE) for x, q, wl in zip(xs, qs, wls)]
     blocks = []
     off, toff = 0, 0
     for wl in wls:
@@ -370,6 +373,53 @@ def run_batched(args, dev, steps):
                        theta[toff:toff + wl.B].contiguous()))
         off += wl.B * wl.n
         toff += wl.B
+    # ---- plain FP32 comparator 1: dense FP32 W planes, SIMT FP32 GEMM per node set
+    t0 = time.perf_counter()
+    dops = [nf.Operator(x, q, wl.kernel, nf.DENSE_FP32) for x, q, wl in zip(xs, qs, wls)]
+    torch.cuda.synchronize(dev)
+    dbuild_ms = 1e3 * (time.perf_counter() - t0)
+    dense_first = torch.cat([nf.nf_nonlocal_apply(op, ub, be, th).reshape(-1)
+                             for op, (ub, be, th) in zip(dops, blocks)]).double().cpu().numpy()
+    dblocks = [(ub.clone(), be, th) for ub, be, th in blocks]
+    for op in dops:
+        op.profile(True, ring=steps)
+
+    def dense_step():
+        for op, (ub, be, th) in zip(dops, dblocks):
+            nf.nf_rk4_advance(op, ub, 0.0, 0.05, 1, be, th)
+
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    ms_d, _ = timed(dense_step, steps)
+    dclocks = sampler.stop()
+    kd = sum(float(sum(sum(st) for st in op.kernel_ms_history(steps))) for op in dops) / (4 * steps)
+    for op in dops:
+        op.check()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_flops = float(sum(2 * wl.B * wl.n * wl.n for wl in wls))
+    lanes = (pipes or {}).get("fma_f32x2", {}).get("per_clk_per_sm") or 128.0
+    mhz = dclocks["sm_mhz"] or 1900.0
+    fp32_peak = sms * lanes * 2.0 * mhz * 1e6 / 1e12
+    fp32_ach = fp32_flops / (kd * 1e-3) / 1e12
+    out["simt_fp32_dense"] = {
+        "ms_per_step": ms_d, "rk4_steps_per_s": 1e3 / ms_d, "pair_evals_per_s": 4 * pairs_per_stage / (ms_d * 1e-3),
+        "kernel_ms_per_stage": kd, "build_ms": dbuild_ms, "clocks": dclocks,
+        "roofline": {"bound": "alu", "fp32": {"achieved": fp32_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                                              "frac": fp32_ach / fp32_peak,
+                                              "peak_basis": f"{sms} SMs x {lanes:.1f} FP32 FMA lanes/clk/SM "
+                                                            f"(measured f32x2 probe) x 2 flop x {mhz:.0f} MHz"}},
+        "gpu_launches_per_step": 4 * len(dops)}
+    if args.accuracy:
+        out["simt_fp32_dense"]["rel_l2_vs_oracle"] = batched_accuracy(
+            wls, [x.cpu().numpy() for x in xs], [q.cpu().numpy() for q in qs], u0.cpu().numpy(),
+            beta.cpu().numpy(), theta.cpu().numpy(), dense_first)
+    out["tc_speedup_vs_simt_fp32_dense"] = ms_d / ms
+    for op in dops:
+        op.close()
+    del dops
+    torch.cuda.empty_cache()
+    # ---- plain FP32 comparator 2: matrix-free pair kernel, B_g trajectories per node set
+    mops = [nf.Operator(x, q, wl.kernel, nf.MATRIX_FREE) for x, q, wl in zip(xs, qs, wls)]
 
     def mf_step():
         for op, (ub, be, th) in zip(mops, blocks):
@@ -736,6 +786,21 @@ def run_adjoint(args, dev):
                     "and 4 nsteps adjoint pair passes"}
 
 
+def probe_pipes(dev):
+    """Measured FP32 FMA (scalar and packed f32x2) and SFU ex2 rates per clock per SM."""
+    import paper_2504_13379_gb300 as nf
+
+    out = {}
+    for name, kind, iters in (("fma_f32", nf.PROBE_FMA, 100000), ("fma_f32x2", nf.PROBE_FMA2, 100000),
+                              ("ex2", nf.PROBE_EX2, 20000)):
+        nf.nf_probe_pipe(kind, 1000)  # warm-up
+        rate, mhz, ms = nf.nf_probe_pipe(kind, iters)
+        out[name] = {"per_clk_per_sm": rate, "sm_mhz": mhz, "ms": ms}
+    out["basis"] = ("one CTA of 1,024 threads per SM, 8 independent chains per thread, cycles from each SM's "
+                    "clock64; median over SMs (nf_probe_pipe)")
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -768,6 +833,7 @@ def run_ours(args, rank, world, local_rank):
     u0 = torch.as_tensor(wl.u0.astype(np.float32), device=dev)
     beta, theta = float(wl.beta[0]), float(wl.theta[0])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pipes = probe_pipes(dev)
     results = {}
     first_sums = {}
     clocks_all = []
@@ -780,7 +846,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         build_ms = 1e3 * (time.perf_counter() - tb)
         first_sums[pname] = nf.nf_nonlocal_apply(op, u0.view(1, -1), beta, theta).double().cpu().numpy().ravel()
-        op.profile(True)
+        op.profile(True, ring=args.steps)  # every timed step keeps its own kernel timings
         u = u0.clone()
         t_sim = 0.0
         for _ in range(args.warmup):
@@ -794,16 +860,16 @@ def run_ours(args, rank, world, local_rank):
         sampler.start()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        kern_ms = 0.0
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
             nf.nf_rk4_advance(op, u, t_sim, wl.dt, 1, beta, theta)
             ev[k][1].record(stream)
             t_sim += wl.dt
-            kern_ms += sum(op.kernel_ms())
         torch.cuda.synchronize(dev)
         clocks = sampler.stop()
+        # the nonlocal kernels' durations in every timed step, read after the loop
+        kern_ms = float(sum(sum(st) for st in op.kernel_ms_history(args.steps)))
         clocks_all.append(clocks)
         op.check()
         step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
@@ -854,13 +920,21 @@ def run_ours(args, rank, world, local_rank):
         mhz = clocks["sm_mhz"] or pk.get("clocks_under_load", {}).get("sm_mhz_median") or 1432.0
         nb = -(-n // 1024)
         ops = LANE_OPS_PER_PAIR * (1.0 + 1.0 / nb)
-        peak = sms * FMA_LANES_PER_CLK_SM * mhz * 1e6 / ops / 1e9     # Gpair/s on the FP32 FMA pipe
+        lanes = pipes["fma_f32x2"]["per_clk_per_sm"]
+        ex2 = pipes["ex2"]["per_clk_per_sm"]
+        fma_peak = sms * lanes * mhz * 1e6 / ops / 1e9                      # Gpair/s on the FP32 FMA pipe
+        sfu_peak = sms * ex2 * mhz * 1e6 / (EX2_PER_PAIR * (1.0 + 1.0 / nb)) / 1e9  # Gpair/s on the SFU
+        peak = min(fma_peak, sfu_peak)
         achieved = n * n / (kms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
                 "traffic": MF_TRAFFIC_BYTES if n == 100000 else None, "traffic_unit": "bytes per launch",
-                "peak_basis": f"{sms} SMs x {FMA_LANES_PER_CLK_SM:g} FP32 FMA-pipe lanes/clk x {mhz:.0f} MHz "
-                              f"(median SM clock in the timed region) / {ops:.3f} lane operations per ordered pair "
-                              f"(symmetric kernel, expanded form, m = 4; SFU: 0.5 exponentials per pair, not binding)"}
+                "peak_basis": f"measured: {sms} SMs x {lanes:.1f} FP32 FMA-pipe lane operations/clk/SM (f32x2 "
+                              f"probe in this run) x {mhz:.0f} MHz (median SM clock in the timed region) / "
+                              f"{ops:.3f} lane operations per ordered pair (symmetric kernel, expanded form, m = 4); "
+                              f"SFU ceiling {sfu_peak:.0f} Gpair/s from {ex2:.1f} ex2/clk/SM measured and "
+                              f"{EX2_PER_PAIR} exponentials per ordered pair",
+                "fma_pipe_peak": fma_peak, "sfu_peak": sfu_peak,
+                "nominal_peak_128_lanes": sms * FMA_LANES_PER_CLK_SM_NOMINAL * mhz * 1e6 / ops / 1e9}
     else:
         bytes_per = 4.0 * n * n
         achieved = bytes_per / (kms * 1e-3) / 1e9
@@ -882,11 +956,12 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": world * 4.0 * n * n / (e2e_ms * 1e-3), "unit": "pair-evals/s",
                 "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches_total,
+        "pipe_rates": pipes,
     }
     # the further sections are measured on rank 0 only (they are not part of `value`)
     extra = rank == 0
     if extra and not args.no_batched:
-        line["batched"] = run_batched(args, dev, args.steps)
+        line["batched"] = run_batched(args, dev, args.steps, pipes)
         line["gpu_launches"] += 4 * args.steps  # tensor-core path: one grouped GEMM per stage
     if extra and not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, dev)
@@ -907,7 +982,33 @@ def run_ours(args, rank, world, local_rank):
             line["paths"][p]["rel_l2_vs_oracle"] = e
         line["accuracy"] = {"metric": "relative L2 error of the first-stage sum vs the FP64 oracle",
                             "sample": line["cpu_baseline"]["sample"], **acc}
+    if "batched" in line:  # a compact copy as the last key, where a truncated log still shows it
+        line["batched_summary"] = batched_summary(line["batched"])
     return line if rank == 0 else None
+
+
+def batched_summary(b):
+    """Steps/s of the batched paths on the same box, roofline fractions, error, clocks."""
+    out = {"workload": b["workload"]}
+    for key in ("tc_bf16x3", "simt_fp32_dense", "mf_fp32"):
+        if key not in b:
+            continue
+        r = b[key]
+        e = {"rk4_steps_per_s": r["rk4_steps_per_s"], "ms_per_step": r["ms_per_step"]}
+        roof = r.get("roofline", {})
+        for part in ("hbm", "tensor", "fp32"):
+            if part in roof:
+                e[f"{part}_frac"] = roof[part]["frac"]
+        if "rel_l2_vs_oracle" in r:
+            e["rel_l2_vs_oracle"] = r["rel_l2_vs_oracle"]
+        if "clocks" in r:
+            e["sm_mhz"] = r["clocks"].get("sm_mhz")
+            e["clock_reasons"] = r["clocks"].get("reasons")
+        out[key] = e
+    for key in ("tc_speedup_vs_simt_fp32_dense", "tc_speedup_vs_plain_fp32"):
+        if key in b:
+            out[key] = b[key]
+    return out
 
 
 def main():

@@ -163,12 +163,22 @@ NF_API nf_status nf_operator_group(nf_operator *const *ops, const int *B_per_op,
  * recorded: clears nothing. */
 NF_API nf_status nf_operator_check(nf_operator *op, void *stream);
 
-/* Measurement helpers.  With profiling enabled, the captured RK4 step records CUDA
- * events immediately before and after each stage's nonlocal-sum launches (the
- * dominant kernels); nf_operator_kernel_ms waits for the most recent step and returns
- * the four stage durations in milliseconds (host float[4]). */
+/* Measurement helpers (no paper counterpart).  With profiling enabled, the captured RK4
+ * step records CUDA events immediately before and after each stage's nonlocal-sum
+ * launches (the dominant kernels).
+ *   nf_operator_profile: enable = 0 switches profiling off; enable = K >= 1 switches it on
+ *     with a ring of K event sets: the K most recent steps of nf_rk4_advance keep their
+ *     own timings (each graph replay records into the next set), so a caller can time
+ *     steps back to back and read them afterwards.  Resets the count of profiled steps.
+ *   nf_operator_kernel_ms: waits for the most recent profiled step and returns its four
+ *     stage durations in milliseconds (host float[4]).
+ *   nf_operator_kernel_ms_history: waits for the most recent profiled step and returns the
+ *     stage durations of the last `steps` profiled steps, oldest first (host float[4 steps]);
+ *     steps <= K and <= the steps launched since profiling was enabled.
+ * Errors: NF_ERR_ARG (profiling off, steps out of range), NF_ERR_CUDA. */
 NF_API nf_status nf_operator_profile(nf_operator *op, int enable);
 NF_API nf_status nf_operator_kernel_ms(nf_operator *op, float *ms);
+NF_API nf_status nf_operator_kernel_ms_history(nf_operator *op, int steps, float *ms);
 /* Launch shape of the matrix-free pair kernel picked by the operator's autotuner (timed
  * once per node count at creation): rows per warp, columns per shared-memory tile and
  * column splits (host ints; -1 for other paths). */
@@ -217,6 +227,18 @@ NF_API nf_status nf_operator_mf_cull(nf_operator *op, int enable, int64_t *live_
  * context stays usable afterwards. */
 NF_API nf_status nf_selftest_timeout(void *stream);
 
+/* Instruction-rate probe (no paper counterpart; it measures the denominators of the
+ * pair kernels' roofline).  One CTA of 1,024 threads per SM runs independent chains of
+ *   kind 0: fma.rn.f32        (1 FP32 FMA-pipe lane operation per instruction)
+ *   kind 1: fma.rn.f32x2      (2 lane operations per instruction)
+ *   kind 2: ex2.approx.ftz.f32 (1 SFU operation)
+ * `iters` times 64 per thread, timed by each SM's cycle counter.  Host outputs: the median
+ * over SMs of operations per clock per SM, the SM clock (MHz) implied by the slowest SM's
+ * cycles over the launch's wall time, and that wall time in ms.  Synchronises `stream`;
+ * allocates a few bytes stream-ordered.  Errors: NF_ERR_ARG, NF_ERR_CUDA. */
+NF_API nf_status nf_probe_pipe(int kind, int64_t iters, double *ops_per_clk_sm, double *sm_mhz, float *ms,
+                               void *stream);
+
 /* Nonlocal sum of Eq. (2.9) for B trajectories:
  *     I[b, i] = sum_j w(|x_i - x_j|) q_j f_b(u[b, j]).
  *   u      B x n  FP32   states (trajectory-major)
@@ -230,19 +252,44 @@ NF_API nf_status nf_nonlocal_apply(nf_operator *op, const float *u, int B, const
  * is a deployment convenience).  For callers that cannot allocate device memory when
  * they need the sum -- e.g. inside a host framework that owns all allocations, or a
  * fixed-budget loop where a cudaMalloc would synchronise the device -- it computes
- *     I[i] = sum_j w(|x_i - x_j|) q_j f(u[j])      (same kernels as the matrix-free path)
- * without an operator handle and without allocating: its working memory is a fixed
- * file-scope device array of about 2.6 MB, held by every GPU that loads the library
- * until the process exits.
+ *     I[i] = sum_j w(|x_i - x_j|) q_j f(u[j])
+ * without an operator handle and without allocating.  It runs the row-block x column-
+ * split pair kernel over ordered pairs with two exponentials per pair (not the
+ * operator's symmetric or packed kernels, which need per-operator set-up), so it is
+ * slower per pair than nf_nonlocal_apply on a matrix-free operator.  Its working memory
+ * is a fixed file-scope device array of about 2.6 MB, held by every GPU that loads the
+ * library until the process exits.
  *   x  n x 3 FP32, q n FP32, u n FP32, I n FP32 (output): caller-owned device memory.
- *   n  1 .. 32768 (larger n returns NF_ERR_ARG: the scratch size is fixed).
+ *   n  1 .. 32768 (larger n returns NF_ERR_ARG: the scratch size is fixed).  The pair
+ *      kernel uses at most 16 column splits, which is what the array holds.
  * The first call on a device looks up the array's device address (with that device
  * current); make that first call before any stream capture.  All calls share the
  * array: each call rewrites what it reads, but calls whose work overlaps on the GPU
  * race and must be serialised by the caller.  Returns after enqueuing on `stream`.
+ * A bounded device wait that gives up (NF_ERR_TIMEOUT, reported by nf_noalloc_status)
+ * makes the call write NaN to every entry of I instead of an incomplete sum.
  * Errors: NF_ERR_ARG, NF_ERR_CUDA. */
 NF_API nf_status nf_nonlocal_apply_noalloc(const float *x, const float *q, int64_t n, nf_kernel kp,
                                            const float *u, float beta, float theta, float *I, void *stream);
+
+/* Status of the most recent nf_nonlocal_apply_noalloc on this device (no paper
+ * counterpart): synchronises `stream`, then reads the scratch array's error flag.
+ * NF_OK, or NF_ERR_TIMEOUT when a bounded wait in that call gave up (its I is NaN).
+ * Allocates nothing. */
+NF_API nf_status nf_noalloc_status(void *stream);
+
+/* Limits of nf_nonlocal_apply_noalloc (no paper counterpart), host outputs: the largest
+ * n it accepts, the most column splits its scratch holds, and the splits a call on n
+ * nodes uses on the current device (always <= max_splits).  Errors: NF_ERR_ARG. */
+NF_API nf_status nf_noalloc_limits(int64_t n, int64_t *max_n, int *max_splits, int *splits);
+
+/* Failure-path self-test of the allocation-free call (no paper counterpart): records a
+ * timeout in the scratch array's flag, as a pair-kernel block that gave up waiting
+ * would, then runs the call's final reduction on n entries of I.  Afterwards every
+ * entry of I is NaN and nf_noalloc_status returns NF_ERR_TIMEOUT; the next
+ * nf_nonlocal_apply_noalloc clears the flag.  No kernel waits or faults.
+ * Errors: NF_ERR_ARG, NF_ERR_CUDA. */
+NF_API nf_status nf_selftest_noalloc_flag(int64_t n, float *I, void *stream);
 
 /* Forcing gamma(t) of Eq. (2.9).
  *  NF_FORCE_NONE: gamma = 0.

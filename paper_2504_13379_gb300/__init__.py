@@ -47,7 +47,9 @@ EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights"
            "nf_operator_destroy", "nf_operator_check", "nf_nonlocal_apply", "nf_mms_sphere_eigs",
            "nf_rk4_advance", "nf_adjoint", "nf_operator_profile", "nf_operator_kernel_ms",
            "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout",
-           "nf_operator_mf_schedule", "nf_operator_mf_cull", "nf_field_advance"]
+           "nf_operator_mf_schedule", "nf_operator_mf_cull", "nf_field_advance", "nf_noalloc_status",
+           "nf_noalloc_limits", "nf_selftest_noalloc_flag", "nf_operator_kernel_ms_history",
+           "nf_probe_pipe"]
 
 
 class NFError(RuntimeError):
@@ -103,12 +105,18 @@ def lib(path: str | None = None):
     L.nf_operator_check.argtypes = [_vp, _vp]
     L.nf_operator_profile.argtypes = [_vp, C.c_int]
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
+    L.nf_operator_kernel_ms_history.argtypes = [_vp, C.c_int, C.POINTER(C.c_float)]
     L.nf_operator_launch_shape.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.nf_operator_mf_schedule.argtypes = [_vp, C.c_int]
     L.nf_operator_mf_cull.argtypes = [_vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]
     L.nf_selftest_timeout.argtypes = [_vp]
     L.nf_nonlocal_apply.argtypes = [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]
     L.nf_nonlocal_apply_noalloc.argtypes = [_vp, _vp, _i64, _Kernel, _vp, C.c_float, C.c_float, _vp, _vp]
+    L.nf_noalloc_status.argtypes = [_vp]
+    L.nf_noalloc_limits.argtypes = [_i64, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nf_selftest_noalloc_flag.argtypes = [_i64, _vp, _vp]
+    L.nf_probe_pipe.argtypes = [C.c_int, _i64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_float),
+                                _vp]
     L.nf_mms_sphere_eigs.argtypes = [_Kernel, C.POINTER(C.c_double)]
     L.nf_rk4_advance.argtypes = [_vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp,
                                  C.POINTER(_Forcing), _vp, C.c_int, _vp]
@@ -219,15 +227,24 @@ class Operator:
             raise RuntimeError("operator destroyed")
         return self._h
 
-    def profile(self, enable: bool = True):
-        """Record events around each stage's nonlocal kernels in captured RK4 steps."""
-        _check(lib().nf_operator_profile(self.handle, int(enable)))
+    def profile(self, enable=True, ring: int = 1):
+        """Record events around each stage's nonlocal kernels in captured RK4 steps; the
+        last ``ring`` steps keep their own timings (read with :meth:`kernel_ms_history`)."""
+        _check(lib().nf_operator_profile(self.handle, max(1, int(ring)) if enable else 0))
 
     def kernel_ms(self):
         """Durations (ms) of the four stages' nonlocal kernels in the last RK4 step."""
         out = (C.c_float * 4)()
         _check(lib().nf_operator_kernel_ms(self.handle, out))
         return list(out)
+
+    def kernel_ms_history(self, steps: int):
+        """Stage durations (ms) of the last ``steps`` profiled RK4 steps, oldest first
+        (a list of 4-element lists)."""
+        out = (C.c_float * (4 * int(steps)))()
+        _check(lib().nf_operator_kernel_ms_history(self.handle, int(steps), out))
+        v = list(out)
+        return [v[4 * k:4 * k + 4] for k in range(int(steps))]
 
     def launch_shape(self):
         """(rows per warp, tile columns, column splits) of the matrix-free pair kernel."""
@@ -318,12 +335,55 @@ def nf_nonlocal_apply_noalloc(x: torch.Tensor, q: torch.Tensor, u: torch.Tensor,
                               out: torch.Tensor) -> torch.Tensor:
     """Single-trajectory nonlocal sum that allocates nothing (neither here nor in the
     library): for callers that cannot allocate device memory at call time.  ``out``
-    must be preallocated (n float32).  n <= 32768; calls that overlap on the GPU race."""
-    n = int(x.shape[0])
+    must be preallocated (n float32).  n <= 32768; calls that overlap on the GPU race.
+    x must be n x 3 and q, u, out hold n elements each, all on the current CUDA device
+    (checked here: the library trusts the sizes it is given)."""
+    n = int(x.shape[0]) if x.dim() >= 1 else 0
+    if x.dim() != 2 or tuple(x.shape) != (n, 3):
+        raise ValueError(f"x must be n x 3, got {tuple(x.shape)}")
+    for name, t in (("q", q), ("u", u), ("out", out)):
+        if t.numel() != n:
+            raise ValueError(f"{name} must hold n = {n} elements, got {t.numel()}")
+    cur = torch.cuda.current_device()
+    for name, t in (("x", x), ("q", q), ("u", u), ("out", out)):
+        if not t.is_cuda or t.device.index != cur:
+            raise ValueError(f"{name} must be on the current CUDA device cuda:{cur}, got {t.device}")
     _check(lib().nf_nonlocal_apply_noalloc(_dptr(x, torch.float32, "x"), _dptr(q, torch.float32, "q"), n,
                                            _kernel(kernel), _dptr(u, torch.float32, "u"), float(beta), float(theta),
                                            _dptr(out, torch.float32, "I"), _stream(x)))
     return out
+
+
+def nf_noalloc_status():
+    """Synchronise the current stream and raise NFError (NF_ERR_TIMEOUT) if the last
+    allocation-free sum on this device gave up a bounded wait (its output is then NaN)."""
+    _check(lib().nf_noalloc_status(_stream()))
+
+
+def nf_noalloc_limits(n: int):
+    """(largest n accepted, column splits the scratch holds, splits a call on n nodes uses)."""
+    mx, ms, sp = C.c_int64(), C.c_int(), C.c_int()
+    _check(lib().nf_noalloc_limits(int(n), C.byref(mx), C.byref(ms), C.byref(sp)))
+    return mx.value, ms.value, sp.value
+
+
+def nf_selftest_noalloc_flag(out: torch.Tensor):
+    """Record a timeout in the allocation-free call's flag and run its final reduction into
+    ``out`` (n float32): every entry becomes NaN.  Exercises the failure path without a wait."""
+    _check(lib().nf_selftest_noalloc_flag(out.numel(), _dptr(out, torch.float32, "I"), _stream(out)))
+    return out
+
+
+PROBE_FMA, PROBE_FMA2, PROBE_EX2 = 0, 1, 2
+
+
+def nf_probe_pipe(kind: int, iters: int = 20000):
+    """Measured rate of one instruction kind on every SM (PROBE_FMA: fma.rn.f32 lane
+    operations, PROBE_FMA2: fma.rn.f32x2 lane operations, PROBE_EX2: SFU ex2): returns
+    (operations per clock per SM, SM MHz during the probe, wall ms)."""
+    r, mhz, ms = C.c_double(), C.c_double(), C.c_float()
+    _check(lib().nf_probe_pipe(int(kind), int(iters), C.byref(r), C.byref(mhz), C.byref(ms), _stream()))
+    return r.value, mhz.value, ms.value
 
 
 def nf_rk4_advance(op: Operator, u: torch.Tensor, t0: float, dt: float, nsteps: int, beta, theta,

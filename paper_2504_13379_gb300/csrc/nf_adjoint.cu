@@ -104,6 +104,31 @@ __global__ void adj_finish_kernel(const double *__restrict__ gk, int cnt, float 
     if (t < cnt) out[t] = (float)gk[t];
 }
 
+// Stream-ordered scratch buffers of one call, released on every return path (an early
+// return after a failed launch or allocation frees what was allocated before it).
+struct StreamScratch {
+    cudaStream_t s;
+    void *p[8] = {};
+    int count = 0;
+    explicit StreamScratch(cudaStream_t st) : s(st) {}
+    StreamScratch(const StreamScratch &) = delete;
+    StreamScratch &operator=(const StreamScratch &) = delete;
+    template <typename T>
+    cudaError_t alloc(T **out, size_t bytes) {
+        *out = nullptr;
+        if (count == 8) return cudaErrorInvalidValue;
+        void *q = nullptr;
+        const cudaError_t e = cudaMallocAsync(&q, bytes, s);
+        if (e != cudaSuccess) return e;
+        p[count++] = q;
+        *out = static_cast<T *>(q);
+        return cudaSuccess;
+    }
+    ~StreamScratch() {
+        for (int i = 0; i < count; ++i) cudaFreeAsync(p[i], s);
+    }
+};
+
 }  // namespace nfi
 
 using namespace nfi;
@@ -136,14 +161,15 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     float *stages = nullptr, *lam = nullptr, *acc = nullptr, *ubuf = nullptr, *wpart = nullptr, *gpart = nullptr;
     float2 *vg = nullptr;
     double *gk = nullptr;
-    NF_CUDA_TRY(cudaMallocAsync(&stages, sizeof(float) * BN * 4 * Cseg, s));
-    NF_CUDA_TRY(cudaMallocAsync(&lam, sizeof(float) * BN, s));
-    NF_CUDA_TRY(cudaMallocAsync(&acc, sizeof(float) * BN, s));
-    NF_CUDA_TRY(cudaMallocAsync(&ubuf, sizeof(float) * BN, s));
-    NF_CUDA_TRY(cudaMallocAsync(&wpart, sizeof(float) * (size_t)slots * B * n_pad, s));
-    NF_CUDA_TRY(cudaMallocAsync(&gpart, sizeof(float) * 4 * (size_t)B * ncta, s));
-    NF_CUDA_TRY(cudaMallocAsync(&vg, sizeof(float2) * (size_t)B * n_pad, s));
-    NF_CUDA_TRY(cudaMallocAsync(&gk, sizeof(double) * 4 * B, s));
+    StreamScratch scratch(s);  // freed (stream-ordered) on every return below
+    NF_CUDA_TRY(scratch.alloc(&stages, sizeof(float) * BN * 4 * Cseg));
+    NF_CUDA_TRY(scratch.alloc(&lam, sizeof(float) * BN));
+    NF_CUDA_TRY(scratch.alloc(&acc, sizeof(float) * BN));
+    NF_CUDA_TRY(scratch.alloc(&ubuf, sizeof(float) * BN));
+    NF_CUDA_TRY(scratch.alloc(&wpart, sizeof(float) * (size_t)slots * B * n_pad));
+    NF_CUDA_TRY(scratch.alloc(&gpart, sizeof(float) * 4 * (size_t)B * ncta));
+    NF_CUDA_TRY(scratch.alloc(&vg, sizeof(float2) * (size_t)B * n_pad));
+    NF_CUDA_TRY(scratch.alloc(&gk, sizeof(double) * 4 * B));
     NF_CUDA_TRY(cudaMemsetAsync(vg, 0, sizeof(float2) * (size_t)B * n_pad, s));  // padded columns stay zero
     NF_CUDA_TRY(cudaMemsetAsync(gk, 0, sizeof(double) * 4 * B, s));
     NF_CUDA_TRY(cudaMemcpyAsync(lam, lambda_T, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
@@ -153,15 +179,14 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     const int T = 256;
     const unsigned eg = (unsigned)ceil_div((int64_t)BN, T);
     const int nseg = (nsteps + C - 1) / C;
-    nf_status st = NF_OK;
-    for (int seg = nseg - 1; seg >= 0 && st == NF_OK; --seg) {
+    for (int seg = nseg - 1; seg >= 0; --seg) {
         const int s0 = seg * C;
         const int cnt = std::min(C, nsteps - s0);
         // ---- recompute the segment forward, keeping every stage input
         NF_CUDA_TRY(cudaMemcpyAsync(ubuf, ckpt + (size_t)seg * BN, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
         NF_TRY(launch_prep_g(op, ubuf, B, beta, theta, true, s));
         NF_TRY(launch_set_clock(op, t0 + (double)s0 * dt, s));
-        for (int j = 0; j < cnt && st == NF_OK; ++j) {
+        for (int j = 0; j < cnt; ++j) {
             float *Sj = stages + (size_t)j * 4 * BN;
             NF_CUDA_TRY(cudaMemcpyAsync(Sj, ubuf, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
             for (int stage = 1; stage <= 4; ++stage) {
@@ -222,13 +247,5 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     NF_CUDA_TRY(cudaMemcpyAsync(grad_u0, lam, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
     adj_finish_kernel<<<(unsigned)ceil_div(4 * B, 256), 256, 0, s>>>(gk, 4 * B, grad_kernel);
     NF_CUDA_TRY(cudaGetLastError());
-    cudaFreeAsync(stages, s);
-    cudaFreeAsync(lam, s);
-    cudaFreeAsync(acc, s);
-    cudaFreeAsync(ubuf, s);
-    cudaFreeAsync(wpart, s);
-    cudaFreeAsync(gpart, s);
-    cudaFreeAsync(vg, s);
-    cudaFreeAsync(gk, s);
-    return st;
+    return NF_OK;
 }

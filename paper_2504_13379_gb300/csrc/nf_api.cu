@@ -85,7 +85,7 @@ SplitPlan mf_plan(nf_operator *op);
 SplitPlan dense_plan(nf_operator *op);
 
 int nonlocal_splits(nf_operator *op, int B) {
-    return (op->path == NF_MATRIX_FREE) ? mf_splits(op, B) : dense_splits(op);
+    return (op->path == NF_MATRIX_FREE) ? mf_splits(op, B) : dense_splits(op, B);
 }
 
 nf_status launch_nonlocal_partial(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
@@ -140,6 +140,7 @@ struct nf_graph_cache {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaGraphNode_t prof_nodes[8] = {};  // the graph's event-record nodes, by event index
 };
 
 namespace nfi {
@@ -181,7 +182,7 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
     for (int stage = 1; stage <= 4 && st == NF_OK; ++stage) {
         int splits = 1;
         if (op->profile) {
-            cudaError_t pe = cudaEventRecordWithFlags(op->prof_ev[2 * (stage - 1)], cs, cudaEventRecordExternal);
+            cudaError_t pe = cudaEventRecordWithFlags(op->prof_ring[2 * (stage - 1)], cs, cudaEventRecordExternal);
             if (pe != cudaSuccess) {
                 st = cuda_fail(pe, "cudaEventRecord", __FILE__, __LINE__);
                 break;
@@ -191,7 +192,7 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
             // stage s reads the F buffer written by stage s-1: odd stages read buffer 0
             st = tc_launch(op, (stage - 1) & 1, 1, nullptr, u, beta, theta, dt, stage, ckpt, C, cs);
             if (st == NF_OK && op->profile) {
-                cudaError_t pe = cudaEventRecordWithFlags(op->prof_ev[2 * (stage - 1) + 1], cs, cudaEventRecordExternal);
+                cudaError_t pe = cudaEventRecordWithFlags(op->prof_ring[2 * (stage - 1) + 1], cs, cudaEventRecordExternal);
                 if (pe != cudaSuccess) st = cuda_fail(pe, "cudaEventRecord", __FILE__, __LINE__);
             }
             continue;
@@ -199,7 +200,7 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
         st = launch_nonlocal_partial(op, B, cs, &splits);
         if (st != NF_OK) break;
         if (op->profile) {
-            cudaError_t pe = cudaEventRecordWithFlags(op->prof_ev[2 * (stage - 1) + 1], cs, cudaEventRecordExternal);
+            cudaError_t pe = cudaEventRecordWithFlags(op->prof_ring[2 * (stage - 1) + 1], cs, cudaEventRecordExternal);
             if (pe != cudaSuccess) {
                 st = cuda_fail(pe, "cudaEventRecord", __FILE__, __LINE__);
                 break;
@@ -230,6 +231,26 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
         return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
     }
     c->graph = g;
+    if (op->profile) {  // find the event-record nodes, so replays can retarget them
+        size_t cnt = 0;
+        NF_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &cnt));
+        cudaGraphNode_t *nodes = new cudaGraphNode_t[cnt];
+        cudaError_t ge = cudaGraphGetNodes(g, nodes, &cnt);
+        for (int k = 0; k < 8; ++k) c->prof_nodes[k] = nullptr;
+        for (size_t i = 0; i < cnt && ge == cudaSuccess; ++i) {
+            cudaGraphNodeType ty;
+            ge = cudaGraphNodeGetType(nodes[i], &ty);
+            if (ge != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            ge = cudaGraphEventRecordNodeGetEvent(nodes[i], &ev);
+            for (int k = 0; k < 8 && ge == cudaSuccess; ++k)
+                if (ev == op->prof_ring[k]) c->prof_nodes[k] = nodes[i];
+        }
+        delete[] nodes;
+        if (ge != cudaSuccess) return cuda_fail(ge, "cudaGraphGetNodes (profiling events)", __FILE__, __LINE__);
+        for (int k = 0; k < 8; ++k)
+            if (!c->prof_nodes[k]) return fail(NF_ERR_CUDA, "profiling event %d not found in the step graph", k);
+    }
     c->valid = true;
     c->u = u;
     c->B = B;
@@ -242,6 +263,31 @@ static nf_status rk4_step_graph(nf_operator *op, float *u, int B, double dt, con
     c->C = C;
     *out = c->exec;
     return NF_OK;
+}
+
+// Replay the captured step nsteps times; with profiling on, each replay records its stage
+// timings into the next slot of the operator's event ring.
+static nf_status launch_steps(nf_operator *op, cudaGraphExec_t exec, int nsteps, cudaStream_t s) {
+    const bool ring = op->profile && op->prof_slots > 1 && op->graphs;
+    for (int st = 0; st < nsteps; ++st) {
+        if (ring) {
+            const int slot = (int)(op->prof_steps % op->prof_slots);
+            for (int k = 0; k < 8; ++k)
+                NF_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(exec, op->graphs->prof_nodes[k],
+                                                                 op->prof_ring[8 * slot + k]));
+        }
+        NF_CUDA_TRY(cudaGraphLaunch(exec, s));
+        if (op->profile) ++op->prof_steps;
+    }
+    return NF_OK;
+}
+
+static void destroy_prof_ring(nf_operator *op) {
+    for (int i = 0; i < 8 * op->prof_slots; ++i)
+        if (op->prof_ring[i]) cudaEventDestroy(op->prof_ring[i]);
+    delete[] op->prof_ring;
+    op->prof_ring = nullptr;
+    op->prof_slots = 0;
 }
 
 static nf_status check_forcing(const nf_operator *op, const nf_forcing *g, const nf_forcing **out) {
@@ -342,8 +388,7 @@ nf_status nf_operator_destroy(nf_operator *op) {
     if (!op) return NF_OK;
     destroy_graphs(op);
     destroy_group(op);
-    for (cudaEvent_t &ev : op->prof_ev)
-        if (ev) cudaEventDestroy(ev);
+    destroy_prof_ring(op);
     cudaFree(op->x4);
     cudaFree(op->xyz);
     cudaFree(op->rowperm);
@@ -425,8 +470,7 @@ nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt,
         NF_TRY(rk4_step_graph(op, u, B, dt, beta, theta, *F, ckpt, ckpt ? C : 1, &exec));
         NF_TRY(tc_prep(op, u, beta, theta, true, 0, s));
         NF_TRY(launch_set_clock(op, t0, s));
-        for (int st = 0; st < nsteps; ++st) NF_CUDA_TRY(cudaGraphLaunch(exec, s));
-        return NF_OK;
+        return launch_steps(op, exec, nsteps, s);
     }
     if (ckpt) NF_CUDA_TRY(cudaMemcpyAsync(ckpt, u, sizeof(float) * B * op->n, cudaMemcpyDeviceToDevice, s));
     if (nsteps == 0) return NF_OK;
@@ -435,27 +479,41 @@ nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt,
     NF_TRY(rk4_step_graph(op, u, B, dt, beta, theta, *F, ckpt, ckpt ? C : 1, &exec));
     NF_TRY(launch_prep_g(op, u, B, beta, theta, true, s));
     NF_TRY(launch_set_clock(op, t0, s));
-    for (int st = 0; st < nsteps; ++st) NF_CUDA_TRY(cudaGraphLaunch(exec, s));
-    return NF_OK;
+    return launch_steps(op, exec, nsteps, s);
 }
 
 nf_status nf_operator_profile(nf_operator *op, int enable) {
     clear_error();
     NF_ARG(op, "op is NULL");
-    if (enable && !op->prof_ev[0])
-        for (cudaEvent_t &ev : op->prof_ev) NF_CUDA_TRY(cudaEventCreate(&ev));
+    NF_ARG(enable >= 0 && enable <= 4096, "enable = %d must be 0 (off) or a ring of 1..4096 steps", enable);
+    if (enable > 0 && enable != op->prof_slots) {
+        destroy_graphs(op);  // captured steps name the old events
+        destroy_prof_ring(op);
+        op->prof_ring = new cudaEvent_t[8 * (size_t)enable]();
+        op->prof_slots = enable;
+        for (int i = 0; i < 8 * enable; ++i) NF_CUDA_TRY(cudaEventCreate(&op->prof_ring[i]));
+    }
     op->profile = enable != 0;
+    op->prof_steps = 0;
     return NF_OK;
 }
 
-nf_status nf_operator_kernel_ms(nf_operator *op, float *ms) {
+nf_status nf_operator_kernel_ms_history(nf_operator *op, int steps, float *ms) {
     clear_error();
     NF_ARG(op && ms, "op and ms must be non-NULL");
-    NF_ARG(op->profile && op->prof_ev[0], "profiling is not enabled on this operator");
-    NF_CUDA_TRY(cudaEventSynchronize(op->prof_ev[7]));
-    for (int st = 0; st < 4; ++st) NF_CUDA_TRY(cudaEventElapsedTime(&ms[st], op->prof_ev[2 * st], op->prof_ev[2 * st + 1]));
+    NF_ARG(op->profile && op->prof_ring, "profiling is not enabled on this operator");
+    NF_ARG(steps >= 1 && steps <= op->prof_slots && steps <= op->prof_steps,
+           "steps = %d: %lld profiled steps launched, the ring keeps %d", steps, op->prof_steps, op->prof_slots);
+    const long long last = op->prof_steps - 1;
+    NF_CUDA_TRY(cudaEventSynchronize(op->prof_ring[8 * (int)(last % op->prof_slots) + 7]));
+    for (int k = 0; k < steps; ++k) {
+        const cudaEvent_t *ev = op->prof_ring + 8 * (int)((last - steps + 1 + k) % op->prof_slots);
+        for (int st = 0; st < 4; ++st) NF_CUDA_TRY(cudaEventElapsedTime(&ms[4 * k + st], ev[2 * st], ev[2 * st + 1]));
+    }
     return NF_OK;
 }
+
+nf_status nf_operator_kernel_ms(nf_operator *op, float *ms) { return nf_operator_kernel_ms_history(op, 1, ms); }
 
 nf_status nf_selftest_timeout(void *stream) {
     clear_error();

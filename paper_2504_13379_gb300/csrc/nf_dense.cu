@@ -352,6 +352,159 @@ gemv_sym_fp32_kernel(const float *__restrict__ K, const float *__restrict__ g_al
     }
 }
 
+// ---------------------------------------------------------------- GEMM (several trajectories)
+// I[b, i] = sum_j WQ[i, j] F[b, j] for B >= kGemmMinB trajectories on the FP32 plane: a
+// register-tiled SIMT GEMM on the FP32 FMA pipe (the plain-FP32 counterpart of the batched
+// tensor-core path), so that W is streamed once per 128 or 64 trajectories instead of once
+// per trajectory.  CTA tile 128 rows (i) x GB_BN trajectories (b) x 16 columns (j) per
+// step, 256 threads; thread (tm, tn) = (tid & 15, tid >> 4) owns the row pairs
+// (2 tm + 32 r, 2 tm + 32 r + 1), r = 0..3, and the trajectories tn * 4 + c (plus
+// 64 + tn * 4 + c when GB_BN = 128).  Accumulators are FP32 pairs along i, updated by
+// fma.rn.f32x2 with the trajectory operand stored twice in shared memory (f, f): per k a
+// warp reads its 32 rows' W values as one 128-byte row of pairs and its two trajectories'
+// F values by broadcast.  Tiles are staged through registers into double-buffered shared
+// memory (transposed: k-major).  Small node sets split K (grid z) into partial-sum slots
+// that the stage kernel adds in a fixed order.
+constexpr int GB_BM = 128, GB_BK = 16, GB_THREADS = 256;
+constexpr int kGemmMinB = 8;
+
+template <int GB_BN>
+struct GemmSmem {
+    float a[2][GB_BK][GB_BM];                   // W tile, k-major
+    unsigned long long b[2][GB_BK][GB_BN];      // (f, f) pairs, k-major
+};
+
+typedef unsigned long long u64d;
+__device__ __forceinline__ u64d d_fma2(u64d a, u64d b, u64d c) {
+    u64d d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64d d_pack(float lo, float hi) {
+    u64d d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+
+template <int GB_BN>
+__global__ void __launch_bounds__(GB_THREADS, 2)
+gemm_fp32_kernel(const float *__restrict__ W, const float *__restrict__ F, int64_t n_pad, int B, int64_t kchunk,
+                 float *__restrict__ partial) {
+    constexpr int NC = GB_BN / 16;                   // trajectories per thread (8 or 4)
+    constexpr int BLD = GB_BN * 4 / GB_THREADS;      // float4 loads of the F tile per thread (2 or 1)
+    extern __shared__ __align__(16) unsigned char gm_raw[];
+    GemmSmem<GB_BN> &sm = *reinterpret_cast<GemmSmem<GB_BN> *>(gm_raw);
+    const int tid = threadIdx.x, tm = tid & 15, tn = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * GB_BM;
+    const int n0 = blockIdx.y * GB_BN;
+    const int64_t k0 = (int64_t)blockIdx.z * kchunk, k1 = min(n_pad, k0 + kchunk);
+    const int nkt = (int)((k1 - k0) / GB_BK);
+    float4 ra[2], rb[BLD];
+    auto load = [&](int kt) {
+        const int64_t kb = k0 + (int64_t)kt * GB_BK;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int idx = tid + GB_THREADS * p, r = idx >> 2, kq = idx & 3;
+            ra[p] = __ldg(reinterpret_cast<const float4 *>(W + (m0 + r) * n_pad + kb + 4 * kq));
+        }
+#pragma unroll
+        for (int p = 0; p < BLD; ++p) {
+            const int idx = tid + GB_THREADS * p, c = idx >> 2, kq = idx & 3;
+            const int b = n0 + c;
+            rb[p] = b < B ? __ldg(reinterpret_cast<const float4 *>(F + (int64_t)b * n_pad + kb + 4 * kq))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int idx = tid + GB_THREADS * p, r = idx >> 2, kq = idx & 3;
+            sm.a[buf][4 * kq + 0][r] = ra[p].x;
+            sm.a[buf][4 * kq + 1][r] = ra[p].y;
+            sm.a[buf][4 * kq + 2][r] = ra[p].z;
+            sm.a[buf][4 * kq + 3][r] = ra[p].w;
+        }
+#pragma unroll
+        for (int p = 0; p < BLD; ++p) {
+            const int idx = tid + GB_THREADS * p, c = idx >> 2, kq = idx & 3;
+            sm.b[buf][4 * kq + 0][c] = d_pack(rb[p].x, rb[p].x);
+            sm.b[buf][4 * kq + 1][c] = d_pack(rb[p].y, rb[p].y);
+            sm.b[buf][4 * kq + 2][c] = d_pack(rb[p].z, rb[p].z);
+            sm.b[buf][4 * kq + 3][c] = d_pack(rb[p].w, rb[p].w);
+        }
+    };
+    u64d acc[4][NC];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[r][c] = 0ull;
+    if (nkt > 0) {
+        load(0);
+        store(0);
+    }
+    __syncthreads();
+    for (int kt = 0; kt < nkt; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nkt) load(kt + 1);  // global loads in flight during the compute below
+#pragma unroll 4
+        for (int k = 0; k < GB_BK; ++k) {
+            u64d bd[NC];
+#pragma unroll
+            for (int c2 = 0; c2 < NC; c2 += 2) {
+                const int col = (c2 < 4 ? tn * 4 : 64 + tn * 4) + (c2 & 3);
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(&sm.b[buf][k][col]);
+                bd[c2] = v.x;
+                bd[c2 + 1] = v.y;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const u64d a = *reinterpret_cast<const u64d *>(&sm.a[buf][k][2 * tm + 32 * r]);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[r][c] = d_fma2(a, bd[c], acc[r][c]);
+            }
+        }
+        if (kt + 1 < nkt) store(buf ^ 1);
+        __syncthreads();
+    }
+    float *out = partial + (int64_t)blockIdx.z * B * n_pad;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int b = n0 + (c < 4 ? tn * 4 : 64 + tn * 4) + (c & 3);
+        if (b >= B) continue;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            *reinterpret_cast<u64d *>(out + (int64_t)b * n_pad + m0 + 2 * tm + 32 * r) = acc[r][c];
+    }
+}
+
+// (K splits, K columns per split) of the GEMM: enough CTAs for two waves where the output
+// tiles alone give fewer, at most 16 splits.
+static SplitPlan gemm_plan(const nf_operator *op, int B) {
+    SplitPlan p{};
+    const int bn = B > 64 ? 128 : 64;
+    const int64_t tiles = (op->n_pad / GB_BM) * ((B + bn - 1) / bn);
+    const int64_t ktiles = op->n_pad / GB_BK;
+    const int64_t want = 2 * (int64_t)num_sms() * 2;  // two waves of two CTAs per SM
+    int s = 1;
+    while (s < 16 && tiles * s < want && ktiles / (s + 1) >= 64) ++s;
+    const int64_t per = ceil_div(ktiles, s);
+    p.rows_per_block = GB_BM;
+    p.row_blocks = op->n_pad / GB_BM;
+    p.splits = (int)ceil_div(ktiles, per);
+    p.jchunk = per * GB_BK;
+    return p;
+}
+
+static bool use_gemm(const nf_operator *op, int B) { return op->path == NF_DENSE_FP32 && B >= kGemmMinB; }
+
+nf_status dense_init_attrs() {
+    NF_CUDA_TRY(cudaFuncSetAttribute(gemm_fp32_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(GemmSmem<128>)));
+    NF_CUDA_TRY(cudaFuncSetAttribute(gemm_fp32_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(GemmSmem<64>)));
+    return NF_OK;
+}
+
 SplitPlan dense_plan(nf_operator *op) {
     int res = 0;
     if (op->path == NF_DENSE_FP32)
@@ -361,7 +514,8 @@ SplitPlan dense_plan(nf_operator *op) {
     return plan_splits(op->n_pad, DG_ROWS, DG_TILE, std::max(res, 1));
 }
 
-int dense_splits(nf_operator *op) {
+int dense_splits(nf_operator *op, int B) {
+    if (use_gemm(op, B)) return gemm_plan(op, B).splits;
     return op->path == NF_DENSE_SYM_FP32 ? (int)(op->n_pad / SB) : dense_plan(op).splits;
 }
 
@@ -379,6 +533,21 @@ nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_
             NF_CUDA_TRY(cudaGetLastError());
         }
         *splits_out = (int)nb;
+        return NF_OK;
+    }
+    if (use_gemm(op, B)) {
+        const SplitPlan gp = gemm_plan(op, B);
+        if (B > 64) {
+            dim3 grid((unsigned)gp.row_blocks, (unsigned)((B + 127) / 128), (unsigned)gp.splits);
+            gemm_fp32_kernel<128><<<grid, GB_THREADS, sizeof(GemmSmem<128>), s>>>(op->W32, op->g, op->n_pad, B,
+                                                                                gp.jchunk, op->partial);
+        } else {
+            dim3 grid((unsigned)gp.row_blocks, (unsigned)((B + 63) / 64), (unsigned)gp.splits);
+            gemm_fp32_kernel<64><<<grid, GB_THREADS, sizeof(GemmSmem<64>), s>>>(op->W32, op->g, op->n_pad, B,
+                                                                              gp.jchunk, op->partial);
+        }
+        NF_CUDA_TRY(cudaGetLastError());
+        *splits_out = gp.splits;
         return NF_OK;
     }
     const SplitPlan pl = dense_plan(op);

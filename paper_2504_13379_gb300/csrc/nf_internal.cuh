@@ -207,9 +207,14 @@ struct nf_operator {
     double *t0_dev = nullptr;       // start time of the current nf_rk4_advance call
     nf_graph_cache *graphs = nullptr;
     nf_group_state *group = nullptr;   // grouped operators only (members are not owned)
-    // live kernel timing: events recorded around each stage's nonlocal launches
+    // live kernel timing: events recorded around each stage's nonlocal launches.  The step
+    // graph is captured with slot 0's eight events; before each replay the graph's event
+    // nodes are pointed at slot (step % prof_slots), so the last prof_slots steps keep
+    // their own timings until they are read.
     bool profile = false;
-    cudaEvent_t prof_ev[8] = {};
+    cudaEvent_t *prof_ring = nullptr;  // prof_slots x 8
+    int prof_slots = 0;
+    long long prof_steps = 0;          // profiled steps launched since profiling was enabled
 };
 
 namespace nfi {
@@ -230,7 +235,8 @@ struct SplitPlan {
     int splits;           // j-range splits (blockIdx.y)
     int64_t jchunk;       // columns per split, a multiple of the tile width
 };
-SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm);
+SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm,
+                      int max_splits = 64);
 
 nf_status ensure_workspace(nf_operator *op, int B, int splits);
 
@@ -249,10 +255,12 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
 nf_status mf_autotune(nf_operator *op, cudaStream_t s);
 void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits);
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out);
+SplitPlan plan_mf_pair_single(int64_t n_pad, int max_splits);
 nf_status launch_mf_pair_single(const float4 *x4, const float *g, int64_t n_pad, const nf_kernel &k, int max_splits,
                                 float *partial, int *err, cudaStream_t s, int *splits_out);
 nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_out);
-int dense_splits(nf_operator *op);           // partial-sum slots of a dense launch
+int dense_splits(nf_operator *op, int B);    // partial-sum slots of a dense launch over B trajectories
+nf_status dense_init_attrs();
 size_t dense_sym_entries(int64_t n_pad);     // stored entries of the symmetric blocked matrix
 // q is applied on the vector side (g = q o f) unless it is folded into a dense operator
 inline bool q_on_vector(const nf_operator *op) {

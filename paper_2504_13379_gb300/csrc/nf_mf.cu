@@ -1024,8 +1024,8 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
 
 // ----------------------------------------------------------------------------
 // split planner: (row blocks x column splits) items of equal cost; pick the number
-// of splits that best fills whole waves of resident blocks.
-SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm) {
+// of splits (at most max_splits) that best fills whole waves of resident blocks.
+SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resident_blocks_per_sm, int max_splits) {
     SplitPlan p{};
     p.rows_per_block = rows_per_block;
     p.row_blocks = n_pad / rows_per_block;
@@ -1033,7 +1033,7 @@ SplitPlan plan_splits(int64_t n_pad, int rows_per_block, int tile_cols, int resi
     const int64_t slots = (int64_t)num_sms() * std::max(1, resident_blocks_per_sm);
     double best = -1.0;
     int best_s = 1;
-    const int64_t smax = std::min<int64_t>(tiles, 64);
+    const int64_t smax = std::min<int64_t>(tiles, std::max(1, max_splits));
     for (int64_t s = 1; s <= smax; ++s) {
         const int64_t per = ceil_div(tiles, s);
         const int64_t s_eff = ceil_div(tiles, per);
@@ -1073,7 +1073,24 @@ static cudaError_t set_adj_attr() {
                                 (int)(AS_SMEM_FLOATS * sizeof(float)));
 }
 
+// The attributes belong to the device's context: set once per device (under a lock, so that
+// concurrent first calls on one device do not race), with that device current.
+static nf_status mf_init_attrs_device();
+
 nf_status mf_init_attrs() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    const int d = device_id();
+    if (d < 0 || d >= 64) return mf_init_attrs_device();
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[d]) return NF_OK;
+    NF_TRY(mf_init_attrs_device());
+    done[d] = true;
+    return NF_OK;
+}
+
+static nf_status mf_init_attrs_device() {
+    NF_TRY(dense_init_attrs());
     NF_CUDA_TRY((set_adj_attr<4, 0>()));
     NF_CUDA_TRY((set_adj_attr<4, 2>()));
     NF_CUDA_TRY((set_adj_attr<4, 3>()));
@@ -1603,18 +1620,18 @@ nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out
     return NF_OK;
 }
 
+// Launch plan of launch_mf_pair_single: at most max_splits column splits.
+SplitPlan plan_mf_pair_single(int64_t n_pad, int max_splits) {
+    const int R = mf_rows_per_warp(n_pad);
+    return plan_splits(n_pad, MF_WARPS * R, MF_TJ, R == 4 ? mf_resident<1, 4>() : mf_resident<1, 2>(), max_splits);
+}
+
 // Single-trajectory pair sums into caller-provided buffers (x4, g padded to n_pad,
-// partial [splits][n_pad]); the split count is capped at max_splits.
+// partial [splits][n_pad]); the planner considers at most max_splits column splits.
 nf_status launch_mf_pair_single(const float4 *x4, const float *g, int64_t n_pad, const nf_kernel &k, int max_splits,
                                 float *partial, int *err, cudaStream_t s, int *splits_out) {
     const int R = mf_rows_per_warp(n_pad);
-    SplitPlan pl = plan_splits(n_pad, MF_WARPS * R, MF_TJ, R == 4 ? mf_resident<1, 4>() : mf_resident<1, 2>());
-    if (pl.splits > max_splits) {
-        const int64_t tiles = n_pad / MF_TJ;
-        const int64_t per = ceil_div(tiles, max_splits);
-        pl.jchunk = per * MF_TJ;
-        pl.splits = (int)ceil_div(tiles, per);
-    }
+    const SplitPlan pl = plan_mf_pair_single(n_pad, max_splits);
     const float L2E = 1.4426950408889634f;
     const float c1 = -L2E / (k.s1 * k.s1), c2 = -L2E / (k.s2 * k.s2);
     dim3 grid((unsigned)pl.row_blocks, (unsigned)pl.splits, 1);

@@ -10,10 +10,19 @@
 // fixed size, which every GPU that loads this library keeps until the process exits.
 //
 // The array is shared by every call: each call rewrites the parts it reads (node
-// and firing-rate arrays including their zero padding) before using them, so no call
-// depends on an earlier call's contents, but calls whose work overlaps on the GPU
-// (for example on two streams at once) race on the array and must be serialised by
-// the caller.
+// and firing-rate arrays including their zero padding, the error flag) before using
+// them, so no call depends on an earlier call's contents, but calls whose work overlaps
+// on the GPU (for example on two streams at once) race on the array and must be
+// serialised by the caller.
+//
+// Failure reporting without a host round trip: the pair kernel records a bounded wait
+// that gave up in the array's flag word (and then skips its partial sums); the final
+// reduction reads the flag and, if it is set, writes NaN to every output entry instead
+// of adding partial sums that were never written.  nf_noalloc_status reads the flag back.
+//
+// The array's device address is looked up once per device and cached; the cache assumes
+// the device's primary context lives until the process exits (after cudaDeviceReset the
+// cached address would be stale).
 #include "nf_internal.cuh"
 
 #include <mutex>
@@ -72,14 +81,26 @@ __global__ void noalloc_pack_kernel(const float *__restrict__ x, const float *__
     }
 }
 
+// I[i] = sum of the splits' partial sums, in split order; NaN everywhere if a pair kernel
+// block gave up waiting (its partial sums were not written).
 __global__ void noalloc_reduce_kernel(const float *__restrict__ partial, int splits, int64_t n, int64_t n_pad,
-                                      float *__restrict__ I) {
+                                      const int *__restrict__ flag, float *__restrict__ I) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (*flag != 0) {
+        I[i] = __int_as_float(0x7fc00000);
+        return;
+    }
     float acc = 0.f;
     for (int sp = 0; sp < splits; ++sp) acc += partial[(int64_t)sp * n_pad + i];
     I[i] = acc;
 }
+
+// Stand-in for a pair kernel that gave up waiting: records a timeout in the flag.
+__global__ void noalloc_set_flag_kernel(int *flag, int code) { *flag = code; }
+
+// Column splits of a call on n_pad padded nodes (the partial-sum rows it writes).
+static int noalloc_splits(int64_t n_pad) { return plan_mf_pair_single(n_pad, kNoallocMaxSplits).splits; }
 
 }  // namespace nfi
 
@@ -107,7 +128,49 @@ extern "C" nf_status nf_nonlocal_apply_noalloc(const float *x, const float *q, i
     NF_CUDA_TRY(cudaGetLastError());
     int splits = 1;
     NF_TRY(launch_mf_pair_single(x4, g, n_pad, kp, kNoallocMaxSplits, partial, flag, s, &splits));
-    noalloc_reduce_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(partial, splits, n, n_pad, I);
+    noalloc_reduce_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(partial, splits, n, n_pad, flag, I);
+    NF_CUDA_TRY(cudaGetLastError());
+    return NF_OK;
+}
+
+extern "C" nf_status nf_noalloc_status(void *stream) {
+    clear_error();
+    nf_status st = NF_OK;
+    unsigned char *base = scratch_address(&st);
+    if (!base) return st;
+    cudaStream_t s = as_stream(stream);
+    NF_CUDA_TRY(cudaStreamSynchronize(s));
+    int flag = 0;
+    NF_CUDA_TRY(cudaMemcpy(&flag, base + kOffFlag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag == DEV_TIMEOUT) return fail(NF_ERR_TIMEOUT, "a bounded wait of the last allocation-free call gave up");
+    if (flag != 0) return fail(NF_ERR_CUDA, "device error flag %d", flag);
+    return NF_OK;
+}
+
+extern "C" nf_status nf_noalloc_limits(int64_t n, int64_t *max_n, int *max_splits, int *splits) {
+    clear_error();
+    NF_ARG(max_n && max_splits && splits, "outputs must be non-NULL");
+    NF_ARG(n >= 1 && n <= kNoallocMaxN, "n = %lld outside 1..%lld", (long long)n, (long long)kNoallocMaxN);
+    NF_TRY(mf_init_attrs());
+    *max_n = kNoallocMaxN;
+    *max_splits = kNoallocMaxSplits;
+    *splits = noalloc_splits(round_up(n, kNodePad));
+    return NF_OK;
+}
+
+extern "C" nf_status nf_selftest_noalloc_flag(int64_t n, float *I, void *stream) {
+    clear_error();
+    NF_ARG(I, "I must be a non-NULL device pointer");
+    NF_ARG(n >= 1 && n <= kNoallocMaxN, "n = %lld outside 1..%lld", (long long)n, (long long)kNoallocMaxN);
+    nf_status st = NF_OK;
+    unsigned char *base = scratch_address(&st);
+    if (!base) return st;
+    cudaStream_t s = as_stream(stream);
+    int *flag = reinterpret_cast<int *>(base + kOffFlag);
+    float *partial = reinterpret_cast<float *>(base + kOffPartial);
+    noalloc_set_flag_kernel<<<1, 1, 0, s>>>(flag, DEV_TIMEOUT);
+    NF_CUDA_TRY(cudaGetLastError());
+    noalloc_reduce_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(partial, 1, n, round_up(n, kNodePad), flag, I);
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
 }

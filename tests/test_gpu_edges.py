@@ -115,3 +115,37 @@ def test_nonfinite_state_is_reported(nf, path):
     with pytest.raises(nf.NFError) as ei:
         bad.check()
     assert ei.value.name == "NF_ERR_NONFINITE"
+
+
+def test_pipe_probe_rates_are_plausible(nf):
+    """The instruction-rate probe behind the pair kernels' roofline: FP32 FMA lanes per
+    clock per SM (scalar and f32x2) and SFU ex2 per clock per SM within the range any
+    recent NVIDIA SM can have, and the implied SM clock within the part's range."""
+    for kind, lo, hi in ((nf.PROBE_FMA, 32.0, 260.0), (nf.PROBE_FMA2, 32.0, 260.0), (nf.PROBE_EX2, 4.0, 64.0)):
+        rate, mhz, ms = nf.nf_probe_pipe(kind, 2000)
+        assert lo <= rate <= hi, (kind, rate)
+        assert 300.0 <= mhz <= 2500.0, (kind, mhz)
+        assert ms > 0.0
+
+
+def test_profiling_ring_keeps_every_step(nf):
+    """With a ring of K event sets, the last K RK4 steps keep their own stage timings; the
+    most recent step's timings equal nf_operator_kernel_ms."""
+    rng = np.random.default_rng(3)
+    n = 5000
+    X = dev(rng.uniform(-1, 1, (n, 3)))
+    q = dev(np.full(n, 1.0 / n))
+    for path in (0, 1):
+        op = nf.Operator(X, q, (1.0, 0.3, 0.5, 0.6), path)
+        op.profile(True, ring=5)
+        u = dev(rng.normal(0.2, 0.3, n)).view(1, -1)
+        for _ in range(3):
+            nf.nf_rk4_advance(op, u, 0.0, 0.05, 1, 20.0, 0.2)
+        nf.nf_rk4_advance(op, u, 0.0, 0.05, 4, 20.0, 0.2)
+        hist = op.kernel_ms_history(5)
+        assert len(hist) == 5 and all(len(h) == 4 and min(h) > 0.0 for h in hist)
+        assert op.kernel_ms() == hist[-1]
+        with pytest.raises(nf.NFError):
+            op.kernel_ms_history(6)
+        op.check()
+        op.close()

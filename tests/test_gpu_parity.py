@@ -355,3 +355,34 @@ def test_symmetric_kernel_several_trajectories(nf, B):
     nf.nf_rk4_advance(op, ub, 0.0, 0.02, 2, dev(beta, torch.float32), dev(theta, torch.float32))
     op.check()
     np.testing.assert_array_equal(ua.cpu().numpy(), ub.cpu().numpy())
+
+
+@pytest.mark.parametrize("n,B", [(1000, 8), (3000, 64), (2100, 65), (1500, 130), (6000, 256)])
+def test_dense_fp32_gemm_several_trajectories(nf, n, B):
+    """Dense FP32 operators with eight or more trajectories run the SIMT FP32 GEMM (tiles
+    of 64 or 128 trajectories, split K on small node sets, ragged trajectory tiles)."""
+    rng = np.random.default_rng(n + 7 * B)
+    X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
+    u = rng.normal(0.3, 0.4, size=(B, n)).astype(np.float32)
+    beta = rng.uniform(10, 40, B).astype(np.float32)
+    theta = rng.uniform(0.1, 0.3, B).astype(np.float32)
+    kern = (1.0, 0.3, 0.5, 0.6)
+    op = nf.Operator(dev(X, torch.float32), dev(q, torch.float32), kern, nf.DENSE_FP32)
+    got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), dev(beta, torch.float32), dev(theta, torch.float32))
+    op.check()
+    sel = np.unique(np.concatenate([[0, B - 1], rng.choice(B, min(B, 6), replace=False)]))
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u[sel]), f32(kern), f32(beta[sel]), f32(theta[sel]))
+    assert rel_l2(got.cpu().numpy()[sel], want) < REL_L2
+    op.close()
+
+
+def test_dense_fp32_gemm_rk4(nf):
+    """RK4 through the GEMM path (24 trajectories) against the oracle."""
+    ns = nodesets.ellipsoid_fibonacci(2500, seed=4)
+    q = np.full(ns.n, 3.0 / ns.n, dtype=np.float32)
+    u0, beta, theta = nodesets.random_bumps(ns, 24, 5, (1.0, 0.8, 0.6))
+    X = ns.nodes.astype(np.float32)
+    got, want = _rk4_pair(nf, X, q, u0.astype(np.float32), W.KERNEL, beta.astype(np.float32),
+                          theta.astype(np.float32), 0.05, 10, nf.DENSE_FP32)
+    assert rel_l2(got, want) < REL_L2
