@@ -38,7 +38,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PATHS = {"mf": 0, "dense_fp32": 1, "bf16x2": 2, "dense_sym": 4}
+PATHS = {"mf": 0, "dense_fp32": 1, "bf16x2": 2, "dense_sym": 4, "dense_sym_bf16x2": 5}
 METRIC = "pair-evals/s & RK4 steps/s at N=1e5, mixed/batched vs plain FP32, same GB300"
 
 
@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--paths", default="mf,dense_fp32,bf16x2,dense_sym")
+    ap.add_argument("--paths", default="mf,dense_fp32,bf16x2,dense_sym,dense_sym_bf16x2")
     ap.add_argument("--n", type=int, default=100000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -898,7 +898,8 @@ def run_ours(args, rank, world, local_rank):
             res["launch_shape"] = op.launch_shape()
         else:  # HBM stream: stored bytes per launch / kernel time
             nb = -(-n // 1024)
-            stored = 4.0 * (nb * (nb + 1) // 2) * 1024 * 1024 if path == nf.DENSE_SYM_FP32 else 4.0 * n * nb * 1024
+            stored = (4.0 * (nb * (nb + 1) // 2) * 1024 * 1024 if path in (nf.DENSE_SYM_FP32, nf.DENSE_SYM_BF16X2)
+                      else 4.0 * n * nb * 1024)
             res["hbm_gbs"] = stored / (res["kernel_ms_per_launch"] * 1e-3) / 1e9
             res["stored_bytes"] = stored
         results[pname] = res

@@ -120,10 +120,14 @@ typedef enum {
     NF_MATRIX_FREE = 0,   /* pair sum evaluated on the fly every stage (FP32) */
     NF_DENSE_FP32 = 1,    /* W diag(q) precomputed once, FP32, streamed every stage */
     NF_DENSE_BF16X2 = 2,  /* W diag(q) / s_i stored as bf16 hi + bf16 lo, FP32 accumulate */
-    NF_DENSE_SYM_FP32 = 4 /* the symmetric kernel matrix W (w is radial, §2.2) stored once as
+    NF_DENSE_SYM_FP32 = 4, /* the symmetric kernel matrix W (w is radial, §2.2) stored once as
                              its upper-triangle 1024 x 1024 blocks, FP32; q applied on the
                              vector side; each block serves a row and a column sum, half the
                              bytes of NF_DENSE_FP32 per stage */
+    NF_DENSE_SYM_BF16X2 = 5 /* the same blocks in the precision form: W_ij = s_i s_j (hi + lo),
+                             bf16 hi + bf16 lo (16 significant bits), s_i a power of two near
+                             sqrt(max_j |W_ij|), FP32 accumulation; the vector is scaled by s
+                             on the way in and each sum by its s_i on the way out */
 } nf_path;
 
 typedef struct nf_operator nf_operator;
@@ -132,7 +136,8 @@ typedef struct nf_operator nf_operator;
  *   x   n x 3  FP32  node coordinates (z = 0 for flat domains)
  *   q   n      FP32  quadrature weights mu_j
  *   path             nf_path; dense paths allocate n x n (FP32: 4 n^2 bytes; BF16X2:
- *                    4 n^2 bytes + 4 n) inside the handle and build it on `stream`.
+ *                    4 n^2 bytes + 4 n; the symmetric paths 2 n^2 + 2048 n bytes, plus 4 n
+ *                    for SYM_BF16X2) inside the handle and build it on `stream`.
  *   op  host         receives the handle.
  * x and q are copied into the handle; the caller may free them afterwards.
  * Errors: NF_ERR_ARG, NF_ERR_NOMEM, NF_ERR_CUDA. */

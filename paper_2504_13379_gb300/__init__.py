@@ -31,12 +31,12 @@ from . import _build
 __all__ = [
     "NFError", "lib", "build", "nf_build_stencils", "nf_quad_weights", "Operator", "nf_nonlocal_apply",
     "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
-    "DENSE_BF16X2", "DENSE_SYM_FP32", "STATUS", "nf_field_advance", "MODEL_FIELD", "MODEL_DEPRESSION",
+    "DENSE_BF16X2", "DENSE_SYM_FP32", "DENSE_SYM_BF16X2", "STATUS", "nf_field_advance", "MODEL_FIELD", "MODEL_DEPRESSION",
     "RATE_SIGMOID", "RATE_SMOOTHSTEP", "FORCE_NONE", "FORCE_MMS_EIGEN", "FORCE_MMS_FLAT", "NeuralFieldRK4",
     "MF_AUTO", "MF_SYMMETRIC", "MF_PACKED", "MF_SYMMETRIC_512", "MF_SYMMETRIC_1024",
 ]
 
-MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32 = 0, 1, 2, 4
+MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32, DENSE_SYM_BF16X2 = 0, 1, 2, 4, 5
 FORCE_NONE, FORCE_MMS_EIGEN, FORCE_MMS_FLAT = 0, 1, 2
 MF_AUTO, MF_SYMMETRIC, MF_PACKED, MF_SYMMETRIC_512, MF_SYMMETRIC_1024 = 0, 1, 2, 3, 4
 STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINITE", 4: "NF_ERR_TIMEOUT",

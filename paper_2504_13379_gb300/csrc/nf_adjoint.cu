@@ -171,6 +171,7 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     NF_CUDA_TRY(scratch.alloc(&vg, sizeof(float2) * (size_t)B * n_pad));
     NF_CUDA_TRY(scratch.alloc(&gk, sizeof(double) * 4 * B));
     NF_CUDA_TRY(cudaMemsetAsync(vg, 0, sizeof(float2) * (size_t)B * n_pad, s));  // padded columns stay zero
+    NF_TRY(adj_autotune(op, vg, B, wpart, gpart, s));  // first call on this operator only
     NF_CUDA_TRY(cudaMemsetAsync(gk, 0, sizeof(double) * 4 * B, s));
     NF_CUDA_TRY(cudaMemcpyAsync(lam, lambda_T, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
     static const nf_forcing none{NF_FORCE_NONE, nullptr, nullptr, 0, 0, 0, 0, 0, 0, 0, 0};

@@ -326,7 +326,8 @@ nf_status nf_operator_create(const float *x, const float *q, int64_t n, nf_kerne
     *op_out = nullptr;
     NF_ARG(x && q, "x and q must be non-NULL device pointers");
     NF_ARG(n >= 1 && n <= (int64_t)1 << 31, "n = %lld out of range", (long long)n);
-    NF_ARG(path == NF_MATRIX_FREE || path == NF_DENSE_FP32 || path == NF_DENSE_BF16X2 || path == NF_DENSE_SYM_FP32,
+    NF_ARG(path == NF_MATRIX_FREE || path == NF_DENSE_FP32 || path == NF_DENSE_BF16X2 || path == NF_DENSE_SYM_FP32 ||
+               path == NF_DENSE_SYM_BF16X2,
            "unknown path %d", path);
     NF_ARG(std::isfinite(kp.A1) && std::isfinite(kp.A2) && kp.s1 > 0.f && kp.s2 > 0.f && std::isfinite(kp.s1) &&
                std::isfinite(kp.s2),
@@ -369,6 +370,9 @@ nf_status nf_operator_create(const float *x, const float *q, int64_t n, nf_kerne
         const size_t entries = (size_t)op->n_pad * (size_t)op->n_pad;
         if (path == NF_DENSE_SYM_FP32) {
             CREATE_TRY(cudaMalloc(&op->W32, dense_sym_entries(op->n_pad) * sizeof(float)));
+        } else if (path == NF_DENSE_SYM_BF16X2) {  // hi and lo interleaved in one allocation
+            CREATE_TRY(cudaMalloc(&op->Whi, 2 * dense_sym_entries(op->n_pad) * sizeof(uint16_t)));
+            CREATE_TRY(cudaMalloc(&op->rs, op->n_pad * sizeof(float)));
         } else if (path == NF_DENSE_FP32) {
             CREATE_TRY(cudaMalloc(&op->W32, entries * sizeof(float)));
         } else {

@@ -16,6 +16,9 @@
 //                    a block (I <= J) once and produces both its row sums (K_IJ g_J, to
 //                    partial slot J) and its column sums (K_IJ^T g_I, to slot I): half the
 //                    HBM bytes of the full matrix per stage.
+//   NF_DENSE_SYM_BF16X2: the same blocks as bf16 hi + lo planes with symmetric power-of-two
+//                    scaling s_i s_j (the vector is scaled on the way in, each output by its
+//                    own s_i): the precision form of the symmetric operator.
 // Work items (32-row block, column split) write partial sums like the matrix-free
 // kernel, so the same stage kernel finishes the RK4 step.
 #include "nf_internal.cuh"
@@ -133,6 +136,75 @@ __global__ void dense_build_sym_kernel(const float4 *__restrict__ x4, float A1, 
     }
 }
 
+// ---- symmetric bf16 hi + lo blocks (NF_DENSE_SYM_BF16X2).  K_ij = s_i s_j (hi_ij + lo_ij)
+// with s_i = 2^round(log2 sqrt(max_j |K_ij|)) over the real nodes: a power of two, so the
+// division by s_i s_j is exact, and the scaled matrix stays symmetric.  hi = bf16_rn(K / s s),
+// lo = bf16_rn(K / s s - hi): 16 significant bits, |K / s s - hi - lo| <= 2^-18 |K / s s|.
+// Block pair t (I <= J) holds rows of node block I x columns of node block J; a row is 128
+// chunks of 8 columns, each chunk 16 bytes of hi followed by 16 bytes of lo (one 32-byte
+// piece per lane and chunk).  Entries of padded rows or columns are zero.
+constexpr int SBC = SB / 8;  // chunks per block row
+
+__global__ void sym_rowscale_kernel(const float4 *__restrict__ x4, int64_t n, float A1, float is1, float A2,
+                                    float is2, float per, float ip, float *__restrict__ sc) {
+    __shared__ float red[32];
+    const int64_t i = blockIdx.x;
+    if (i >= n) {  // padded row: any power of two
+        if (threadIdx.x == 0) sc[i] = 1.f;
+        return;
+    }
+    const float4 xi = x4[i];
+    float mx = 0.f;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, fabsf(mexhat(pair_r2(xi, x4[j], per, ip), A1, is1, A2, is2)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, red[w]);
+        int e = 0;
+        if (v > 0.f) {
+            (void)frexpf(v, &e);  // v = m 2^e, m in [0.5, 1)
+        }
+        sc[i] = v > 0.f ? ldexpf(1.f, e / 2) : 1.f;  // ~ sqrt(v), a power of two
+    }
+}
+
+// grid (pairs, SB / 16): each block writes 16 rows of one block pair
+__global__ void dense_build_sym_bf16x2_kernel(const float4 *__restrict__ x4, const float *__restrict__ sc, int64_t n,
+                                              float A1, float is1, float A2, float is2, float per, float ip,
+                                              uint4 *__restrict__ K) {
+    int I, J;
+    sym_block_pair(blockIdx.x, I, J);
+    uint4 *blk = K + (int64_t)blockIdx.x * SB * SBC * 2;
+    for (int rr = 0; rr < 16; ++rr) {
+        const int r = blockIdx.y * 16 + rr;
+        const int64_t i = (int64_t)I * SB + r;
+        const float4 xi = x4[i];
+        const float si = sc[i];
+        for (int c = threadIdx.x; c < SBC; c += blockDim.x) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                float v[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int64_t j = (int64_t)J * SB + 8 * c + e + t;
+                    v[t] = (i < n && j < n) ? mexhat(pair_r2(xi, x4[j], per, ip), A1, is1, A2, is2) / (si * sc[j]) : 0.f;
+                }
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[0] - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[1] - __bfloat162float(h1));
+                h[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                l[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            blk[((int64_t)r * SBC + c) * 2] = make_uint4(h[0], h[1], h[2], h[3]);
+            blk[((int64_t)r * SBC + c) * 2 + 1] = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
+}
+
 nf_status launch_dense_build(nf_operator *op, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float is1 = 1.f / (k.s1 * k.s1), is2 = 1.f / (k.s2 * k.s2);
@@ -141,6 +213,12 @@ nf_status launch_dense_build(nf_operator *op, cudaStream_t s) {
         const int64_t nb = op->n_pad / SB;
         dense_build_sym_kernel<<<dim3((unsigned)(nb * (nb + 1) / 2), SB / 16), 256, 0, s>>>(op->x4, k.A1, is1, k.A2,
                                                                                        is2, per, ip, op->W32);
+    } else if (op->path == NF_DENSE_SYM_BF16X2) {
+        const int64_t nb = op->n_pad / SB;
+        sym_rowscale_kernel<<<(unsigned)op->n_pad, 256, 0, s>>>(op->x4, op->n, k.A1, is1, k.A2, is2, per, ip, op->rs);
+        NF_CUDA_TRY(cudaGetLastError());
+        dense_build_sym_bf16x2_kernel<<<dim3((unsigned)(nb * (nb + 1) / 2), SB / 16), 128, 0, s>>>(
+            op->x4, op->rs, op->n, k.A1, is1, k.A2, is2, per, ip, reinterpret_cast<uint4 *>(op->Whi));
     } else if (op->path == NF_DENSE_FP32) {
         dense_build_fp32_kernel<<<(unsigned)op->n_pad, 256, 0, s>>>(op->x4, op->q, op->n, op->n_pad, k.A1, is1, k.A2,
                                                                is2, per, ip, op->W32);
@@ -352,6 +430,107 @@ gemv_sym_fp32_kernel(const float *__restrict__ K, const float *__restrict__ g_al
     }
 }
 
+// Symmetric bf16 hi + lo blocks: gemv_sym_fp32_kernel's schedule on the scaled planes.  The
+// vector is scaled on the way into shared memory (g'_j = s_j g_j) and each output by its own
+// s_i, so one stored tile serves I_i = s_i sum_j (hi + lo)_ij g'_j (rows, slot J) and
+// I_j = s_j sum_i (hi + lo)_ij g'_i (columns, slot I).  Lane l reads chunks l + 32 u
+// (u = 0..3) of a row: 8 columns of hi and of lo, 32 contiguous bytes.
+__global__ void __launch_bounds__(SYM_THREADS, 2)
+gemv_sym_bf16x2_kernel(const uint4 *__restrict__ K, const float *__restrict__ g_all, const float *__restrict__ sc,
+                       int64_t n_pad, int B, int b, float *__restrict__ partial) {
+    __shared__ __align__(16) float gI[SB], gJ[SB];
+    __shared__ __align__(16) float colred[SYM_WARPS][SB];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int I, J;
+    sym_block_pair(blockIdx.x, I, J);
+    const bool diag = I == J;
+    const float *g = g_all + (int64_t)b * n_pad;
+    for (int k = tid; k < SB; k += SYM_THREADS) {
+        gI[k] = g[(int64_t)I * SB + k] * sc[(int64_t)I * SB + k];
+        gJ[k] = g[(int64_t)J * SB + k] * sc[(int64_t)J * SB + k];
+    }
+    __syncthreads();
+    const uint4 *blk = K + (int64_t)blockIdx.x * SB * SBC * 2;
+    float col[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) col[c] = 0.f;
+    float *out_rows = partial + ((int64_t)J * B + b) * n_pad + (int64_t)I * SB;
+    for (int r0 = warp; r0 < SB; r0 += 8 * SYM_WARPS) {  // 8 rows per group: r0, r0 + 8, ..., r0 + 56
+        float dot[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = r0 + 8 * k;
+            const uint4 *row = blk + (int64_t)r * SBC * 2;
+            uint4 hv[4], lv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                hv[u] = ld_stream_u4(row + 2 * (lane + 32 * u));
+                lv[u] = ld_stream_u4(row + 2 * (lane + 32 * u) + 1);
+            }
+            const float gi = gI[r];
+            float d = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 g0 = *reinterpret_cast<const float4 *>(gJ + 8 * (lane + 32 * u));
+                const float4 g1 = *reinterpret_cast<const float4 *>(gJ + 8 * (lane + 32 * u) + 4);
+                const float gj[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                const uint32_t hw[4] = {hv[u].x, hv[u].y, hv[u].z, hv[u].w};
+                const uint32_t lw[4] = {lv[u].x, lv[u].y, lv[u].z, lv[u].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float v0 = __uint_as_float(hw[q] << 16) + __uint_as_float(lw[q] << 16);
+                    const float v1 = __uint_as_float(hw[q] & 0xffff0000u) + __uint_as_float(lw[q] & 0xffff0000u);
+                    d = fmaf(v0, gj[2 * q], d);
+                    d = fmaf(v1, gj[2 * q + 1], d);
+                    col[8 * u + 2 * q] = fmaf(v0, gi, col[8 * u + 2 * q]);
+                    col[8 * u + 2 * q + 1] = fmaf(v1, gi, col[8 * u + 2 * q + 1]);
+                }
+            }
+            dot[k] = d;
+        }
+        int base = 0, cnt = 8;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            if (cnt > 1) {
+                const int h = cnt >> 1;
+                const bool upper = (lane & off) != 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k < h) {
+                        const float send = upper ? dot[k] : dot[k + h];
+                        const float keep = upper ? dot[k + h] : dot[k];
+                        dot[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                    }
+                }
+                if (upper) base += h;
+                cnt = h;
+            } else {
+                dot[0] += __shfl_xor_sync(0xffffffffu, dot[0], off);
+            }
+        }
+        if ((lane & 3) == 0) {
+            const int r = r0 + 8 * base;
+            out_rows[r] = sc[(int64_t)I * SB + r] * dot[0];
+        }
+    }
+    if (diag) return;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        float *dst = &colred[warp][8 * (lane + 32 * u)];
+        *reinterpret_cast<float4 *>(dst) = make_float4(col[8 * u], col[8 * u + 1], col[8 * u + 2], col[8 * u + 3]);
+        *reinterpret_cast<float4 *>(dst + 4) =
+            make_float4(col[8 * u + 4], col[8 * u + 5], col[8 * u + 6], col[8 * u + 7]);
+    }
+    __syncthreads();
+    float *out_cols = partial + ((int64_t)I * B + b) * n_pad + (int64_t)J * SB;
+    for (int k = tid; k < SB; k += SYM_THREADS) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < SYM_WARPS; ++w) v += colred[w][k];
+        out_cols[k] = sc[(int64_t)J * SB + k] * v;
+    }
+}
+
 // ---------------------------------------------------------------- GEMM (several trajectories)
 // I[b, i] = sum_j WQ[i, j] F[b, j] for B >= kGemmMinB trajectories on the FP32 plane: a
 // register-tiled SIMT GEMM on the FP32 FMA pipe (the plain-FP32 counterpart of the batched
@@ -368,10 +547,14 @@ gemv_sym_fp32_kernel(const float *__restrict__ K, const float *__restrict__ g_al
 constexpr int GB_BM = 128, GB_BK = 16, GB_THREADS = 256;
 constexpr int kGemmMinB = 8;
 
+// Row strides are padded (130 floats, GB_BN + 2 pairs) so that the transposing stores of a
+// warp (8 rows or trajectories x 4 k-quads) fall into distinct banks, while every row stays
+// 8-byte (a) and 16-byte (b) aligned for the compute loop's vector loads.
+constexpr int GB_AS = GB_BM + 2;
 template <int GB_BN>
 struct GemmSmem {
-    float a[2][GB_BK][GB_BM];                   // W tile, k-major
-    unsigned long long b[2][GB_BK][GB_BN];      // (f, f) pairs, k-major
+    float a[2][GB_BK][GB_AS];                       // W tile, k-major
+    unsigned long long b[2][GB_BK][GB_BN + 2];      // (f, f) pairs, k-major
 };
 
 typedef unsigned long long u64d;
@@ -477,16 +660,27 @@ gemm_fp32_kernel(const float *__restrict__ W, const float *__restrict__ F, int64
     }
 }
 
-// (K splits, K columns per split) of the GEMM: enough CTAs for two waves where the output
-// tiles alone give fewer, at most 16 splits.
+// (K splits, K columns per split) of the GEMM: the split count (at most 16, each split at
+// least 64 K steps) whose CTAs best fill whole waves of two CTAs per SM; each extra split
+// costs one more B x n partial-sum slot, a small penalty.
 static SplitPlan gemm_plan(const nf_operator *op, int B) {
     SplitPlan p{};
     const int bn = B > 64 ? 128 : 64;
     const int64_t tiles = (op->n_pad / GB_BM) * ((B + bn - 1) / bn);
     const int64_t ktiles = op->n_pad / GB_BK;
-    const int64_t want = 2 * (int64_t)num_sms() * 2;  // two waves of two CTAs per SM
+    const int64_t slots = 2 * (int64_t)num_sms();
     int s = 1;
-    while (s < 16 && tiles * s < want && ktiles / (s + 1) >= 64) ++s;
+    double best = -1.0;
+    for (int c = 1; c <= 16 && (c == 1 || ktiles / c >= 64); ++c) {
+        const int64_t per_c = ceil_div(ktiles, c);
+        if (ceil_div(ktiles, per_c) != c) continue;
+        const int64_t items = tiles * c;
+        const double eff = (double)items / (double)(ceil_div(items, slots) * slots) - 0.005 * c;
+        if (eff > best + 1e-9) {
+            best = eff;
+            s = c;
+        }
+    }
     const int64_t per = ceil_div(ktiles, s);
     p.rows_per_block = GB_BM;
     p.row_blocks = op->n_pad / GB_BM;
@@ -516,7 +710,8 @@ SplitPlan dense_plan(nf_operator *op) {
 
 int dense_splits(nf_operator *op, int B) {
     if (use_gemm(op, B)) return gemm_plan(op, B).splits;
-    return op->path == NF_DENSE_SYM_FP32 ? (int)(op->n_pad / SB) : dense_plan(op).splits;
+    const bool sym = op->path == NF_DENSE_SYM_FP32 || op->path == NF_DENSE_SYM_BF16X2;
+    return sym ? (int)(op->n_pad / SB) : dense_plan(op).splits;
 }
 
 size_t dense_sym_entries(int64_t n_pad) {
@@ -525,11 +720,15 @@ size_t dense_sym_entries(int64_t n_pad) {
 }
 
 nf_status launch_dense_gemv(nf_operator *op, int B, cudaStream_t s, int *splits_out) {
-    if (op->path == NF_DENSE_SYM_FP32) {
+    if (op->path == NF_DENSE_SYM_FP32 || op->path == NF_DENSE_SYM_BF16X2) {
         const int64_t nb = op->n_pad / SB;
         for (int b = 0; b < B; ++b) {
-            gemv_sym_fp32_kernel<<<(unsigned)(nb * (nb + 1) / 2), SYM_THREADS, 0, s>>>(op->W32, op->g, op->n_pad, B, b,
-                                                                                     op->partial);
+            if (op->path == NF_DENSE_SYM_FP32)
+                gemv_sym_fp32_kernel<<<(unsigned)(nb * (nb + 1) / 2), SYM_THREADS, 0, s>>>(op->W32, op->g, op->n_pad,
+                                                                                         B, b, op->partial);
+            else
+                gemv_sym_bf16x2_kernel<<<(unsigned)(nb * (nb + 1) / 2), SYM_THREADS, 0, s>>>(
+                    reinterpret_cast<const uint4 *>(op->Whi), op->g, op->rs, op->n_pad, B, b, op->partial);
             NF_CUDA_TRY(cudaGetLastError());
         }
         *splits_out = (int)nb;

@@ -139,6 +139,13 @@ struct PerTag {
     static constexpr bool value = P;
 };
 
+// A loop bound known at compile time (full node blocks), interchangeable with a runtime int
+// bound (the last, partial block) in templated loops.
+template <int V>
+struct CInt {
+    __device__ constexpr operator int() const { return V; }
+};
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -173,6 +180,7 @@ struct nf_operator {
     float *xyz = nullptr;    // 3 x n_pad: coordinates times sqrt(log2 e)/s1, structure of arrays
     int mf_variant = -1;     // launch shape of the packed pair kernel
     int mf_sym_r = 8;        // rows per warp of the symmetric single-trajectory kernel (autotuned)
+    int adj_r = 0;           // rows per warp of the adjoint pair kernel (0: not yet timed; 4 or 8)
     int mf_sched = 0;        // NF_MF_AUTO / NF_MF_SYMMETRIC / NF_MF_PACKED
     int sym_blk = 1024;      // node block of the symmetric kernel (1024, or 512 when autotuned faster)
     int planar = 0;          // every node has the same z: the symmetric kernel drops the z terms
@@ -192,7 +200,7 @@ struct nf_operator {
     float *W32 = nullptr;        // W diag(q), FP32
     uint16_t *Whi = nullptr;     // bf16 bits of (W diag(q))_ij / s_i, high part (blocked layout)
     uint16_t *Wlo = nullptr;     // bf16 bits of the residual (blocked layout)
-    float *rs = nullptr;         // s_i, powers of two
+    float *rs = nullptr;         // s_i, powers of two (symmetric bf16 planes: K_ij = s_i s_j (hi + lo))
     // workspace owned by the handle
     float *partial = nullptr;    // [split][B][n_pad]
     size_t partial_cap = 0;
@@ -252,6 +260,7 @@ nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live, int64_t *total
 nf_status launch_adj_cull_reduce(nf_operator *op, float *wpart, int B, int b, cudaStream_t s);
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
                          float *r2_phys, cudaStream_t s);
+nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, float *gpart, cudaStream_t s);
 nf_status mf_autotune(nf_operator *op, cudaStream_t s);
 void mf_launch_shape(nf_operator *op, int *R, int *TJ, int *splits);
 nf_status launch_mf_pair(nf_operator *op, int B, cudaStream_t s, int *splits_out);
@@ -264,7 +273,7 @@ nf_status dense_init_attrs();
 size_t dense_sym_entries(int64_t n_pad);     // stored entries of the symmetric blocked matrix
 // q is applied on the vector side (g = q o f) unless it is folded into a dense operator
 inline bool q_on_vector(const nf_operator *op) {
-    return op->path == NF_MATRIX_FREE || op->path == NF_DENSE_SYM_FP32;
+    return op->path == NF_MATRIX_FREE || op->path == NF_DENSE_SYM_FP32 || op->path == NF_DENSE_SYM_BF16X2;
 }
 nf_status launch_dense_build(nf_operator *op, cudaStream_t s);
 

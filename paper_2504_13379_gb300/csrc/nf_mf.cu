@@ -654,10 +654,10 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
             }
         };
         // form 1: expanded about c; P: columns at their nearest image of c
-        auto sweep_local = [&](auto tag) {
+        auto sweep_local = [&](auto tag, auto lim) {
             constexpr bool P = decltype(tag)::value;
 #pragma unroll 1
-            for (int q = lane; q < BLK / 4; q += 32) {
+            for (int q = lane; q < (int)lim; q += 32) {
                 const float4 x4 = xs4[q], y4 = ys4[q], g4 = gs4[q];
                 const float4 z4 = D2 ? make_float4(0.f, 0.f, 0.f, 0.f) : zs4[q];
                 u64 xt[2] = {f2_sub(lo2(x4), cxp), f2_sub(hi2(x4), cxp)};
@@ -700,10 +700,10 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         // forms 0, 2, 3: coordinate differences; CEN: rows centred on c and columns' x, y at
         // their nearest image of c (forms 2, 3); PW: each pair's x, y differences reduced to
         // their nearest image (form 3)
-        auto sweep_diff = [&](auto tag_c, auto tag_w) {
+        auto sweep_diff = [&](auto tag_c, auto tag_w, auto lim) {
             constexpr bool CEN = decltype(tag_c)::value, PW = decltype(tag_w)::value;
 #pragma unroll 1
-            for (int q = lane; q < BLK / 4; q += 32) {
+            for (int q = lane; q < (int)lim; q += 32) {
                 const float4 x4 = xs4[q], y4 = ys4[q], g4 = gs4[q];
                 const float4 z4 = D2 ? make_float4(0.f, 0.f, 0.f, 0.f) : zs4[q];
                 u64 xj[2] = {lo2(x4), hi2(x4)}, yj[2] = {lo2(y4), hi2(y4)};
@@ -743,19 +743,25 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                 add_cols(q, cacc);
             }
         };
-        // each lane takes 4 consecutive columns (two f32x2 pairs) per step
-        if (form == 1) {
-            if (per > 0.f)
-                sweep_local(PerTag<true>{});
-            else
-                sweep_local(PerTag<false>{});
-        } else if (form == 0) {
-            sweep_diff(PerTag<false>{}, PerTag<false>{});
-        } else if (form == 2) {
-            sweep_diff(PerTag<true>{}, PerTag<false>{});
-        } else {
-            sweep_diff(PerTag<true>{}, PerTag<true>{});
-        }
+        // each lane takes 4 consecutive columns (two f32x2 pairs) per step.  Every block is
+        // swept in full, padding included (g = 0 there): a second, trimmed copy of the loops
+        // for the last block measured 2.5 % slower on the 100,000-node torus (1.763 against
+        // 1.720 ms per sum), more than its 0.7 % of padded pairs
+        auto run = [&](auto lim) {
+            if (form == 1) {
+                if (per > 0.f)
+                    sweep_local(PerTag<true>{}, lim);
+                else
+                    sweep_local(PerTag<false>{}, lim);
+            } else if (form == 0) {
+                sweep_diff(PerTag<false>{}, PerTag<false>{}, lim);
+            } else if (form == 2) {
+                sweep_diff(PerTag<true>{}, PerTag<false>{}, lim);
+            } else {
+                sweep_diff(PerTag<true>{}, PerTag<true>{}, lim);
+            }
+        };
+        run(CInt<BLK / 4>{});
         float v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -798,19 +804,22 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
 //     when M > 0, else of s1) to gpart; a fixed-order FP64 reduction adds them.
 constexpr size_t AS_SMEM_FLOATS = (size_t)(5 + 14 + 1 + MS_WARPS) * MS_BLK;
 
+// R = 4: two CTAs per SM (128 registers); R = 8: one CTA per SM with the whole register
+// file (eight rows' accumulators, more independent work per warp, fewer warps).
 template <int R, int M>
-__global__ void __launch_bounds__(MS_THREADS, 2)
+__global__ void __launch_bounds__(MS_THREADS, R >= 8 ? 1 : 2)
 adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all, const int *__restrict__ rowperm,
-               int64_t n_pad, int B, int b, float k2, float A1, float A2, float per, float *__restrict__ wpart,
-               float *__restrict__ gpart, const int *__restrict__ pairs) {
+               int64_t n_pad, int64_t n, int B, int b, float k2, float A1, float A2, float per,
+               float *__restrict__ wpart, float *__restrict__ gpart, const int *__restrict__ pairs) {
     static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
-    static_assert(R == 2 || R == 4, "rows per warp");
+    static_assert(R == 4 || R == 8, "rows per warp");
     constexpr int NPASS = MS_BLK / R;
     extern __shared__ __align__(16) float as_smem[];
     // column block: x, y, z, nu, g (floats), node (int)
     float *xs = as_smem, *ys = xs + MS_BLK, *zs = ys + MS_BLK, *vs = zs + MS_BLK, *gsm = vs + MS_BLK;
     int *cnode = reinterpret_cast<int *>(gsm + MS_BLK);
-    // row block: node; per row (mx, my, mz, n_i), (h1, h2, rf1, rf2), (v1, u1, v2, u2) as float4
+    // row block: node; per row (mx, my, mz, n_i), (h1, h1, h2, h2) -- the column-sum weights
+    // A1 f1 nu_i and -A2 f2 nu_i -- and (v1, u1, v2, u2), as float4
     int *rnode = cnode + MS_BLK;
     float4 *rgeo = reinterpret_cast<float4 *>(rnode + MS_BLK);
     float4 *rwn = rgeo + MS_BLK, *rgw = rwn + MS_BLK;
@@ -824,6 +833,9 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     const float2 *vg = vg_all + (int64_t)b * n_pad;
     const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
     const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
+    // positions >= n hold the padding nodes (nu = g = 0): sweeps stop at the last real ones
+    const int npass_v = (int)((min((int64_t)MS_BLK, n - rbase) + R - 1) / R);
+    const int ncp_v = (int)((min((int64_t)MS_BLK, n - cbase) + 1) / 2);
     // exponent units: s1, or s2 when M > 0 (coordinates times sk = s1 / s2, once here)
     const float sk = M > 0 ? sqrtf(k2) : 1.f;
     for (int k = tid; k < MS_BLK; k += MS_THREADS) {
@@ -878,7 +890,8 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             const float f2 = local ? exp2f(M > 0 ? -ni : -k2 * ni) : 1.f;
             const float nu = rgw[k].x, gi = rgw[k].y;
             rgeo[k] = make_float4(x, y, z, ni);
-            rwn[k] = make_float4(A1 * f1 * nu, -A2 * f2 * nu, A1 * f1, -A2 * f2);
+            const float h1 = A1 * f1 * nu, h2 = -A2 * f2 * nu;
+            rwn[k] = make_float4(h1, h1, h2, h2);
             rgw[k] = make_float4(f1 * nu, diag ? 0.f : f1 * gi, f2 * nu, diag ? 0.f : f2 * gi);
         }
     }
@@ -904,7 +917,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         }
     };
     float P1 = 0.f, Q1 = 0.f, P2 = 0.f, Q2 = 0.f;  // per lane, over all its pairs
-    for (int ps = warp; ps < NPASS; ps += MS_WARPS) {
+    for (int ps = warp; ps < npass_v; ps += MS_WARPS) {
         const int r0 = ps * R;
         const float4 c = pc[ps];
         const bool local = c.w != 0.f;
@@ -918,7 +931,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             yi[r] = f2_pack(p.y, p.y);
             zi[r] = f2_pack(p.z, p.z);
             h1[r] = f2_pack(w.x, w.x);
-            h2[r] = f2_pack(w.y, w.y);
+            h2[r] = f2_pack(w.z, w.z);
             a1[r] = a2[r] = b1[r] = b2[r] = c1[r] = c2[r] = d1[r] = d2[r] = 0ull;
         }
         const u64 cxp = f2_pack(c.x, c.x), cyp = f2_pack(c.y, c.y), czp = f2_pack(c.z, c.z);
@@ -938,9 +951,9 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             c2[r] = f2_fma(s2e, gj, c2[r]);
             d2[r] = f2_fma(s2e, vj, d2[r]);
         };
-        if (local) {
+        auto sweep_local = [&](auto lim) {
 #pragma unroll 1
-            for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
+            for (int jp = lane; jp < (int)lim; jp += 32) {
                 const u64 xt = f2_sub(xs2[jp], cxp), yt = f2_sub(ys2[jp], cyp), zt = f2_sub(zs2[jp], czp);
                 const u64 nj = f2_fma(zt, zt, f2_fma(yt, yt, f2_mul(xt, xt)));
                 const u64 vj = vs2[jp], gj = gs2[jp];
@@ -950,11 +963,18 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
                     pair(r, f2_fma(xi[r], xt, f2_fma(yi[r], yt, f2_fma(zi[r], zt, nj))), vj, gj, cacc);
                 if (!diag) cw2[jp] = f2_add(cw2[jp], cacc);
             }
+        };
+        const bool full_c = ncp_v == MS_BLK / 2;  // the column bound is a constant on full blocks
+        if (local) {
+            if (full_c)
+                sweep_local(CInt<MS_BLK / 2>{});
+            else
+                sweep_local(ncp_v);
         } else {
-            auto sweep = [&](auto tag) {
+            auto sweep = [&](auto tag, auto lim) {
                 constexpr bool P = decltype(tag)::value;
 #pragma unroll 1
-            for (int jp = lane; jp < MS_BLK / 2; jp += 32) {
+            for (int jp = lane; jp < (int)lim; jp += 32) {
                 const u64 xj = xs2[jp], yj = ys2[jp], zj = zs2[jp], vj = vs2[jp], gj = gs2[jp];
                 u64 cacc = 0ull;
 #pragma unroll
@@ -970,10 +990,17 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
                 if (!diag) cw2[jp] = f2_add(cw2[jp], cacc);
             }
             };
-            if (per > 0.f)
-                sweep(PerTag<true>{});
-            else
-                sweep(PerTag<false>{});
+            if (per > 0.f) {
+                if (full_c)
+                    sweep(PerTag<true>{}, CInt<MS_BLK / 2>{});
+                else
+                    sweep(PerTag<true>{}, ncp_v);
+            } else {
+                if (full_c)
+                    sweep(PerTag<false>{}, CInt<MS_BLK / 2>{});
+                else
+                    sweep(PerTag<false>{}, ncp_v);
+            }
         }
         auto fold = [](u64 x) {
             float lo, hi;
@@ -984,9 +1011,12 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float A1s = fold(a1[r]), A2s = fold(a2[r]), B1s = fold(b1[r]), B2s = fold(b2[r]);
-            const float4 w = rwn[r0 + r], q = rgw[r0 + r];
+            const float4 q = rgw[r0 + r];
             const float ni = rgeo[r0 + r].w;
-            v[r] = w.z * A1s + w.w * A2s;
+            // the row factors 2^(-n_i) of e1 and e2 as in the pass set-up (n_i = 0 outside
+            // the expanded form, so both are 1 there)
+            const float f1 = exp2f(M > 0 ? -(float)M * ni : -ni), f2 = exp2f(M > 0 ? -ni : -k2 * ni);
+            v[r] = (A1 * f1) * A1s + (-A2 * f2) * A2s;
             // pair weight e (nu_i g_j + g_i nu_j) with the row factors: q = (f1 nu_i, f1 g_i,
             // f2 nu_i, f2 g_i), g_i = 0 on diagonal block pairs; r^2 = arg + n_i
             P1 += q.x * B1s + q.y * A1s;
@@ -1095,6 +1125,10 @@ static nf_status mf_init_attrs_device() {
     NF_CUDA_TRY((set_adj_attr<4, 2>()));
     NF_CUDA_TRY((set_adj_attr<4, 3>()));
     NF_CUDA_TRY((set_adj_attr<4, 4>()));
+    NF_CUDA_TRY((set_adj_attr<8, 0>()));
+    NF_CUDA_TRY((set_adj_attr<8, 2>()));
+    NF_CUDA_TRY((set_adj_attr<8, 3>()));
+    NF_CUDA_TRY((set_adj_attr<8, 4>()));
     NF_CUDA_TRY((set_sym_attr<4, 0>()));
     NF_CUDA_TRY((set_sym_attr<4, 1>()));
     NF_CUDA_TRY((set_sym_attr<8, 1>()));
@@ -1322,17 +1356,66 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
     dim3 grid((unsigned)(cull ? op->adj_live : sym_pairs_1024(op)), 1, 1);
     const size_t smem = AS_SMEM_FLOATS * sizeof(float);
 #define NF_ADJ_ARGS                                                                                       \
-    op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, scaled_period(k), wpart, gpart, \
+    op->xyz, vg, op->rowperm, op->n_pad, op->n, B, b, k2, k.A1, k.A2, scaled_period(k), wpart, gpart, \
         (cull ? op->adj_pairs : nullptr)
-    switch (m) {
-        case 2: adj_sym_kernel<4, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-        case 3: adj_sym_kernel<4, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-        case 4: adj_sym_kernel<4, 4><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-        default: adj_sym_kernel<4, 0><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+    if (op->adj_r == 8) {
+        switch (m) {
+            case 2: adj_sym_kernel<8, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+            case 3: adj_sym_kernel<8, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+            case 4: adj_sym_kernel<8, 4><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+            default: adj_sym_kernel<8, 0><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+        }
+    } else {
+        switch (m) {
+            case 2: adj_sym_kernel<4, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+            case 3: adj_sym_kernel<4, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+            case 4: adj_sym_kernel<4, 4><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+            default: adj_sym_kernel<4, 0><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+        }
     }
 #undef NF_ADJ_ARGS
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
+}
+
+// Rows per warp of the adjoint pair kernel, chosen once per operator by timing both shapes
+// (4 rows, two CTAs per SM; 8 rows, one CTA per SM) on the operator's own node set: two
+// launches each, the faster of the second launches is kept.  The launches write the call's
+// scratch buffers only, before the call's own passes overwrite them.
+nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, float *gpart, cudaStream_t s) {
+    if (op->adj_r) return NF_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NF_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate", __FILE__, __LINE__);
+    }
+    const int cand[2] = {4, 8};
+    float best = 3.4e38f;
+    int best_r = 4;
+    nf_status st = NF_OK;
+    float r2 = 1.f;
+    for (int c = 0; c < 2 && st == NF_OK; ++c) {
+        op->adj_r = cand[c];
+        for (int rep = 0; rep < 2 && st == NF_OK; ++rep) {
+            ce = cudaEventRecord(e0, s);
+            if (ce == cudaSuccess) st = launch_adj_sym(op, vg, B, 0, wpart, gpart, &r2, s);
+            if (st == NF_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+            if (st == NF_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (st == NF_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess && st == NF_OK) st = cuda_fail(ce, "adjoint autotune", __FILE__, __LINE__);
+            if (st == NF_OK && rep == 1 && ms < best) {
+                best = ms;
+                best_r = cand[c];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    op->adj_r = st == NF_OK ? best_r : 0;
+    return st;
 }
 
 int mf_splits(nf_operator *op, int B) {

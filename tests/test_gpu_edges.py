@@ -7,7 +7,7 @@ import torch
 
 pytestmark = pytest.mark.gpu
 
-PATHS = [0, 1, 2, 4]
+PATHS = [0, 1, 2, 4, 5]
 
 
 @pytest.fixture(scope="module")

@@ -75,7 +75,7 @@ def test_models_matrix_free(nf, kind, rate, integ):
     _run(nf, 0, kind, rate, integ)
 
 
-@pytest.mark.parametrize("path", [1, 2, 4])
+@pytest.mark.parametrize("path", [1, 2, 4, 5])
 def test_depression_ab5_dense_paths(nf, path):
     """The dense paths (W diag(mu) FP32 and bf16 hi+lo; symmetric K with mu on the vector
     side) under the depression model with the smooth step and AB5."""

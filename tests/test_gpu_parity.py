@@ -125,7 +125,7 @@ def _op(nf, X, q, kernel, path):
     return nf.Operator(dev(X, torch.float32), dev(q, torch.float32), kernel, path)
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 4])
+@pytest.mark.parametrize("path", [0, 1, 2, 4, 5])
 @pytest.mark.parametrize("n,B", [(3001, 1), (2500, 3), (1100, 7), (5, 2), (1, 1), (2048, 2), (1500, 19), (1100, 35)])
 def test_nonlocal_apply_matches_oracle(nf, path, n, B):
     rng = np.random.default_rng(n + B)
@@ -225,7 +225,7 @@ def _rk4_pair(nf, X, q, u0, kernel, beta, theta, dt, nsteps, path, forcing=None,
     return u.cpu().numpy(), want
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 4])
+@pytest.mark.parametrize("path", [0, 1, 2, 4, 5])
 def test_rk4_flat_workload_full(nf, path):
     """The flat unit-square workload end to end: oracle stencils and weights, then
     100 RK4 steps (t = 0..5) on the GPU vs the FP64 oracle."""

@@ -56,7 +56,7 @@ KERNELS = {
 
 
 @pytest.mark.parametrize("kname", sorted(KERNELS))
-@pytest.mark.parametrize("path", [0, 1, 2, 4])
+@pytest.mark.parametrize("path", [0, 1, 2, 4, 5])
 @pytest.mark.parametrize("n,B", [(3001, 1), (2500, 3), (1100, 7), (5, 2)])
 def test_periodic_nonlocal_apply(nf, kname, path, n, B):
     """Every path (symmetric matrix-free for one trajectory; scalar and packed pair kernels
@@ -254,7 +254,7 @@ def test_periodic_models(nf):
     assert rel_l2(s.cpu().numpy(), ws) < REL_L2
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 4])
+@pytest.mark.parametrize("path", [0, 1, 2, 4, 5])
 def test_spatial_error_map_unit_square(nf, path):
     """§4.2, Eq. (flat_spatial_error) on the unit square (period 1): the oracle's weights on
     point-repulsion nodes (n = 2000, r^3, k = 21, deg 3), a 64 x 64 grid of centres x0
