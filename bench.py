@@ -355,7 +355,7 @@ def run_batched(args, dev, steps, pipes=None):
                      "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak},
                      "tensor": {"achieved": tfl, "peak": tc_peak, "unit": "TFLOP/s", "frac": tfl / tc_peak,
                                 "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (kernel inside a long step)"}},
-        "gpu_launches_per_step": 4}
+        "gpu_launches_per_step": 4, "tuning": grp.tuning()}
     if args.accuracy:
         out["tc_bf16x3"]["rel_l2_vs_oracle"] = batched_accuracy(
             wls, [x.cpu().numpy() for x in xs], [q.cpu().numpy() for q in qs], u0.cpu().numpy(),

@@ -147,19 +147,34 @@ NF_API nf_status nf_operator_create(const float *x, const float *q, int64_t n, n
 NF_API nf_status nf_operator_destroy(nf_operator *op);
 
 /* Batched tensor-core operator over several node sets (the batching form of Eq. (2.9)):
- * ops[g] (count <= 4) are NF_DENSE_BF16X2 operators with n_g >= 64 nodes, advanced with
- * B_per_op[g] (1..256) trajectories each.  Per RK4 stage one persistent tcgen05 GEMM
- * computes, for every group, D = Whi Fhi + Whi Flo + Wlo Fhi (bf16 inputs, FP32 tensor-
- * memory accumulation; F = f(U) split into bf16 hi + lo) and its epilogue performs the
- * stage update.  A grouped operator takes, in nf_nonlocal_apply / nf_rk4_advance, B = the
- * total number of trajectories and u, I as the concatenation over g (in ops order) of the
- * B_g x n_g blocks; beta, theta likewise concatenated; forcing must be NONE; ckpt holds
- * (nsteps / C + 1) copies of the concatenated state.  The members must outlive the group,
- * which does not own them (nf_operator_destroy on the group frees only its own buffers).
- * Errors: NF_ERR_ARG, NF_ERR_NOMEM, NF_ERR_CUDA, NF_ERR_UNSUPPORTED (no two-SM cluster of
- * the kernel fits on the device). */
+ * ops[g] (count <= 8) are NF_DENSE_BF16X2 operators with n_g >= 64 nodes, advanced with
+ * B_per_op[g] trajectories each.  Per RK4 stage one persistent tcgen05 GEMM computes, for
+ * every group, D = Whi Fhi + Whi Flo + Wlo Fhi (bf16 inputs, FP32 tensor-memory
+ * accumulation; F = f(U) split into bf16 hi + lo) and its epilogue performs the stage
+ * update.  The GEMM works on sub-groups of at most 256 trajectories of one node set (its
+ * MMA width); one launch holds at most 8 sub-groups, so sum_g ceil(B_g / 256) <= 8
+ * (otherwise NF_ERR_UNSUPPORTED).  At creation the call times a small set of launch
+ * configurations on the device (ring depth, whether members of 128 or more trajectories are
+ * cut in two, the weight of the MMA term in the tile schedule) and keeps the fastest; see
+ * nf_operator_group_tuning.  Results do not depend on that choice.  A grouped operator
+ * takes, in nf_nonlocal_apply / nf_rk4_advance, B = the total number of trajectories and
+ * u, I as the concatenation over g (in ops order) of the B_g x n_g blocks; beta, theta
+ * likewise concatenated; forcing must be NONE; ckpt holds (nsteps / C + 1) copies of the
+ * concatenated state.  The members must outlive the group, which does not own them
+ * (nf_operator_destroy on the group frees only its own buffers).  Synchronises `stream`.
+ * Errors: NF_ERR_ARG, NF_ERR_NOMEM, NF_ERR_CUDA, NF_ERR_UNSUPPORTED (more than 8 sub-groups;
+ * no two-SM cluster of the kernel fits on the device), NF_ERR_TIMEOUT (a bounded wait gave
+ * up during the timing launches). */
 NF_API nf_status nf_operator_group(nf_operator *const *ops, const int *B_per_op, int count, void *stream,
                                    nf_operator **grouped);
+
+/* Launch configuration the autotuner of nf_operator_group chose (no paper counterpart),
+ * host outputs: ring depth (64 KB shared-memory slots in flight per CTA: 2 or 3), the
+ * number of pieces a member of 128 or more trajectories was cut into (1 or 2), the weight of
+ * the MMA term in the longest-processing-time tile costs, the sub-groups of one launch, and
+ * the chosen configuration's time per nonlocal-sum launch (ms).  Errors: NF_ERR_ARG. */
+NF_API nf_status nf_operator_group_tuning(nf_operator *op, int *ring_depth, int *traj_split, double *lpt_coef,
+                                          int *subgroups, float *ms);
 
 /* Synchronise `stream` and report device-side failures recorded on the operator:
  * NF_ERR_TIMEOUT when a bounded wait in a kernel gave up; NF_ERR_NONFINITE when a step of

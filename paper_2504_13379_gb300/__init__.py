@@ -49,7 +49,7 @@ EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights"
            "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout",
            "nf_operator_mf_schedule", "nf_operator_mf_cull", "nf_field_advance", "nf_noalloc_status",
            "nf_noalloc_limits", "nf_selftest_noalloc_flag", "nf_operator_kernel_ms_history",
-           "nf_probe_pipe"]
+           "nf_probe_pipe", "nf_operator_group_tuning"]
 
 
 class NFError(RuntimeError):
@@ -102,6 +102,8 @@ def lib(path: str | None = None):
     L.nf_operator_create.argtypes = [_vp, _vp, _i64, _Kernel, C.c_int, _vp, C.POINTER(_vp)]
     L.nf_operator_destroy.argtypes = [_vp]
     L.nf_operator_group.argtypes = [C.POINTER(_vp), C.POINTER(C.c_int), C.c_int, _vp, C.POINTER(_vp)]
+    L.nf_operator_group_tuning.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_int), C.POINTER(C.c_float)]
     L.nf_operator_check.argtypes = [_vp, _vp]
     L.nf_operator_profile.argtypes = [_vp, C.c_int]
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
@@ -300,6 +302,14 @@ class GroupedOperator(Operator):
         h = C.c_void_p()
         _check(lib().nf_operator_group(arr, bs, len(self.members), _stream(), C.byref(h)))
         self._h = h
+
+    def tuning(self):
+        """The launch configuration the autotuner chose at creation."""
+        d, sp, c, g, ms = C.c_int(), C.c_int(), C.c_double(), C.c_int(), C.c_float()
+        _check(lib().nf_operator_group_tuning(self.handle, C.byref(d), C.byref(sp), C.byref(c), C.byref(g),
+                                              C.byref(ms)))
+        return {"ring_depth": d.value, "traj_split": sp.value, "lpt_coef": c.value, "subgroups": g.value,
+                "ms_per_launch": ms.value}
 
     def split(self, flat: torch.Tensor):
         """View a concatenated state as the list of per-member (B_g x n_g) blocks."""

@@ -49,9 +49,10 @@ namespace nfi {
 constexpr int TC_M = 128;          // rows per CTA
 constexpr int TC_PAIR_M = 256;     // rows per cluster pair (MMA M)
 constexpr int TC_BK = 64;          // K elements per stage: 128-byte rows
-constexpr int TC_NMAX = 256;
-constexpr int TC_STAGES = 3;
-constexpr int TC_MAXG = 4;
+constexpr int TC_NMAX = 256;      // trajectories of one sub-group (MMA N, tensor-memory columns)
+constexpr int TC_STAGES = 3;      // ring slots in shared memory; a launch uses 2 or 3 (tuned)
+constexpr int TC_MAXG = 8;        // sub-groups per launch: (node set, range of <= 256 trajectories)
+constexpr int TC_MAXM = 8;        // node sets (member operators) of a grouped operator
 constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 TMEM + MMA, warps 2..9 epilogue
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_CHUNK = 4;        // K blocks (256 elements) accumulated in tensor memory per chunk
@@ -61,8 +62,9 @@ constexpr uint32_t TC_BH_BYTES = (TC_NMAX / 2) * TC_BK * 2;   // 16 KB per plane
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_BH_BYTES;
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
 
+// One sub-group: the rows of one member node set against a range of its trajectories.
 struct TcGroup {
-    int n, B, n_mma, mtiles;  // mtiles: pair tiles of 256 rows
+    int n, B, n_mma, mtiles;  // B: trajectories of the range; mtiles: pair tiles of 256 rows
     int nkb_pad;              // 32-column blocks per row block of the blocked W planes
     int64_t ldF;          // leading dimension (elements) of the F planes, [b][ldF]
     int64_t state_off;    // offset of the group's B x n block in the concatenated state
@@ -74,7 +76,8 @@ struct TcGroup {
 struct TcParams {
     CUtensorMap tmA_hi[TC_MAXG], tmA_lo[TC_MAXG], tmB_hi[TC_MAXG], tmB_lo[TC_MAXG];
     TcGroup grp[TC_MAXG];
-    int ngroups;
+    int ngroups;           // sub-groups
+    int nst;               // ring slots in use (2 or 3)
     int tile_start[TC_MAXG + 1];
     const int *sched;      // pair tiles in processing order, cluster c owns sched[sched_off[c] ..]
     const int *sched_off;  // [clusters + 1]
@@ -178,6 +181,10 @@ __device__ __forceinline__ float tc_firing(float u, float beta, float theta) {
     return 1.0f / (1.0f + expf(-beta * (u - theta)));
 }
 
+// Registers: the ten warps of a CTA sit three to a scheduler on two of the SM's four
+// schedulers, and each scheduler's register file holds 16,384, so a thread may use at most
+// 168 (a cap of 200 leaves no CTA resident); at 168 the epilogue's 128 FP32 accumulators
+// spill about 130 bytes a thread.
 template <int STAGE>  // 0: write I (nonlocal apply); 1..4: fused RK4 stage
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     tc_grouped_kernel(const __grid_constant__ TcParams p) {
@@ -222,7 +229,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         // ------------------------------------------------------------- TMA producer
         if (lane == 0) {
-            uint32_t it = 0;
+            int s = 0;          // ring slot and its phase, advanced per K block
+            uint32_t ph = 0;
             for (int ti = tbeg; ti < tend && !timed_out; ++ti) {
                 const int t = p.sched[ti];
                 const int g = tile_group(p, t);
@@ -231,9 +239,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 const int nk = (G.n + TC_BK - 1) / TC_BK;
                 const int nh = G.n_mma >> 1;
                 const uint32_t bytes = 2 * (2 * TC_A_BYTES + 2u * (uint32_t)nh * TC_BK * 2u);
-                for (int kb = 0; kb < nk; ++kb, ++it) {
-                    const int s = (int)(it % TC_STAGES);
-                    const uint32_t ph = (it / TC_STAGES) & 1u;
+                for (int kb = 0; kb < nk; ++kb) {
                     if (!mbar_spin_bounded(&empty[s], ph ^ 1u)) {
                         timed_out = true;
                         break;
@@ -245,6 +251,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                     tma_load_2d_pair(sA_lo(s), &p.tmA_lo[g], 0, wy, fb);
                     tma_load_2d_pair(sB_hi(s), &p.tmB_hi[g], kb * TC_BK, (int)rank * nh, fb);
                     tma_load_2d_pair(sB_lo(s), &p.tmB_lo[g], kb * TC_BK, (int)rank * nh, fb);
+                    if (++s == p.nst) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             if (timed_out) set_dev_error(p.err, DEV_TIMEOUT);
@@ -252,7 +262,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer (leader)
         if (lane == 0 && rank == 0) {
-            uint32_t it = 0, ci = 0;
+            uint32_t ci = 0;
+            int s = 0;          // ring slot and its phase, as in the producer
+            uint32_t ph = 0;
             for (int ti = tbeg; ti < tend && !timed_out; ++ti) {
                 const int t = p.sched[ti];
                 const int g = tile_group(p, t);
@@ -271,9 +283,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t d = tmem + ab * TC_NMAX;
                     const int kend = min(nk, kc + TC_CHUNK);
-                    for (int kb = kc; kb < kend; ++kb, ++it) {
-                        const int s = (int)(it % TC_STAGES);
-                        const uint32_t ph = (it / TC_STAGES) & 1u;
+                    for (int kb = kc; kb < kend; ++kb) {
                         if (!mbar_spin_bounded(&full[s], ph)) {
                             timed_out = true;
                             break;
@@ -289,6 +299,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                             umma_bf16_pair(d, alo + off, bhi + off, idesc, 1u);
                         }
                         umma_commit_pair(&empty[s]);  // the slot is free in both CTAs once read
+                        if (++s == p.nst) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
                     if (timed_out) break;
                     umma_commit_pair(&accf[ab]);      // chunk accumulators ready in both CTAs
@@ -457,7 +471,7 @@ struct TcPrepGroup {
     uint16_t *Fhi, *Flo;
 };
 struct TcPrepArgs {
-    TcPrepGroup grp[TC_MAXG];
+    TcPrepGroup grp[TC_MAXM];
     int ngroups;
     const float *u;
     float *U;
@@ -523,53 +537,86 @@ static nf_status make_map(CUtensorMap *m, const void *base, int64_t cols, int64_
 
 // Group state lives in the grouped operator handle.
 struct nf_group_state {
-    int count = 0;
-    nf_operator *members[nfi::TC_MAXG] = {};
-    int B[nfi::TC_MAXG] = {};
-    int order[nfi::TC_MAXG] = {};          // groups in launch order (largest N first)
-    uint16_t *F[nfi::TC_MAXG][2][2] = {};  // [group][buffer][hi/lo]
+    int count = 0;                           // member node sets
+    nf_operator *members[nfi::TC_MAXM] = {};
+    int B[nfi::TC_MAXM] = {};
+    int64_t state_off[nfi::TC_MAXM] = {};    // member blocks in the concatenated state (caller order)
+    int traj_off[nfi::TC_MAXM] = {};
+    uint16_t *F[nfi::TC_MAXM][2][2] = {};    // [member][buffer][hi/lo]: B_m x n_pad bf16 planes
+    // sub-groups in launch order (most trajectories first): member, first trajectory, count
+    int nsub = 0;
+    int sub_m[nfi::TC_MAXG] = {}, sub_b0[nfi::TC_MAXG] = {}, sub_nb[nfi::TC_MAXG] = {};
     int64_t state_total = 0;
     int traj_total = 0;
-    int nclusters = 0;                     // CTA pairs per launch
-    float *Iscr = nullptr;                 // state_total: sums awaiting the deferred RK4 update
-    int *sched = nullptr;                  // device: [nclusters + 1] offsets, then the tile list
-    nfi::TcParams params[2];               // [0]: reads F buffer 0, writes 1; [1]: reads 1, writes 0
+    int nclusters = 0;                       // CTA pairs per launch
+    float *Iscr = nullptr;                   // state_total: sums awaiting the deferred RK4 update
+    int *sched = nullptr;                    // device: [nclusters + 1] offsets, then the tile list
+    nfi::TcParams params[2];                 // [0]: reads F buffer 0, writes 1; [1]: reads 1, writes 0
+    // launch configuration chosen by the autotuner at nf_operator_group
+    int nst = nfi::TC_STAGES;                // ring slots in use
+    int split = 1;                           // pieces a member of >= 128 trajectories is cut into
+    double lpt_coef = 8.0;                   // MMA weight of a tile's K step in the LPT cost
+    float tuned_ms = 0.f;                    // the chosen configuration's time per launch
 };
 
 namespace nfi {
+
+// Cut every member's trajectories into sub-groups of at most TC_NMAX: ceil(B / 256) pieces,
+// or `split` pieces for members of at least 128 trajectories when that is more; piece sizes
+// are multiples of 16 (the MMA's N granularity) except the last.  Launch order: most
+// trajectories first.  Returns false when the pieces exceed TC_MAXG.
+static bool make_subgroups(nf_group_state *gs, int split) {
+    int m_of[TC_MAXG * 4], b0_of[TC_MAXG * 4], nb_of[TC_MAXG * 4];
+    int cnt = 0;
+    for (int m = 0; m < gs->count; ++m) {
+        const int Bm = gs->B[m];
+        int np = (Bm + TC_NMAX - 1) / TC_NMAX;
+        if (Bm >= 128) np = std::max(np, split);
+        const int piece = ((Bm + np - 1) / np + 15) / 16 * 16;
+        for (int b0 = 0; b0 < Bm; b0 += piece) {
+            if (cnt == TC_MAXG) return false;
+            m_of[cnt] = m;
+            b0_of[cnt] = b0;
+            nb_of[cnt] = std::min(piece, Bm - b0);
+            ++cnt;
+        }
+    }
+    int order[TC_MAXG];
+    std::iota(order, order + cnt, 0);
+    std::stable_sort(order, order + cnt, [&](int a, int b) { return nb_of[a] > nb_of[b]; });
+    gs->nsub = cnt;
+    for (int k = 0; k < cnt; ++k) {
+        gs->sub_m[k] = m_of[order[k]];
+        gs->sub_b0[k] = b0_of[order[k]];
+        gs->sub_nb[k] = nb_of[order[k]];
+    }
+    return true;
+}
 
 static nf_status build_group_params(nf_operator *op) {
     nf_group_state *gs = op->group;
     for (int par = 0; par < 2; ++par) {
         TcParams &P = gs->params[par];
         memset(&P, 0, sizeof(P));
-        P.ngroups = gs->count;
+        P.ngroups = gs->nsub;
+        P.nst = gs->nst;
         int tiles = 0;
-        int64_t soff = 0;
-        int toff = 0;
-        // state offsets follow the caller's member order; launch order is by N
-        int64_t state_off[TC_MAXG], traj_off[TC_MAXG];
-        for (int m = 0; m < gs->count; ++m) {
-            state_off[m] = soff;
-            traj_off[m] = toff;
-            soff += (int64_t)gs->B[m] * gs->members[m]->n;
-            toff += gs->B[m];
-        }
-        for (int k = 0; k < gs->count; ++k) {
-            const int m = gs->order[k];
+        for (int k = 0; k < gs->nsub; ++k) {
+            const int m = gs->sub_m[k], b0 = gs->sub_b0[k];
             nf_operator *mo = gs->members[m];
             TcGroup &G = P.grp[k];
             G.n = (int)mo->n;
-            G.B = gs->B[m];
+            G.B = gs->sub_nb[k];
             G.n_mma = (G.B + 15) / 16 * 16;
             G.mtiles = (int)ceil_div(mo->n, TC_PAIR_M);
             G.ldF = mo->n_pad;
-            G.state_off = state_off[m];
-            G.traj_off = (int)traj_off[m];
+            G.state_off = gs->state_off[m] + (int64_t)b0 * mo->n;
+            G.traj_off = gs->traj_off[m] + b0;
             G.rs = mo->rs;
             const int in = par, out = 1 - par;
-            G.Fhi_out = gs->F[m][out][0];
-            G.Flo_out = gs->F[m][out][1];
+            const int64_t foff = (int64_t)b0 * mo->n_pad;  // 16-byte aligned: n_pad is a multiple of 1024
+            G.Fhi_out = gs->F[m][out][0] + foff;
+            G.Flo_out = gs->F[m][out][1] + foff;
             // W planes in the blocked layout: viewed as (n_pad / 128) x (n_pad / 64) blocks of
             // 128 rows x 64 columns stacked row after row, so block (rb, kb) starts at row
             // (rb * n_pad / 64 + kb) * 128 of a 64-column matrix
@@ -577,13 +624,13 @@ static nf_status build_group_params(nf_operator *op) {
             NF_TRY(make_map(&P.tmA_hi[k], mo->Whi, kBlkCols, wrows, kBlkCols, TC_M));
             NF_TRY(make_map(&P.tmA_lo[k], mo->Wlo, kBlkCols, wrows, kBlkCols, TC_M));
             G.nkb_pad = (int)(mo->n_pad / kBlkCols);
-            // each CTA of a pair stages half of the N trajectory rows
-            NF_TRY(make_map(&P.tmB_hi[k], gs->F[m][in][0], mo->n, G.B, mo->n_pad, G.n_mma / 2));
-            NF_TRY(make_map(&P.tmB_lo[k], gs->F[m][in][1], mo->n, G.B, mo->n_pad, G.n_mma / 2));
+            // each CTA of a pair stages half of the sub-group's N trajectory rows
+            NF_TRY(make_map(&P.tmB_hi[k], gs->F[m][in][0] + foff, mo->n, G.B, mo->n_pad, G.n_mma / 2));
+            NF_TRY(make_map(&P.tmB_lo[k], gs->F[m][in][1] + foff, mo->n, G.B, mo->n_pad, G.n_mma / 2));
             P.tile_start[k] = tiles;
             tiles += G.mtiles;
         }
-        P.tile_start[gs->count] = tiles;
+        P.tile_start[gs->nsub] = tiles;
         P.state_total = gs->state_total;
         P.err = op->err;
         P.step_ctr = op->step_ctr;
@@ -594,10 +641,12 @@ static nf_status build_group_params(nf_operator *op) {
 }
 
 // Longest-processing-time assignment of the pair tiles to the clusters of one launch.  A
-// tile's cost is its number of 32-wide K steps times the larger of the per-SM MMA time of a
-// block (3 products x 128 x N x 32 FMA at 4096 FMA per clock: 3 N clocks) and the time to
-// stream its 16 KB of W hi/lo per SM at an even share of HBM bandwidth (~760 clocks).
-static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
+// tile's cost is its number of 32-wide K steps times the larger of an MMA term, coef x N
+// (N = the sub-group's MMA width; the tensor-core time of a step grows with N), and a
+// floor of 840 for streaming its 16 KB of W hi/lo at an even share of HBM bandwidth; coef
+// is chosen by the autotuner.  Every other cluster runs its list backwards, so that wide
+// (tensor-bound) and narrow (HBM-bound) tiles overlap instead of running in two phases.
+static nf_status build_schedule(nf_operator *op, double coef, cudaStream_t s) {
     nf_group_state *gs = op->group;
     const TcParams &P = gs->params[0];
     const int ntiles = P.tile_start[P.ngroups];
@@ -612,12 +661,7 @@ static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
     std::vector<double> cost(ntiles);
     for (int k = 0; k < P.ngroups; ++k) {
         const TcGroup &G = P.grp[k];
-        // time per K step: the MMAs (∝ N) or the W stream, whichever is longer.  Run alone on
-        // GB300, a 64-wide step takes 1.36 µs for N = 256 tiles and 0.84 µs for N = 64 tiles
-        // (HBM-bound); in the mixed launch the N = 256 tiles weigh more still (coefficient of
-        // N swept over 4.5 / 5.3 / 6.5 / 8: 2.101 / 2.112 / 2.087 / 2.084 ms per launch on
-        // the 448-trajectory workload, 2.154 ms with the former 3 / 760 model)
-        const double c = (double)ceil_div(G.n, 32) * std::max(8.0 * G.n_mma, 840.0);
+        const double c = (double)ceil_div(G.n, 32) * std::max(coef * G.n_mma, 840.0);
         for (int t = P.tile_start[k]; t < P.tile_start[k + 1]; ++t) cost[t] = c;
     }
     std::vector<int> order(ntiles);
@@ -630,9 +674,6 @@ static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
         lists[c].push_back(t);
         load[c] += cost[t];
     }
-    // LPT leaves every cluster's list in decreasing cost order, so all clusters would run
-    // their tensor-bound (wide) tiles at the same time and their HBM-bound (narrow) tiles
-    // later; every other cluster runs its list backwards, so the two kinds overlap
     for (int c = 1; c < nclust; c += 2) std::reverse(lists[c].begin(), lists[c].end());
     std::vector<int> host;
     host.reserve(nclust + 1 + ntiles);
@@ -643,6 +684,9 @@ static nf_status build_schedule(nf_operator *op, cudaStream_t s) {
     }
     host.push_back(off);
     for (int c = 0; c < nclust; ++c) host.insert(host.end(), lists[c].begin(), lists[c].end());
+    NF_CUDA_TRY(cudaStreamSynchronize(s));  // no launch may still read the previous list
+    if (gs->sched) NF_CUDA_TRY(cudaFree(gs->sched));
+    gs->sched = nullptr;
     NF_CUDA_TRY(cudaMalloc(&gs->sched, sizeof(int) * host.size()));
     NF_CUDA_TRY(cudaMemcpyAsync(gs->sched, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, s));
     NF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -674,31 +718,26 @@ nf_status tc_prep(nf_operator *op, const float *u, const float *beta, const floa
     nf_group_state *gs = op->group;
     TcPrepArgs a{};
     a.ngroups = gs->count;
-    int64_t soff = 0;
-    int toff = 0;
     for (int m = 0; m < gs->count; ++m) {
         TcPrepGroup &G = a.grp[m];
         G.n = (int)gs->members[m]->n;
         G.B = gs->B[m];
         G.ldF = gs->members[m]->n_pad;
-        G.state_off = soff;
-        G.traj_off = toff;
+        G.state_off = gs->state_off[m];
+        G.traj_off = gs->traj_off[m];
         G.Fhi = gs->F[m][buffer][0];
         G.Flo = gs->F[m][buffer][1];
-        soff += (int64_t)G.B * G.n;
-        toff += G.B;
     }
     a.u = u;
     a.U = copy_U ? op->U : nullptr;
     a.beta = beta;
     a.theta = theta;
-    a.total = soff;
+    a.total = gs->state_total;
     tc_prep_kernel<<<(unsigned)ceil_div(a.total, 256), 256, 0, s>>>(a);
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
 }
 
-// One grouped GEMM launch.  mode 0 writes I; mode 1 runs RK4 stage `stage`.
 nf_status tc_launch(nf_operator *op, int parity, int mode, float *I, float *u, const float *beta, const float *theta,
                     double dt, int stage, float *ckpt, int C, cudaStream_t s) {
     TcParams P = op->group->params[parity];
@@ -739,18 +778,101 @@ nf_status tc_init_attr() {
 
 using namespace nfi;
 
+namespace nfi {
+
+// Time one launch configuration: one warm-up and two timed nonlocal-sum launches (mode 0,
+// output into the group's scratch state); the faster timed launch counts.
+static nf_status time_config(nf_operator *op, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    nf_group_state *gs = op->group;
+    float best = 3.4e38f;
+    for (int rep = 0; rep < 3; ++rep) {
+        NF_CUDA_TRY(cudaEventRecord(e0, s));
+        NF_TRY(tc_launch(op, 0, 0, gs->Iscr, nullptr, nullptr, nullptr, 0.0, 0, nullptr, 1, s));
+        NF_CUDA_TRY(cudaEventRecord(e1, s));
+        NF_CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        NF_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        if (rep > 0) best = std::min(best, t);
+    }
+    *ms = best;
+    return NF_OK;
+}
+
+// The batched path's autotuner.  Candidates: trajectory split {1, 2} (a member of 128..256
+// trajectories as one sub-group of MMA width up to 256, or as two of half the width: more
+// tiles to balance, W streamed twice), LPT weight of the MMA term {4, 8, 12} (how much more
+// a wide tile costs than a narrow, HBM-bound one), ring depth {3, 2} (64 KB slots in flight).
+// Each candidate is timed on the device (time_config) and the fastest is kept; the results
+// do not depend on the choice (each output is the same MMA chain over K in the same order).
+static nf_status tc_autotune(nf_operator *op, cudaStream_t s) {
+    nf_group_state *gs = op->group;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NF_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate", __FILE__, __LINE__);
+    }
+    struct Best {
+        int split, nst;
+        double coef;
+        float ms;
+    } best{1, TC_STAGES, 8.0, 3.4e38f};
+    nf_status st = NF_OK;
+    const int splits[2] = {1, 2};
+    const double coefs[3] = {4.0, 8.0, 12.0};
+    const int depths[2] = {TC_STAGES, 2};
+    for (int a = 0; a < 2 && st == NF_OK; ++a) {
+        if (!make_subgroups(gs, splits[a])) continue;
+        if (a > 0) {  // a split that changes nothing is not timed twice
+            bool changed = false;
+            for (int m = 0; m < gs->count; ++m) changed |= gs->B[m] >= 128;
+            if (!changed) continue;
+        }
+        for (int c = 0; c < 3 && st == NF_OK; ++c) {
+            for (int d = 0; d < 2 && st == NF_OK; ++d) {
+                gs->nst = depths[d];
+                st = build_group_params(op);
+                if (st == NF_OK) st = build_schedule(op, coefs[c], s);
+                float ms = 0.f;
+                if (st == NF_OK) st = time_config(op, s, e0, e1, &ms);
+                if (st == NF_OK && ms < best.ms) best = Best{splits[a], depths[d], coefs[c], ms};
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != NF_OK) return st;
+    gs->split = best.split;
+    gs->nst = best.nst;
+    gs->lpt_coef = best.coef;
+    gs->tuned_ms = best.ms;
+    if (!make_subgroups(gs, gs->split)) return fail(NF_ERR_UNSUPPORTED, "no feasible sub-group split");
+    NF_TRY(build_group_params(op));
+    return build_schedule(op, gs->lpt_coef, s);
+}
+
+}  // namespace nfi
+
 extern "C" nf_status nf_operator_group(nf_operator *const *ops, const int *B_per_op, int count, void *stream,
                                        nf_operator **grouped) {
     clear_error();
     NF_ARG(ops && B_per_op && grouped, "ops, B_per_op and grouped must be non-NULL");
     *grouped = nullptr;
-    NF_ARG(count >= 1 && count <= TC_MAXG, "count = %d must be in 1..%d", count, TC_MAXG);
+    NF_ARG(count >= 1 && count <= TC_MAXM, "count = %d must be in 1..%d", count, TC_MAXM);
+    int pieces = 0;
     for (int m = 0; m < count; ++m) {
         NF_ARG(ops[m], "ops[%d] is NULL", m);
         NF_ARG(ops[m]->path == NF_DENSE_BF16X2, "ops[%d] must use the NF_DENSE_BF16X2 path", m);
-        NF_ARG(B_per_op[m] >= 1 && B_per_op[m] <= TC_NMAX, "B[%d] = %d must be in 1..%d", m, B_per_op[m], TC_NMAX);
+        NF_ARG(B_per_op[m] >= 1 && B_per_op[m] <= TC_MAXG * TC_NMAX, "B[%d] = %d must be in 1..%d", m, B_per_op[m],
+               TC_MAXG * TC_NMAX);
         NF_ARG(ops[m]->n >= TC_BK, "ops[%d] has n = %lld < %d nodes", m, (long long)ops[m]->n, TC_BK);
+        pieces += (B_per_op[m] + TC_NMAX - 1) / TC_NMAX;
     }
+    if (pieces > TC_MAXG)
+        return fail(NF_ERR_UNSUPPORTED,
+                    "the members need %d sub-groups of <= %d trajectories; one launch holds at most %d", pieces,
+                    TC_NMAX, TC_MAXG);
     NF_TRY(tc_init_attr());
     cudaStream_t s = as_stream(stream);
     nf_operator *op = new nf_operator();
@@ -765,11 +887,11 @@ extern "C" nf_status nf_operator_group(nf_operator *const *ops, const int *B_per
     for (int m = 0; m < count; ++m) {
         gs->members[m] = ops[m];
         gs->B[m] = B_per_op[m];
-        gs->order[m] = m;
+        gs->state_off[m] = total;
+        gs->traj_off[m] = traj;
         total += (int64_t)B_per_op[m] * ops[m]->n;
         traj += B_per_op[m];
     }
-    std::stable_sort(gs->order, gs->order + count, [&](int a, int b) { return gs->B[a] > gs->B[b]; });
     gs->state_total = total;
     gs->traj_total = traj;
     op->n = total;  // state length of one "trajectory" of the group (the concatenation)
@@ -797,9 +919,28 @@ extern "C" nf_status nf_operator_group(nf_operator *const *ops, const int *B_per
     if (e == cudaSuccess) e = cudaMalloc(&gs->Iscr, sizeof(float) * total);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(state)", __FILE__, __LINE__));
     op->state_cap = (size_t)total;
-    nf_status st = build_group_params(op);
-    if (st == NF_OK) st = build_schedule(op, s);
+    nf_status st = tc_autotune(op, s);
+    if (st == NF_OK) {  // the tuning launches may have recorded a timeout; start clean
+        int flag = 0;
+        e = cudaMemcpy(&flag, op->err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy(flag)", __FILE__, __LINE__);
+        else if (flag != 0) st = fail(NF_ERR_TIMEOUT, "a bounded wait gave up while tuning the batched GEMM");
+    }
     if (st != NF_OK) return cleanup(st);
     *grouped = op;
+    return NF_OK;
+}
+
+extern "C" nf_status nf_operator_group_tuning(nf_operator *op, int *ring_depth, int *traj_split, double *lpt_coef,
+                                              int *subgroups, float *ms) {
+    clear_error();
+    NF_ARG(op && ring_depth && traj_split && lpt_coef && subgroups && ms, "arguments must be non-NULL");
+    NF_ARG(op->path == NF_GROUPED && op->group, "not a grouped operator");
+    const nf_group_state *gs = op->group;
+    *ring_depth = gs->nst;
+    *traj_split = gs->split;
+    *lpt_coef = gs->lpt_coef;
+    *subgroups = gs->nsub;
+    *ms = gs->tuned_ms;
     return NF_OK;
 }

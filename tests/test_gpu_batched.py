@@ -128,3 +128,51 @@ def test_group_rejects_non_bf16_members(nf):
     with pytest.raises(nf.NFError) as ei:
         nf.GroupedOperator([op], [4])
     assert ei.value.name == "NF_ERR_ARG"
+
+
+@pytest.mark.parametrize("specs", [
+    [(1200, 40, 11), (900, 17, 12), (2000, 64, 13), (700, 5, 14), (1500, 130, 15), (1100, 33, 16)],  # six node sets
+    [(1800, 300, 21), (1000, 20, 22)],   # 300 trajectories: two sub-groups of one node set
+])
+def test_grouped_more_sets_and_trajectories(nf, specs):
+    """Grouped operators beyond four node sets and beyond 256 trajectories per set, after the
+    autotuner has picked the launch configuration: nonlocal sums and 5 RK4 steps against the
+    oracle on sampled trajectories of every set."""
+    kern = (1.0, 0.1, 0.5, 0.2)
+    data, ops = _members(nf, specs, kern)
+    grp = nf.GroupedOperator(ops, [s[1] for s in specs])
+    t = grp.tuning()
+    assert t["ring_depth"] in (2, 3) and t["traj_split"] in (1, 2) and t["lpt_coef"] in (4.0, 8.0, 12.0)
+    assert len(specs) <= t["subgroups"] <= 8 and t["ms_per_launch"] > 0
+    u = torch.cat([dev(d[3]).reshape(-1) for d in data])
+    beta = torch.cat([dev(d[4]) for d in data])
+    theta = torch.cat([dev(d[5]) for d in data])
+    I = nf.nf_nonlocal_apply(grp, u, beta, theta)
+    nsteps, dt = 5, 0.05
+    nf.nf_rk4_advance(grp, u, 0.0, dt, nsteps, beta, theta)
+    grp.check()
+    rng = np.random.default_rng(len(specs))
+    for (ns, X, q, u0, be, th), gI, gu in zip(data, grp.split(I), grp.split(u)):
+        B = u0.shape[0]
+        sel = np.unique(np.concatenate([[0, B - 1], rng.choice(B, min(B, 3), replace=False)]))
+        wI = oracle.nonlocal_sum(f32(X), f32(q), f32(u0[sel]), f32(kern), f32(be[sel]), f32(th[sel]))
+        wu = oracle.rk4(f32(X), f32(q), f32(u0[sel]), f32(kern), f32(be[sel]), f32(th[sel]), 0.0, dt, nsteps)
+        for got, want in ((gI.cpu().numpy()[sel], wI), (gu.cpu().numpy()[sel], wu)):
+            err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+            assert err.max() < REL_L2, err.max()
+    grp.close()
+    for op in ops:
+        op.close()
+
+
+def test_group_limits(nf):
+    """Nine node sets, or trajectories needing more than eight sub-groups of 256, are refused."""
+    X = np.random.default_rng(1).uniform(size=(256, 3)).astype(np.float32)
+    op = nf.Operator(dev(X), dev(np.full(256, 1 / 256)), (1.0, 0.3, 0.5, 0.6), nf.DENSE_BF16X2)
+    with pytest.raises(nf.NFError) as ei:
+        nf.GroupedOperator([op] * 9, [4] * 9)
+    assert ei.value.name == "NF_ERR_ARG"
+    with pytest.raises(nf.NFError) as ei:
+        nf.GroupedOperator([op, op], [1800, 300])   # 8 + 2 sub-groups
+    assert ei.value.name == "NF_ERR_UNSUPPORTED"
+    op.close()
