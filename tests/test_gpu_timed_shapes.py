@@ -12,10 +12,13 @@ finishes in seconds.
   10 RK4 steps through the grouped tensor-core path, against the oracle's RK4 on sampled
   trajectories of every node set.
 
-Tolerances (relative L2 unless stated): dL/du0 1e-5; dL/d(A1, s1, A2, s2) 1e-4, since each
-is a sum over 4 x 200 stages of FP32 pair sums whose cancellation (the Mexican hat's two
-Gaussians of opposite sign) FP32 cannot avoid; the directional derivative 1e-4; the bf16 x 3
-grouped trajectories 2e-5, the per-term bound of the split (2^-17 + 2^-17 + 2^-18)."""
+Tolerances (relative L2 unless stated): dL/du0 1e-5; dL/d(A1, s1, A2, s2) 1e-5 as a vector
+and 1e-4 per component, since a single small component is a sum over 4 x 200 stages of FP32
+pair sums whose cancellation (the Mexican hat's two Gaussians of opposite sign) FP32 cannot
+avoid (measured on GB300: 4e-7 and 9e-8 as vectors); the directional derivative 1e-4; the
+bf16 x 3 grouped trajectories 1e-5, the bar of the FP32 paths: the split's per-term bound is
+2^-17 + 2^-17 + 2^-18 ~= 1.9e-5, but with thousands of terms per sum the errors average out
+(measured 1.1e-7 after 10 steps)."""
 import numpy as np
 import pytest
 import torch
@@ -89,7 +92,7 @@ def test_adjoint_200_steps_checkpoints_every_20(nf, n, B, kern):
         e_k = np.linalg.norm(gk[b] - gk_o[b]) / np.linalg.norm(gk_o[b])
         print(f"n={X.shape[0]} B={B} kern={kern} traj {b}: dL/du0 rel L2 {e_u:.2e}, dL/dkernel rel L2 {e_k:.2e}")
         assert e_u < 1e-5
-        assert e_k < 1e-4
+        assert e_k < 1e-5  # the four gradients as a vector
         np.testing.assert_allclose(gk[b], gk_o[b], rtol=1e-4, atol=1e-6 * np.abs(gk_o[b]).max())
 
 
@@ -151,7 +154,7 @@ def test_grouped_rk4_at_batched_trajectory_counts(nf):
         err = np.linalg.norm(g - want, axis=1) / np.linalg.norm(want, axis=1)
         worst = max(worst, float(err.max()))
     print(f"grouped RK4 at the batched trajectory counts: worst relative L2 {worst:.3e}")
-    assert worst < 2e-5
+    assert worst < 1e-5
     grp.close()
     for op in ops:
         op.close()
