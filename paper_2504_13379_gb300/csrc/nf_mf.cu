@@ -1368,9 +1368,10 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
 }
 
 // Rows per warp of the adjoint pair kernel, chosen once per operator by timing both shapes
-// (4 rows, two CTAs per SM; 8 rows, one CTA per SM) on the operator's own node set: two
-// launches each, the faster of the second launches is kept.  The launches write the call's
-// scratch buffers only, before the call's own passes overwrite them.
+// (4 rows, two CTAs per SM; 8 rows, one CTA per SM) on the operator's own node set: three
+// launches each, each between its own events; the fastest of the last two counts.  The
+// launches write the call's scratch buffers only, before the call's own passes overwrite
+// them.
 nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, float *gpart, cudaStream_t s) {
     if (op->adj_r) return NF_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1387,7 +1388,7 @@ nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, f
     float r2 = 1.f;
     for (int c = 0; c < 2 && st == NF_OK; ++c) {
         op->adj_r = cand[c];
-        for (int rep = 0; rep < 2 && st == NF_OK; ++rep) {
+        for (int rep = 0; rep < 3 && st == NF_OK; ++rep) {
             ce = cudaEventRecord(e0, s);
             if (ce == cudaSuccess) st = launch_adj_sym(op, vg, B, 0, wpart, gpart, &r2, s);
             if (st == NF_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, s);
@@ -1395,7 +1396,7 @@ nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, f
             float ms = 0.f;
             if (st == NF_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
             if (ce != cudaSuccess && st == NF_OK) st = cuda_fail(ce, "adjoint autotune", __FILE__, __LINE__);
-            if (st == NF_OK && rep == 1 && ms < best) {
+            if (st == NF_OK && rep >= 1 && ms < best) {  // the first launch warms up
                 best = ms;
                 best_r = cand[c];
             }
@@ -1473,12 +1474,18 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
         op->mf_sym_r = sh.first;
         op->sym_blk = sh.second;
         NF_TRY(launch_sym(op, 1, 0, s));  // warm-up
-        NF_CUDA_TRY(cudaEventRecord(e0, s));
-        for (int rep = 0; rep < 2; ++rep) NF_TRY(launch_sym(op, 1, 0, s));
-        NF_CUDA_TRY(cudaEventRecord(e1, s));
-        NF_CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        NF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        // each launch between its own events, the fastest of three: host-side gaps between
+        // launches (a profiler attached to the process, a busy host) then do not enter
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            NF_CUDA_TRY(cudaEventRecord(e0, s));
+            NF_TRY(launch_sym(op, 1, 0, s));
+            NF_CUDA_TRY(cudaEventRecord(e1, s));
+            NF_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            NF_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            ms = std::min(ms, t);
+        }
         if (ms < best) {
             best = ms;
             best_r = sh.first;
