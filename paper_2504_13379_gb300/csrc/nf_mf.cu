@@ -612,6 +612,10 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     auto lo2 = [](float4 v) { return f2_pack(v.x, v.y); };
     auto hi2 = [](float4 v) { return f2_pack(v.z, v.w); };
     // e1, e2 of two pairs from the exponent argument (expanded s_ij or r^2)
+    // e1 = e2^M by squaring on the FMA pipe.  Taking it from the SFU instead (ex2 of -M s:
+    // one multiply and two more exponentials in place of two multiplies) measured slower,
+    // 1.772-1.776 against 1.720 ms per sum on the 100,000-node torus, for half or all of
+    // the column pairs: the SFU results' register moves cost more than the multiply saved.
     auto exps = [&](u64 arg, u64 &e1, u64 &e2) {
         float s0, s1v;
         f2_unpack(arg, s0, s1v);

@@ -56,7 +56,13 @@ constexpr int TC_MAXM = 8;        // node sets (member operators) of a grouped o
 constexpr int TC_THREADS = 320;    // warp 0 TMA, warp 1 TMEM + MMA, warps 2..9 epilogue
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_CHUNK = 4;        // K blocks (256 elements) accumulated in tensor memory per chunk
-constexpr int TC_EPI_BATCH = 2;    // trajectory columns per batch of epilogue loads
+constexpr int TC_EPI_BATCH = 2;    // trajectory columns per batch of epilogue loads (accumulators live)
+constexpr int TC_EPI_TAIL = 8;     // the same once the accumulators are written out
+
+template <int V>
+struct BatchTag {
+    static constexpr int value = V;
+};
 constexpr uint32_t TC_A_BYTES = TC_M * TC_BK * 2;             // 16 KB per plane
 constexpr uint32_t TC_BH_BYTES = (TC_NMAX / 2) * TC_BK * 2;   // 16 KB per plane: half of N = 256
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_BH_BYTES;
@@ -326,7 +332,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
         // does not wait for its global-memory latency.  Pending job: group pg (< 0: none),
         // pair tile pmt, next column pnext (warp-uniform).
         int pg = -1, pmt = 0, pnext = 0;
-        auto rk4_slice = [&](int upto) {
+        // NBT columns per batch of loads: TC_EPI_BATCH between chunk drains, while the 128
+        // accumulators are live; TC_EPI_TAIL once they are written out (the rest of a tile and
+        // the cluster's last tile, which no MMA overlaps), for more loads in flight.
+        auto rk4_slice = [&](int upto, auto nbt_tag) {
+            constexpr int NBT = decltype(nbt_tag)::value;
             if (pg < 0) return;
             const TcGroup &PG = p.grp[pg];
             const int pncol = PG.n_mma >> 1, pcol0 = half * pncol;
@@ -334,12 +344,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             const int i = pmt * TC_PAIR_M + row_in_tile;
             if (i < PG.n) {
                 const int64_t base = PG.state_off + i;
-                for (int c0 = pnext; c0 < end && pcol0 + c0 < PG.B; c0 += TC_EPI_BATCH) {
+                for (int c0 = pnext; c0 < end && pcol0 + c0 < PG.B; c0 += NBT) {
                     // every load of the batch is issued before any result is used
-                    float Dv[TC_EPI_BATCH], Uv[TC_EPI_BATCH], uv[TC_EPI_BATCH], kv[TC_EPI_BATCH], bb[TC_EPI_BATCH],
-                        th[TC_EPI_BATCH];
+                    float Dv[NBT], Uv[NBT], uv[NBT], kv[NBT], bb[NBT], th[NBT];
 #pragma unroll
-                    for (int j = 0; j < TC_EPI_BATCH; ++j) {
+                    for (int j = 0; j < NBT; ++j) {
                         const int b = min(pcol0 + c0 + j, PG.B - 1);
                         const int64_t idx = base + (int64_t)b * PG.n;
                         Dv[j] = p.Iscr[idx];
@@ -350,9 +359,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                         th[j] = __ldg(p.theta + PG.traj_off + b);
                     }
 #pragma unroll
-                    for (int j = 0; j < TC_EPI_BATCH; ++j) {
+                    for (int j = 0; j < NBT; ++j) {
                         const int b = pcol0 + c0 + j;
-                        if (b >= PG.B) break;
+                        if (b >= PG.B || c0 + j >= end) break;
                         const int64_t idx = base + (int64_t)b * PG.n;
                         const float k = -Uv[j] + Dv[j];
                         float Un;
@@ -400,7 +409,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             for (int c = 0; c < 128; ++c) acc[c] = 0.f;
             for (int kc = 0; kc < nk; kc += TC_CHUNK, ++ci) {
                 const uint32_t ab = ci & 1u, aph = (ci >> 1) & 1u;
-                if (STAGE > 0) rk4_slice(pnext + per);  // while this chunk is on the tensor core
+                if (STAGE > 0) rk4_slice(pnext + per, BatchTag<TC_EPI_BATCH>{});  // while this chunk is on the tensor core
                 if (!mbar_wait_bounded(&accf[ab], aph)) {
                     if (lane == 0) set_dev_error(p.err, DEV_TIMEOUT);
                     timed_out = true;
@@ -421,7 +430,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) mbar_arrive_remote(acce_leader[ab]);
             }
             if (timed_out) break;
-            if (STAGE > 0) rk4_slice(1 << 30);  // whatever of the previous tile is left
             const int i = mt * TC_PAIR_M + row_in_tile;
             if (i < G.n) {
                 const float si = G.rs[i];
@@ -435,12 +443,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 }
             }
             if (STAGE > 0) {
+                // whatever of the previous tile is left (other tiles' state than this one's)
+                rk4_slice(1 << 30, BatchTag<TC_EPI_TAIL>{});
                 pg = g;
                 pmt = mt;
                 pnext = 0;
             }
         }
-        if (STAGE > 0 && !timed_out) rk4_slice(1 << 30);
+        if (STAGE > 0 && !timed_out) rk4_slice(1 << 30, BatchTag<TC_EPI_TAIL>{});
     }
     // After a timeout, copies already issued may still land in shared memory and count on
     // the leader's barriers: give them time before the pair leaves (bounded, ~1 ms).
