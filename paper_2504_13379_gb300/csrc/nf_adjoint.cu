@@ -151,12 +151,9 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     const int64_t n = op->n, n_pad = op->n_pad;
     const size_t BN = (size_t)B * n;
     NF_TRY(ensure_workspace(op, B, mf_splits(op, B)));
-    const int slots = adj_slots(op);  // one W nu slot per 1,024-node block
-    const int64_t ncta = sym_pair_count(op);
     // block-pair culling (nf_operator_mf_cull): the adjoint kernel runs over its own live
     // pairs, and each node's live W nu slots are added into slot 0 before the epilogue
     const bool cull = op->mf_cull && op->adj_pairs;
-    const int64_t ncta_run = cull ? op->adj_live : ncta;
     const int Cseg = std::min(C, std::max(nsteps, 1));
     float *stages = nullptr, *lam = nullptr, *acc = nullptr, *ubuf = nullptr, *wpart = nullptr, *gpart = nullptr;
     float2 *vg = nullptr;
@@ -166,12 +163,16 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     NF_CUDA_TRY(scratch.alloc(&lam, sizeof(float) * BN));
     NF_CUDA_TRY(scratch.alloc(&acc, sizeof(float) * BN));
     NF_CUDA_TRY(scratch.alloc(&ubuf, sizeof(float) * BN));
-    NF_CUDA_TRY(scratch.alloc(&wpart, sizeof(float) * (size_t)slots * B * n_pad));
-    NF_CUDA_TRY(scratch.alloc(&gpart, sizeof(float) * 4 * (size_t)B * ncta));
+    // W nu slots and parameter partials for the smallest node block the kernel may take
+    NF_CUDA_TRY(scratch.alloc(&wpart, sizeof(float) * (size_t)adj_slot_capacity(op) * B * n_pad));
+    NF_CUDA_TRY(scratch.alloc(&gpart, sizeof(float) * 4 * (size_t)B * adj_pair_capacity(op)));
     NF_CUDA_TRY(scratch.alloc(&vg, sizeof(float2) * (size_t)B * n_pad));
     NF_CUDA_TRY(scratch.alloc(&gk, sizeof(double) * 4 * B));
     NF_CUDA_TRY(cudaMemsetAsync(vg, 0, sizeof(float2) * (size_t)B * n_pad, s));  // padded columns stay zero
     NF_TRY(adj_autotune(op, vg, B, wpart, gpart, s));  // first call on this operator only
+    const int slots = adj_slots(op);  // one W nu slot per node block of the chosen shape
+    const int64_t ncta = sym_pair_count(op);
+    const int64_t ncta_run = cull ? op->adj_live : ncta;
     NF_CUDA_TRY(cudaMemsetAsync(gk, 0, sizeof(double) * 4 * B, s));
     NF_CUDA_TRY(cudaMemcpyAsync(lam, lambda_T, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
     static const nf_forcing none{NF_FORCE_NONE, nullptr, nullptr, 0, 0, 0, 0, 0, 0, 0, 0};

@@ -181,6 +181,7 @@ struct nf_operator {
     int mf_variant = -1;     // launch shape of the packed pair kernel
     int mf_sym_r = 8;        // rows per warp of the symmetric single-trajectory kernel (autotuned)
     int adj_r = 0;           // rows per warp of the adjoint pair kernel (0: not yet timed; 4 or 8)
+    int adj_blk = 0;         // its node block (0: not yet timed; 1024 or 512)
     int mf_sched = 0;        // NF_MF_AUTO / NF_MF_SYMMETRIC / NF_MF_PACKED
     int sym_blk = 1024;      // node block of the symmetric kernel (1024, or 512 when autotuned faster)
     int planar = 0;          // every node has the same z: the symmetric kernel drops the z terms
@@ -255,7 +256,9 @@ SplitPlan mf_plan(nf_operator *op);     // column splits of the multi-trajectory
 int mf_splits(nf_operator *op, int B);  // partial-sum slots of a matrix-free launch over B trajectories
 int64_t sym_pair_count(const nf_operator *op);  // block pairs of the symmetric kernels
 int sym_slots(const nf_operator *op);   // node blocks of the symmetric schedule (W nu slots)
-int adj_slots(const nf_operator *op);   // node blocks of the adjoint kernel (1,024 nodes)
+int adj_slots(const nf_operator *op);   // node blocks of the adjoint kernel (its W nu slots)
+int64_t adj_pair_capacity(const nf_operator *op);  // block pairs / slots of the adjoint kernel's
+int adj_slot_capacity(const nf_operator *op);      // smallest block (512): scratch sizes
 nf_status mf_set_cull(nf_operator *op, int enable, int64_t *live, int64_t *total, cudaStream_t s);
 nf_status launch_adj_cull_reduce(nf_operator *op, float *wpart, int B, int b, cudaStream_t s);
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,

@@ -806,29 +806,32 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
 //     (sum e nu_j is the W nu row sum), with arg = r^2 - n_i; the pass end forms the
 //     four sums from them.  Each CTA writes its four sums (r^2 in exponent units: of s2
 //     when M > 0, else of s1) to gpart; a fixed-order FP64 reduction adds them.
-constexpr size_t AS_SMEM_FLOATS = (size_t)(5 + 14 + 1 + MS_WARPS) * MS_BLK;
+constexpr size_t as_smem_floats(int blk) { return (size_t)(5 + 14 + 1 + MS_WARPS) * blk; }
 
 // R = 4: two CTAs per SM (128 registers); R = 8: one CTA per SM with the whole register
-// file (eight rows' accumulators, more independent work per warp, fewer warps).
-template <int R, int M>
+// file (eight rows' accumulators, more independent work per warp, fewer warps).  BLK: node
+// block of 1,024 or 512 (four times the CTAs, for node sets whose 1,024-node block pairs
+// leave the last wave of CTAs partly empty).
+template <int R, int M, int BLK>
 __global__ void __launch_bounds__(MS_THREADS, R >= 8 ? 1 : 2)
 adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all, const int *__restrict__ rowperm,
                int64_t n_pad, int B, int b, float k2, float A1, float A2, float per,
                float *__restrict__ wpart, float *__restrict__ gpart, const int *__restrict__ pairs) {
     static_assert(M == 0 || (M >= 2 && M <= 4), "width ratio M must be 0 (general), 2, 3 or 4");
     static_assert(R == 4 || R == 8, "rows per warp");
-    constexpr int NPASS = MS_BLK / R;
+    static_assert(BLK == 512 || BLK == 1024, "block size");
+    constexpr int NPASS = BLK / R;
     extern __shared__ __align__(16) float as_smem[];
     // column block: x, y, z, nu, g (floats), node (int)
-    float *xs = as_smem, *ys = xs + MS_BLK, *zs = ys + MS_BLK, *vs = zs + MS_BLK, *gsm = vs + MS_BLK;
-    int *cnode = reinterpret_cast<int *>(gsm + MS_BLK);
+    float *xs = as_smem, *ys = xs + BLK, *zs = ys + BLK, *vs = zs + BLK, *gsm = vs + BLK;
+    int *cnode = reinterpret_cast<int *>(gsm + BLK);
     // row block: node; per row (mx, my, mz, n_i), (h1, h1, h2, h2) -- the column-sum weights
     // A1 f1 nu_i and -A2 f2 nu_i -- and (v1, u1, v2, u2), as float4
-    int *rnode = cnode + MS_BLK;
-    float4 *rgeo = reinterpret_cast<float4 *>(rnode + MS_BLK);
-    float4 *rwn = rgeo + MS_BLK, *rgw = rwn + MS_BLK;
-    float4 *pc = rgw + MS_BLK;                               // per pass: centre, form
-    float *colacc = reinterpret_cast<float *>(pc + MS_BLK / 4);  // [MS_WARPS][MS_BLK]
+    int *rnode = cnode + BLK;
+    float4 *rgeo = reinterpret_cast<float4 *>(rnode + BLK);
+    float4 *rwn = rgeo + BLK, *rgw = rwn + BLK;
+    float4 *pc = rgw + BLK;                               // per pass: centre, form
+    float *colacc = reinterpret_cast<float *>(pc + BLK / 4);  // [MS_WARPS][BLK]
     __shared__ float gred[MS_WARPS][4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int I, J;
@@ -836,10 +839,10 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     const bool diag = I == J;
     const float2 *vg = vg_all + (int64_t)b * n_pad;
     const float *X = xyz, *Y = xyz + n_pad, *Z = xyz + 2 * n_pad;
-    const int64_t cbase = (int64_t)J * MS_BLK, rbase = (int64_t)I * MS_BLK;
+    const int64_t cbase = (int64_t)J * BLK, rbase = (int64_t)I * BLK;
     // exponent units: s1, or s2 when M > 0 (coordinates times sk = s1 / s2, once here)
     const float sk = M > 0 ? sqrtf(k2) : 1.f;
-    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+    for (int k = tid; k < BLK; k += MS_THREADS) {
         const int node = __ldg(rowperm + cbase + k);
         cnode[k] = node;
         xs[k] = X[node] * sk;
@@ -854,7 +857,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         rgeo[k] = make_float4(X[rn] * sk, Y[rn] * sk, Z[rn] * sk, 0.f);
         rgw[k] = make_float4(pr.x, pr.y, 0.f, 0.f);
     }
-    for (int k = tid; k < MS_WARPS * MS_BLK; k += MS_THREADS) colacc[k] = 0.f;
+    for (int k = tid; k < MS_WARPS * BLK; k += MS_THREADS) colacc[k] = 0.f;
     __syncthreads();
     // one thread per pass: centre, form and the rows' operands (see mf_sym_kernel)
     for (int ps = tid; ps < NPASS; ps += MS_THREADS) {
@@ -903,7 +906,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     const u64 *xs2 = reinterpret_cast<const u64 *>(xs), *ys2 = reinterpret_cast<const u64 *>(ys);
     const u64 *zs2 = reinterpret_cast<const u64 *>(zs), *vs2 = reinterpret_cast<const u64 *>(vs);
     const u64 *gs2 = reinterpret_cast<const u64 *>(gsm);
-    u64 *cw2 = reinterpret_cast<u64 *>(colacc + warp * MS_BLK);
+    u64 *cw2 = reinterpret_cast<u64 *>(colacc + warp * BLK);
     float *out_rows = wpart + ((int64_t)J * B + b) * n_pad;
     auto exps = [&](u64 arg, u64 &e1, u64 &e2) {
         float s0, s1v;
@@ -969,7 +972,7 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         // last real column measured no faster (809 against 811 ms for the 200-step gradient
         // at n = 40,000, whose padding is 5 % of the pairs)
         if (local) {
-            sweep_local(CInt<MS_BLK / 2>{});
+            sweep_local(CInt<BLK / 2>{});
         } else {
             auto sweep = [&](auto tag, auto lim) {
                 constexpr bool P = decltype(tag)::value;
@@ -991,9 +994,9 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             }
             };
             if (per > 0.f)
-                sweep(PerTag<true>{}, CInt<MS_BLK / 2>{});
+                sweep(PerTag<true>{}, CInt<BLK / 2>{});
             else
-                sweep(PerTag<false>{}, CInt<MS_BLK / 2>{});
+                sweep(PerTag<false>{}, CInt<BLK / 2>{});
         }
         auto fold = [](u64 x) {
             float lo, hi;
@@ -1037,10 +1040,10 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     }
     if (diag) return;
     float *out_cols = wpart + ((int64_t)I * B + b) * n_pad;
-    for (int k = tid; k < MS_BLK; k += MS_THREADS) {
+    for (int k = tid; k < BLK; k += MS_THREADS) {
         float s = 0.f;
 #pragma unroll
-        for (int w = 0; w < MS_WARPS; ++w) s += colacc[w * MS_BLK + k];
+        for (int w = 0; w < MS_WARPS; ++w) s += colacc[w * BLK + k];
         out_cols[cnode[k]] = s;
     }
 }
@@ -1090,10 +1093,10 @@ static cudaError_t set_sym_attr() {
                                 (int)ms_smem_bytes(BLK));
 }
 
-template <int R, int M>
+template <int R, int M, int BLK>
 static cudaError_t set_adj_attr() {
-    return cudaFuncSetAttribute(adj_sym_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(AS_SMEM_FLOATS * sizeof(float)));
+    return cudaFuncSetAttribute(adj_sym_kernel<R, M, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(as_smem_floats(BLK) * sizeof(float)));
 }
 
 // The attributes belong to the device's context: set once per device (under a lock, so that
@@ -1114,14 +1117,22 @@ nf_status mf_init_attrs() {
 
 static nf_status mf_init_attrs_device() {
     NF_TRY(dense_init_attrs());
-    NF_CUDA_TRY((set_adj_attr<4, 0>()));
-    NF_CUDA_TRY((set_adj_attr<4, 2>()));
-    NF_CUDA_TRY((set_adj_attr<4, 3>()));
-    NF_CUDA_TRY((set_adj_attr<4, 4>()));
-    NF_CUDA_TRY((set_adj_attr<8, 0>()));
-    NF_CUDA_TRY((set_adj_attr<8, 2>()));
-    NF_CUDA_TRY((set_adj_attr<8, 3>()));
-    NF_CUDA_TRY((set_adj_attr<8, 4>()));
+    NF_CUDA_TRY((set_adj_attr<4, 0, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<4, 2, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<4, 3, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<4, 4, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<8, 0, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<8, 2, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<8, 3, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<8, 4, 1024>()));
+    NF_CUDA_TRY((set_adj_attr<4, 0, 512>()));
+    NF_CUDA_TRY((set_adj_attr<4, 2, 512>()));
+    NF_CUDA_TRY((set_adj_attr<4, 3, 512>()));
+    NF_CUDA_TRY((set_adj_attr<4, 4, 512>()));
+    NF_CUDA_TRY((set_adj_attr<8, 0, 512>()));
+    NF_CUDA_TRY((set_adj_attr<8, 2, 512>()));
+    NF_CUDA_TRY((set_adj_attr<8, 3, 512>()));
+    NF_CUDA_TRY((set_adj_attr<8, 4, 512>()));
     NF_CUDA_TRY((set_sym_attr<4, 0>()));
     NF_CUDA_TRY((set_sym_attr<4, 1>()));
     NF_CUDA_TRY((set_sym_attr<8, 1>()));
@@ -1300,8 +1311,21 @@ static nf_status launch_sym(nf_operator *op, int B, int b_base, cudaStream_t s) 
 // Adjoint pair sums of trajectory b over all 1,024-node block pairs (see adj_sym_kernel):
 // W nu slots into wpart [n_pad / 1024][B][n_pad], parameter sums into gpart [B][pairs][4]
 // with r^2 in exponent units; *r2_phys receives the factor to physical r^2.
-int64_t sym_pair_count(const nf_operator *op) { return sym_pairs_1024(op); }
-int adj_slots(const nf_operator *op) { return (int)(op->n_pad / MS_BLK); }
+// The adjoint kernel's node block: the tuned one, or 1,024 when culling (its live-pair lists
+// are built over 1,024-node blocks).
+static int adj_block(const nf_operator *op) {
+    return (op->mf_cull && op->adj_pairs) || op->adj_blk == 0 ? MS_BLK : op->adj_blk;
+}
+int64_t sym_pair_count(const nf_operator *op) {
+    const int64_t nb = op->n_pad / adj_block(op);
+    return nb * (nb + 1) / 2;
+}
+int adj_slots(const nf_operator *op) { return (int)(op->n_pad / adj_block(op)); }
+int64_t adj_pair_capacity(const nf_operator *op) {
+    const int64_t nb = op->n_pad / 512;
+    return nb * (nb + 1) / 2;
+}
+int adj_slot_capacity(const nf_operator *op) { return (int)(op->n_pad / 512); }
 int sym_slots(const nf_operator *op) { return (int)(op->n_pad / op->sym_blk); }
 
 // Up to kSymMaxB trajectories take the symmetric kernel, one launch with a grid z per
@@ -1346,38 +1370,65 @@ nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float 
     const double L2E = 1.4426950408889634;
     *r2_phys = (float)((m > 0 ? (double)k.s2 * k.s2 : (double)k.s1 * k.s1) / L2E);
     const bool cull = op->mf_cull && op->adj_pairs;
-    dim3 grid((unsigned)(cull ? op->adj_live : sym_pairs_1024(op)), 1, 1);
-    const size_t smem = AS_SMEM_FLOATS * sizeof(float);
+    const int blk = adj_block(op);
+    dim3 grid((unsigned)(cull ? op->adj_live : sym_pair_count(op)), 1, 1);
+    const size_t smem = as_smem_floats(blk) * sizeof(float);
 #define NF_ADJ_ARGS                                                                                       \
     op->xyz, vg, op->rowperm, op->n_pad, B, b, k2, k.A1, k.A2, scaled_period(k), wpart, gpart, \
         (cull ? op->adj_pairs : nullptr)
-    if (op->adj_r == 8) {
-        switch (m) {
-            case 2: adj_sym_kernel<8, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-            case 3: adj_sym_kernel<8, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-            case 4: adj_sym_kernel<8, 4><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-            default: adj_sym_kernel<8, 0><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+#define NF_ADJ_LAUNCH(RR, BB)                                                                     \
+    switch (m) {                                                                                  \
+        case 2: adj_sym_kernel<RR, 2, BB><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;     \
+        case 3: adj_sym_kernel<RR, 3, BB><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;     \
+        case 4: adj_sym_kernel<RR, 4, BB><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;     \
+        default: adj_sym_kernel<RR, 0, BB><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;    \
+    }
+    if (blk == 512) {
+        if (op->adj_r == 8) {
+            NF_ADJ_LAUNCH(8, 512)
+        } else {
+            NF_ADJ_LAUNCH(4, 512)
         }
     } else {
-        switch (m) {
-            case 2: adj_sym_kernel<4, 2><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-            case 3: adj_sym_kernel<4, 3><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-            case 4: adj_sym_kernel<4, 4><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
-            default: adj_sym_kernel<4, 0><<<grid, MS_THREADS, smem, s>>>(NF_ADJ_ARGS); break;
+        if (op->adj_r == 8) {
+            NF_ADJ_LAUNCH(8, 1024)
+        } else {
+            NF_ADJ_LAUNCH(4, 1024)
         }
     }
+#undef NF_ADJ_LAUNCH
 #undef NF_ADJ_ARGS
     NF_CUDA_TRY(cudaGetLastError());
     return NF_OK;
 }
 
-// Rows per warp of the adjoint pair kernel, chosen once per operator by timing both shapes
-// (4 rows, two CTAs per SM; 8 rows, one CTA per SM) on the operator's own node set: three
-// launches each, each between its own events; the fastest of the last two counts.  The
-// launches write the call's scratch buffers only, before the call's own passes overwrite
-// them.
+// Shape of the adjoint pair kernel -- rows per warp (4: two CTAs per SM; 8: one CTA per SM)
+// and node block (1,024, or 512 where the 1,024-node block pairs fill fewer than eight waves
+// of CTAs) -- chosen by timing the candidates on the operator's own node set: three launches
+// each, each between its own events; the fastest of the last two counts.  The launches write
+// the call's scratch buffers only (sized for 512-node blocks), before the call's own passes
+// overwrite them.
 nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, float *gpart, cudaStream_t s) {
     if (op->adj_r) return NF_OK;
+    // 512-node blocks only on the automatic schedule without culling: an explicit symmetric
+    // schedule pins the block size, and the culled pass's live-pair lists use 1,024-node
+    // blocks.  The choice is cached per (device, node count, kernel form, whether 512 is
+    // allowed), so operators on the same node set run the same shape (culled and unculled
+    // gradients then agree bit for bit).
+    static std::mutex mu;
+    static std::map<std::tuple<int, int64_t, int, bool>, std::pair<int, int>> cache;
+    const bool cull = op->mf_cull && op->adj_pairs;
+    const bool try512 = !cull && op->mf_sched == NF_MF_AUTO && sym_pairs_1024(op) < 8 * (int64_t)num_sms();
+    const auto key = std::make_tuple(op->device, op->n_pad, mf_width_ratio(op->kp), try512);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            op->adj_r = it->second.first;
+            op->adj_blk = it->second.second;
+            return NF_OK;
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     NF_CUDA_TRY(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -1385,13 +1436,14 @@ nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, f
         cudaEventDestroy(e0);
         return cuda_fail(ce, "cudaEventCreate", __FILE__, __LINE__);
     }
-    const int cand[2] = {4, 8};
+    const int cand_r[4] = {4, 8, 4, 8}, cand_b[4] = {1024, 1024, 512, 512};
     float best = 3.4e38f;
-    int best_r = 4;
+    int best_r = 4, best_b = 1024;
     nf_status st = NF_OK;
     float r2 = 1.f;
-    for (int c = 0; c < 2 && st == NF_OK; ++c) {
-        op->adj_r = cand[c];
+    for (int c = 0; c < (try512 ? 4 : 2) && st == NF_OK; ++c) {
+        op->adj_r = cand_r[c];
+        op->adj_blk = cand_b[c];
         for (int rep = 0; rep < 3 && st == NF_OK; ++rep) {
             ce = cudaEventRecord(e0, s);
             if (ce == cudaSuccess) st = launch_adj_sym(op, vg, B, 0, wpart, gpart, &r2, s);
@@ -1402,13 +1454,19 @@ nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, f
             if (ce != cudaSuccess && st == NF_OK) st = cuda_fail(ce, "adjoint autotune", __FILE__, __LINE__);
             if (st == NF_OK && rep >= 1 && ms < best) {  // the first launch warms up
                 best = ms;
-                best_r = cand[c];
+                best_r = cand_r[c];
+                best_b = cand_b[c];
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     op->adj_r = st == NF_OK ? best_r : 0;
+    op->adj_blk = st == NF_OK ? best_b : 0;
+    if (st == NF_OK) {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[key] = {best_r, best_b};
+    }
     return st;
 }
 
@@ -1467,9 +1525,9 @@ nf_status mf_autotune(nf_operator *op, cudaStream_t s) {
     float best = 1e30f;
     int best_r = 8, best_blk = 1024;
     // (rows per warp, block size): 512-node blocks only where 1,024-node pairs fill fewer than
-    // two waves of two CTAs per SM (n below ~35,000); measured on GB300 they win there (n =
-    // 20,000: 0.177 vs 0.198 ms) and lose badly on large sets (n = 1e5: 7.2 vs 1.8 ms)
-    const bool try512 = sym_pairs_1024(op) < 4 * (int64_t)num_sms();
+    // four waves of two CTAs per SM (n below ~49,000); measured on GB300 they win on small
+    // sets (n = 20,000: 0.177 vs 0.198 ms) and lose badly on large ones (n = 1e5: 7.2 vs 1.8 ms)
+    const bool try512 = sym_pairs_1024(op) < 8 * (int64_t)num_sms();
     NF_TRY(ensure_workspace(op, 1, (int)(op->n_pad / (try512 ? 512 : MS_BLK))));
     NF_CUDA_TRY(cudaMemsetAsync(op->g, 0, sizeof(float) * op->n_pad, s));
     const std::pair<int, int> shapes[3] = {{4, 1024}, {8, 1024}, {8, 512}};
