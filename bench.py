@@ -792,7 +792,7 @@ def probe_pipes(dev):
 
     out = {}
     for name, kind, iters in (("fma_f32", nf.PROBE_FMA, 100000), ("fma_f32x2", nf.PROBE_FMA2, 100000),
-                              ("ex2", nf.PROBE_EX2, 20000)):
+                              ("ex2", nf.PROBE_EX2, 20000), ("fma_f32x2_outer", nf.PROBE_FMA2_OUTER, 100000)):
         nf.nf_probe_pipe(kind, 1000)  # warm-up
         rate, mhz, ms = nf.nf_probe_pipe(kind, iters)
         out[name] = {"per_clk_per_sm": rate, "sm_mhz": mhz, "ms": ms}
@@ -926,6 +926,8 @@ def run_ours(args, rank, world, local_rank):
         lanes = pipes["fma_f32x2"]["per_clk_per_sm"]
         ex2 = pipes["ex2"]["per_clk_per_sm"]
         fma_peak = sms * lanes * mhz * 1e6 / ops / 1e9                      # Gpair/s on the FP32 FMA pipe
+        lanes_gen = pipes["fma_f32x2_outer"]["per_clk_per_sm"]  # packed FMAs with varied operands
+        fma_peak_gen = sms * lanes_gen * mhz * 1e6 / ops / 1e9
         sfu_peak = sms * ex2 * mhz * 1e6 / (EX2_PER_PAIR * (1.0 + 1.0 / nb)) / 1e9  # Gpair/s on the SFU
         peak = min(fma_peak, sfu_peak)
         achieved = n * n / (kms * 1e-3) / 1e9
@@ -937,6 +939,7 @@ def run_ours(args, rank, world, local_rank):
                               f"SFU ceiling {sfu_peak:.0f} Gpair/s from {ex2:.1f} ex2/clk/SM measured and "
                               f"{EX2_PER_PAIR} exponentials per ordered pair",
                 "fma_pipe_peak": fma_peak, "sfu_peak": sfu_peak,
+                "fma_pipe_peak_varied_operands": fma_peak_gen, "frac_vs_varied_operands": achieved / fma_peak_gen,
                 "nominal_peak_128_lanes": sms * FMA_LANES_PER_CLK_SM_NOMINAL * mhz * 1e6 / ops / 1e9}
     else:
         bytes_per = 4.0 * n * n

@@ -176,6 +176,15 @@ NF_API nf_status nf_operator_group(nf_operator *const *ops, const int *B_per_op,
 NF_API nf_status nf_operator_group_tuning(nf_operator *op, int *ring_depth, int *traj_split, double *lpt_coef,
                                           int *subgroups, float *ms);
 
+/* Set the launch configuration of a grouped operator instead of the autotuner's choice (no
+ * paper counterpart; for reproducible measurements and for testing every candidate):
+ * ring_depth 2 or 3, traj_split 1 or 2, lpt_coef > 0.  Synchronises `stream`, drops captured
+ * RK4 steps (the next nf_rk4_advance captures again).  Results do not depend on the
+ * configuration.  Errors: NF_ERR_ARG, NF_ERR_UNSUPPORTED (the split needs more than 8
+ * sub-groups), NF_ERR_CUDA. */
+NF_API nf_status nf_operator_group_configure(nf_operator *op, int ring_depth, int traj_split, double lpt_coef,
+                                             void *stream);
+
 /* Synchronise `stream` and report device-side failures recorded on the operator:
  * NF_ERR_TIMEOUT when a bounded wait in a kernel gave up; NF_ERR_NONFINITE when a step of
  * nf_rk4_advance on the matrix-free or a dense path left a non-finite value (NaN or
@@ -252,6 +261,8 @@ NF_API nf_status nf_selftest_timeout(void *stream);
  *   kind 0: fma.rn.f32        (1 FP32 FMA-pipe lane operation per instruction)
  *   kind 1: fma.rn.f32x2      (2 lane operations per instruction)
  *   kind 2: ex2.approx.ftz.f32 (1 SFU operation)
+ *   kind 3: fma.rn.f32x2 as a 4 x 2 outer product (8 accumulators, a different pair of
+ *           operand registers in every instruction, as in a register-tiled GEMM)
  * `iters` times 64 per thread, timed by each SM's cycle counter.  Host outputs: the median
  * over SMs of operations per clock per SM, the SM clock (MHz) implied by the slowest SM's
  * cycles over the launch's wall time, and that wall time in ms.  Synchronises `stream`;

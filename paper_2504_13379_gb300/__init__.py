@@ -49,7 +49,7 @@ EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights"
            "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout",
            "nf_operator_mf_schedule", "nf_operator_mf_cull", "nf_field_advance", "nf_noalloc_status",
            "nf_noalloc_limits", "nf_selftest_noalloc_flag", "nf_operator_kernel_ms_history",
-           "nf_probe_pipe", "nf_operator_group_tuning"]
+           "nf_probe_pipe", "nf_operator_group_tuning", "nf_operator_group_configure"]
 
 
 class NFError(RuntimeError):
@@ -104,6 +104,7 @@ def lib(path: str | None = None):
     L.nf_operator_group.argtypes = [C.POINTER(_vp), C.POINTER(C.c_int), C.c_int, _vp, C.POINTER(_vp)]
     L.nf_operator_group_tuning.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                            C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    L.nf_operator_group_configure.argtypes = [_vp, C.c_int, C.c_int, C.c_double, _vp]
     L.nf_operator_check.argtypes = [_vp, _vp]
     L.nf_operator_profile.argtypes = [_vp, C.c_int]
     L.nf_operator_kernel_ms.argtypes = [_vp, C.POINTER(C.c_float)]
@@ -311,6 +312,12 @@ class GroupedOperator(Operator):
         return {"ring_depth": d.value, "traj_split": sp.value, "lpt_coef": c.value, "subgroups": g.value,
                 "ms_per_launch": ms.value}
 
+    def configure(self, ring_depth: int, traj_split: int, lpt_coef: float):
+        """Set the launch configuration instead of the autotuner's choice."""
+        _check(lib().nf_operator_group_configure(self.handle, int(ring_depth), int(traj_split), float(lpt_coef),
+                                                 _stream()))
+        return self
+
     def split(self, flat: torch.Tensor):
         """View a concatenated state as the list of per-member (B_g x n_g) blocks."""
         out, off = [], 0
@@ -384,12 +391,13 @@ def nf_selftest_noalloc_flag(out: torch.Tensor):
     return out
 
 
-PROBE_FMA, PROBE_FMA2, PROBE_EX2 = 0, 1, 2
+PROBE_FMA, PROBE_FMA2, PROBE_EX2, PROBE_FMA2_OUTER = 0, 1, 2, 3
 
 
 def nf_probe_pipe(kind: int, iters: int = 20000):
     """Measured rate of one instruction kind on every SM (PROBE_FMA: fma.rn.f32 lane
-    operations, PROBE_FMA2: fma.rn.f32x2 lane operations, PROBE_EX2: SFU ex2): returns
+    operations, PROBE_FMA2: fma.rn.f32x2 lane operations, PROBE_EX2: SFU ex2,
+    PROBE_FMA2_OUTER: fma.rn.f32x2 as an outer product with distinct operands): returns
     (operations per clock per SM, SM MHz during the probe, wall ms)."""
     r, mhz, ms = C.c_double(), C.c_double(), C.c_float()
     _check(lib().nf_probe_pipe(int(kind), int(iters), C.byref(r), C.byref(mhz), C.byref(ms), _stream()))

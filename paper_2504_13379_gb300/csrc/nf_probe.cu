@@ -42,7 +42,10 @@ __device__ __forceinline__ float p_ex2(float a) {
 }
 
 // kind 0: fma.rn.f32 (1 lane operation each), kind 1: fma.rn.f32x2 (2 lane operations),
-// kind 2: ex2.approx.ftz.f32 (1 SFU operation).  cyc[blockIdx.x] = cycles of the chains.
+// kind 2: ex2.approx.ftz.f32 (1 SFU operation), kind 3: fma.rn.f32x2 as a 4 x 2 outer
+// product (8 accumulators against 4 + 2 operand registers, a different pair of operand
+// registers in every instruction, as in a register-tiled GEMM; 2 lane operations each).
+// cyc[blockIdx.x] = cycles of the chains.
 // The FMA chains contract towards a fixed point (multiplier 0.999) and the ex2 chain maps
 // [-1, 1] into itself, so every value stays finite; sink receives their sum only under a
 // condition the compiler cannot rule out, so no chain is removed.
@@ -58,6 +61,12 @@ __global__ void __launch_bounds__(PR_THREADS, 1) probe_kernel(long long iters, l
     }
     const float m = 0.999f, k = 1e-4f;
     const u64p mp = p_pack(m, m), kp = p_pack(k, k);
+    // outer-product operands (small, so the accumulators grow slowly and stay finite)
+    u64p opa[PR_CHAINS / 2], opb[2];
+#pragma unroll
+    for (int c = 0; c < PR_CHAINS / 2; ++c) opa[c] = p_pack(1e-7f * (c + 1), 2e-7f * (c + 1) + seed * 1e-6f);
+    opb[0] = p_pack(0.5f, 0.25f);
+    opb[1] = p_pack(0.125f, 0.75f);
     __syncthreads();
     long long t0 = 0;
     if (threadIdx.x == 0) t0 = clock64();
@@ -69,6 +78,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1) probe_kernel(long long iters, l
             for (int c = 0; c < PR_CHAINS; ++c) {
                 if constexpr (KIND == 0) a[c] = p_fma(a[c], m, k);
                 else if constexpr (KIND == 1) p[c] = p_fma2(p[c], mp, kp);
+                else if constexpr (KIND == 3) p[c] = p_fma2(opa[c >> 1], opb[c & 1], p[c]);
                 else a[c] = p_ex2(-a[c]) - 1.0f;  // stays in [-1, 1]: one SFU op + one add
             }
         }
@@ -93,7 +103,8 @@ extern "C" nf_status nf_probe_pipe(int kind, int64_t iters, double *ops_per_clk_
                                    void *stream) {
     clear_error();
     NF_ARG(ops_per_clk_sm && sm_mhz && ms, "outputs must be non-NULL");
-    NF_ARG(kind >= 0 && kind <= 2, "kind = %d must be 0 (fma.f32), 1 (fma.f32x2) or 2 (ex2)", kind);
+    NF_ARG(kind >= 0 && kind <= 3, "kind = %d must be 0 (fma.f32), 1 (fma.f32x2), 2 (ex2) or 3 (f32x2 outer product)",
+           kind);
     NF_ARG(iters >= 1 && iters <= (int64_t)1 << 24, "iters out of range");
     cudaStream_t s = as_stream(stream);
     const int grid = num_sms();
@@ -108,7 +119,8 @@ extern "C" nf_status nf_probe_pipe(int kind, int64_t iters, double *ops_per_clk_
     if (e == cudaSuccess) {
         if (kind == 0) probe_kernel<0><<<grid, PR_THREADS, 0, s>>>(iters, cyc, sink);
         else if (kind == 1) probe_kernel<1><<<grid, PR_THREADS, 0, s>>>(iters, cyc, sink);
-        else probe_kernel<2><<<grid, PR_THREADS, 0, s>>>(iters, cyc, sink);
+        else if (kind == 2) probe_kernel<2><<<grid, PR_THREADS, 0, s>>>(iters, cyc, sink);
+        else probe_kernel<3><<<grid, PR_THREADS, 0, s>>>(iters, cyc, sink);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
@@ -121,7 +133,7 @@ extern "C" nf_status nf_probe_pipe(int kind, int64_t iters, double *ops_per_clk_
     cudaFreeAsync(cyc, s);
     if (e != cudaSuccess) return cuda_fail(e, "probe launch", __FILE__, __LINE__);
     // operations per CTA: threads x chains x unroll x iterations (x 2 lanes for f32x2)
-    const double ops = (double)PR_THREADS * PR_CHAINS * PR_UNROLL * (double)iters * (kind == 1 ? 2.0 : 1.0);
+    const double ops = (double)PR_THREADS * PR_CHAINS * PR_UNROLL * (double)iters * (kind == 1 || kind == 3 ? 2.0 : 1.0);
     std::vector<double> rate(grid);
     long long cmax = 1;
     for (int i = 0; i < grid; ++i) {

@@ -39,6 +39,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -939,6 +940,27 @@ extern "C" nf_status nf_operator_group(nf_operator *const *ops, const int *B_per
     if (st != NF_OK) return cleanup(st);
     *grouped = op;
     return NF_OK;
+}
+
+extern "C" nf_status nf_operator_group_configure(nf_operator *op, int ring_depth, int traj_split, double lpt_coef,
+                                                 void *stream) {
+    clear_error();
+    NF_ARG(op && op->path == NF_GROUPED && op->group, "not a grouped operator");
+    NF_ARG(ring_depth == 2 || ring_depth == 3, "ring_depth = %d must be 2 or 3", ring_depth);
+    NF_ARG(traj_split == 1 || traj_split == 2, "traj_split = %d must be 1 or 2", traj_split);
+    NF_ARG(std::isfinite(lpt_coef) && lpt_coef > 0.0, "lpt_coef must be finite and > 0");
+    nf_group_state *gs = op->group;
+    cudaStream_t s = as_stream(stream);
+    NF_CUDA_TRY(cudaStreamSynchronize(s));  // no launch may still use the current parameters
+    if (!make_subgroups(gs, traj_split))
+        return fail(NF_ERR_UNSUPPORTED, "traj_split = %d needs more than %d sub-groups", traj_split, TC_MAXG);
+    destroy_graphs(op);  // captured steps hold the old parameters
+    gs->split = traj_split;
+    gs->nst = ring_depth;
+    gs->lpt_coef = lpt_coef;
+    gs->tuned_ms = 0.f;
+    NF_TRY(build_group_params(op));
+    return build_schedule(op, lpt_coef, s);
 }
 
 extern "C" nf_status nf_operator_group_tuning(nf_operator *op, int *ring_depth, int *traj_split, double *lpt_coef,

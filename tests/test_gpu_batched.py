@@ -176,3 +176,44 @@ def test_group_limits(nf):
         nf.GroupedOperator([op, op], [1800, 300])   # 8 + 2 sub-groups
     assert ei.value.name == "NF_ERR_UNSUPPORTED"
     op.close()
+
+
+def test_grouped_every_configuration_matches(nf):
+    """Every launch configuration the autotuner chooses from (ring depth 2 or 3, a member of
+    128+ trajectories whole or in two, LPT weights 4 / 8 / 12) gives sums within the oracle's
+    bar, and the same sums: ring depth and schedule only reorder work, the split only the
+    tile a column belongs to."""
+    specs = [(2100, 160, 31), (1300, 24, 32), (900, 64, 33)]
+    kern = (1.0, 0.1, 0.5, 0.2)
+    data, ops = _members(nf, specs, kern)
+    grp = nf.GroupedOperator(ops, [s[1] for s in specs])
+    u = torch.cat([dev(d[3]).reshape(-1) for d in data])
+    beta = torch.cat([dev(d[4]) for d in data])
+    theta = torch.cat([dev(d[5]) for d in data])
+    wants = [oracle.nonlocal_sum(f32(X), f32(q), f32(u0), f32(kern), f32(be), f32(th))
+             for (ns, X, q, u0, be, th) in data]
+    ref = None
+    for depth in (3, 2):
+        for split in (1, 2):
+            for coef in (4.0, 8.0, 12.0):
+                grp.configure(depth, split, coef)
+                t = grp.tuning()
+                assert (t["ring_depth"], t["traj_split"], t["lpt_coef"]) == (depth, split, coef)
+                I = nf.nf_nonlocal_apply(grp, u, beta, theta)
+                u2 = u.clone()
+                nf.nf_rk4_advance(grp, u2, 0.0, 0.05, 2, beta, theta)
+                grp.check()
+                for got, want in zip(grp.split(I), wants):
+                    err = np.linalg.norm(got.cpu().numpy() - want, axis=1) / np.linalg.norm(want, axis=1)
+                    assert err.max() < REL_L2, (depth, split, coef, err.max())
+                cur = (I.cpu().numpy(), u2.cpu().numpy())
+                if ref is None:
+                    ref = cur
+                else:
+                    np.testing.assert_allclose(cur[0], ref[0], rtol=1e-6, atol=1e-7 * np.abs(ref[0]).max())
+                    np.testing.assert_allclose(cur[1], ref[1], rtol=1e-6, atol=1e-7 * np.abs(ref[1]).max())
+    with pytest.raises(nf.NFError):
+        grp.configure(4, 1, 8.0)
+    grp.close()
+    for op in ops:
+        op.close()
