@@ -74,6 +74,13 @@ NF_API nf_status nf_build_stencils(const double *nodes, int64_t n, int dim,
                             const int32_t *tris, int64_t m, int k,
                             int32_t *stencils, void *stream);
 
+/* The same selection around m caller-given centres (m x dim FP64 device array) instead of
+ * triangle centroids: row e lists the k nodes nearest to centers[e], ascending (distance^2,
+ * index).  Centres may lie anywhere (the search grid covers nodes and centres).
+ * Errors: NF_ERR_ARG (sizes, k, non-finite coordinates), NF_ERR_CUDA. */
+NF_API nf_status nf_build_stencils_at(const double *nodes, int64_t n, int dim, const double *centers, int64_t m,
+                                      int k, int32_t *stencils, void *stream);
+
 /* ------------------------------------------------------------------------------
  * §3.2 Eq. (3.5) (flat, dim = 2) and §3.3 Eq. (3.6) (closed surfaces, dim = 3):
  * RBF quadrature weights mu (written q here).  Per element: polyharmonic spline
@@ -99,6 +106,20 @@ NF_API nf_status nf_build_stencils(const double *nodes, int64_t n, int dim,
 NF_API nf_status nf_quad_weights(const double *nodes, const double *normals, int64_t n, int dim,
                           const int32_t *tris, int64_t m, const int32_t *stencils, int k,
                           int deg, double *q, int64_t *bad_element, void *stream);
+
+/* The same call with the options gathered in a struct: dim (2 flat, 3 surface), phs_order
+ * (the polyharmonic spline r^phs_order of Eq. (3.3); 3 is what is implemented, others
+ * return NF_ERR_UNSUPPORTED), poly_deg (0..4), curved (1: closed surface, normals required;
+ * must agree with dim).  o is a host pointer.  Errors as nf_quad_weights. */
+typedef struct {
+    int dim;
+    int phs_order;
+    int poly_deg;
+    int curved;
+} nf_quad_opts;
+NF_API nf_status nf_quad_weights_opts(const double *nodes, const double *normals, int64_t n, const int32_t *tris,
+                                      int64_t m, const int32_t *stencils, int k, const nf_quad_opts *o, double *q,
+                                      int64_t *bad_element, void *stream);
 
 /* ------------------------------------------------------------------------------
  * Kernel and operator.
@@ -339,7 +360,12 @@ NF_API nf_status nf_selftest_noalloc_flag(int64_t n, float *I, void *stream);
  *    the integral in closed form (w and G are products of one-dimensional Gaussians; each
  *    factor splits where the nearest image of x0 changes and integrates with erf).
  *    Fields used: c, radius, sigma, scale; Y1, Y2 unused. */
-enum { NF_FORCE_NONE = 0, NF_FORCE_MMS_EIGEN = 1, NF_FORCE_MMS_FLAT = 2 };
+/*  NF_FORCE_MMS_SPHERE: the NF_FORCE_MMS_EIGEN form on the unit sphere with the library
+ *    supplying what the caller would: Y1 = z/2 and Y2 = x y at the operator's nodes, and the
+ *    eigenvalues lam0, lam1, lam2 of the operator's kernel (nf_mms_sphere_eigs).  Fields
+ *    used: c, a0 (0 < c -+ 1.5 |a0| < 1, so that z stays in (0, 1)).  Euclidean (chord)
+ *    distance only; nf_adjoint refuses it (the eigenvalues depend on the kernel). */
+enum { NF_FORCE_NONE = 0, NF_FORCE_MMS_EIGEN = 1, NF_FORCE_MMS_FLAT = 2, NF_FORCE_MMS_SPHERE = 3 };
 typedef struct {
     int kind;
     const float *Y1;

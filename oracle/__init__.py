@@ -42,6 +42,7 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         L.or_knn.argtypes = [_dp, C.c_int64, C.c_int, _ip, C.c_int64, _lp, C.c_int64, C.c_int, _ip]
+        L.or_knn_at.argtypes = [_dp, C.c_int64, C.c_int, _dp, C.c_int64, C.c_int, _ip]
         L.or_tri_r3.argtypes = [_dp, _dp]
         L.or_tri_r3.restype = C.c_double
         L.or_tri_mono.argtypes = [C.c_int, C.c_int, _dp]
@@ -124,6 +125,19 @@ def knn(nodes, tris, k, elems=None):
     rc = lib().or_knn(pn, n, dim, pt, m, pe, ne, k, out.ctypes.data_as(_ip))
     if rc != 0:
         raise ValueError("or_knn: bad arguments")
+    return out
+
+
+def knn_at(nodes, centers, k):
+    """The k nodes nearest to each of the given centres (m x dim), ordered by (squared
+    distance, index) ascending: the selection of §3.1 around arbitrary points."""
+    nodes, pn = _d(nodes)
+    n, dim = nodes.shape
+    centers, pc = _d(centers)
+    m = centers.shape[0]
+    out = np.empty((m, k), dtype=np.int32)
+    if lib().or_knn_at(pn, n, dim, pc, m, k, out.ctypes.data_as(_ip)) != 0:
+        raise ValueError("or_knn_at: bad arguments")
     return out
 
 

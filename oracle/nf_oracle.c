@@ -86,6 +86,28 @@ static double dist2(const double *x, const double *c, int dim) {
     return s;
 }
 
+/* The k nodes nearest to the point c, in ascending (distance^2, index): every node is
+ * compared with the current k-th entry and inserted in order (a full scan). */
+static void knn_point(const double *nodes, int64_t n, int dim, const double *c, int k, int32_t *out) {
+    double bd[OR_MAXK];
+    int32_t bi[OR_MAXK];
+    int cnt = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        double d2 = dist2(nodes + j * dim, c, dim);
+        if (cnt == k && !(d2 < bd[k - 1] || (d2 == bd[k - 1] && j < bi[k - 1]))) continue;
+        int pos = (cnt < k) ? cnt : k - 1;
+        while (pos > 0 && (d2 < bd[pos - 1] || (d2 == bd[pos - 1] && j < bi[pos - 1]))) {
+            bd[pos] = bd[pos - 1];
+            bi[pos] = bi[pos - 1];
+            --pos;
+        }
+        bd[pos] = d2;
+        bi[pos] = (int32_t)j;
+        if (cnt < k) ++cnt;
+    }
+    memcpy(out, bi, sizeof(int32_t) * k);
+}
+
 /* elems == NULL: all m elements, output row t = element t.
  * Otherwise: output row t = element elems[t]. */
 int or_knn(const double *nodes, int64_t n, int dim, const int32_t *tris, int64_t m,
@@ -103,25 +125,17 @@ int or_knn(const double *nodes, int64_t n, int dim, const int32_t *tris, int64_t
         }
         double c[3];
         element_centroid(nodes, dim, tris + 3 * e, c);
-        double bd[OR_MAXK];
-        int32_t bi[OR_MAXK];
-        int cnt = 0;
-        for (int64_t j = 0; j < n; ++j) {
-            double d2 = dist2(nodes + j * dim, c, dim);
-            if (cnt == k && !(d2 < bd[k - 1] || (d2 == bd[k - 1] && j < bi[k - 1]))) continue;
-            int pos = (cnt < k) ? cnt : k - 1;
-            while (pos > 0 && (d2 < bd[pos - 1] || (d2 == bd[pos - 1] && j < bi[pos - 1]))) {
-                bd[pos] = bd[pos - 1];
-                bi[pos] = bi[pos - 1];
-                --pos;
-            }
-            bd[pos] = d2;
-            bi[pos] = (int32_t)j;
-            if (cnt < k) ++cnt;
-        }
-        memcpy(stencils + t * k, bi, sizeof(int32_t) * k);
+        knn_point(nodes, n, dim, c, k, stencils + t * k);
     }
     return bad ? -1 : 0;
+}
+
+/* The same selection around m given centres (m x dim), one output row per centre. */
+int or_knn_at(const double *nodes, int64_t n, int dim, const double *centers, int64_t m, int k, int32_t *stencils) {
+    if (k < 1 || k > n || k > OR_MAXK || (dim != 2 && dim != 3)) return -1;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t t = 0; t < m; ++t) knn_point(nodes, n, dim, centers + t * dim, k, stencils + t * k);
+    return 0;
 }
 
 /* ================================================================================

@@ -32,12 +32,13 @@ __all__ = [
     "NFError", "lib", "build", "nf_build_stencils", "nf_quad_weights", "Operator", "nf_nonlocal_apply",
     "nf_rk4_advance", "nf_adjoint", "nf_mms_sphere_eigs", "Forcing", "MATRIX_FREE", "DENSE_FP32",
     "DENSE_BF16X2", "DENSE_SYM_FP32", "DENSE_SYM_BF16X2", "STATUS", "nf_field_advance", "MODEL_FIELD", "MODEL_DEPRESSION",
-    "RATE_SIGMOID", "RATE_SMOOTHSTEP", "FORCE_NONE", "FORCE_MMS_EIGEN", "FORCE_MMS_FLAT", "NeuralFieldRK4",
+    "RATE_SIGMOID", "RATE_SMOOTHSTEP", "FORCE_NONE", "FORCE_MMS_EIGEN", "FORCE_MMS_FLAT", "FORCE_MMS_SPHERE",
+    "NeuralFieldRK4", "nf_build_stencils_at",
     "MF_AUTO", "MF_SYMMETRIC", "MF_PACKED", "MF_SYMMETRIC_512", "MF_SYMMETRIC_1024",
 ]
 
 MATRIX_FREE, DENSE_FP32, DENSE_BF16X2, DENSE_SYM_FP32, DENSE_SYM_BF16X2 = 0, 1, 2, 4, 5
-FORCE_NONE, FORCE_MMS_EIGEN, FORCE_MMS_FLAT = 0, 1, 2
+FORCE_NONE, FORCE_MMS_EIGEN, FORCE_MMS_FLAT, FORCE_MMS_SPHERE = 0, 1, 2, 3
 MF_AUTO, MF_SYMMETRIC, MF_PACKED, MF_SYMMETRIC_512, MF_SYMMETRIC_1024 = 0, 1, 2, 3, 4
 STATUS = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_SINGULAR", 3: "NF_ERR_NONFINITE", 4: "NF_ERR_TIMEOUT",
           5: "NF_ERR_NOMEM", 6: "NF_ERR_CUDA", 7: "NF_ERR_UNSUPPORTED"}
@@ -49,7 +50,8 @@ EXPORTS = ["nf_last_error", "nf_version", "nf_build_stencils", "nf_quad_weights"
            "nf_nonlocal_apply_noalloc", "nf_operator_group", "nf_operator_launch_shape", "nf_selftest_timeout",
            "nf_operator_mf_schedule", "nf_operator_mf_cull", "nf_field_advance", "nf_noalloc_status",
            "nf_noalloc_limits", "nf_selftest_noalloc_flag", "nf_operator_kernel_ms_history",
-           "nf_probe_pipe", "nf_operator_group_tuning", "nf_operator_group_configure"]
+           "nf_probe_pipe", "nf_operator_group_tuning", "nf_operator_group_configure", "nf_build_stencils_at",
+           "nf_quad_weights_opts"]
 
 
 class NFError(RuntimeError):
@@ -66,6 +68,10 @@ class _Kernel(C.Structure):
 class _Model(C.Structure):
     _fields_ = [("kind", C.c_int), ("rate", C.c_int), ("a", C.c_float), ("b", C.c_float), ("tau", C.c_float),
                 ("beta_d", C.c_float)]
+
+
+class _QuadOpts(C.Structure):
+    _fields_ = [("dim", C.c_int), ("phs_order", C.c_int), ("poly_deg", C.c_int), ("curved", C.c_int)]
 
 
 class _Forcing(C.Structure):
@@ -97,6 +103,9 @@ def lib(path: str | None = None):
     for name in EXPORTS[2:]:
         getattr(L, name).restype = C.c_int
     L.nf_build_stencils.argtypes = [_vp, _i64, C.c_int, _vp, _i64, C.c_int, _vp, _vp]
+    L.nf_build_stencils_at.argtypes = [_vp, _i64, C.c_int, _vp, _i64, C.c_int, _vp, _vp]
+    L.nf_quad_weights_opts.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, C.c_int, C.POINTER(_QuadOpts), _vp,
+                                       C.POINTER(C.c_int64), _vp]
     L.nf_quad_weights.argtypes = [_vp, _vp, _i64, C.c_int, _vp, _i64, _vp, C.c_int, C.c_int, _vp,
                                   C.POINTER(C.c_int64), _vp]
     L.nf_operator_create.argtypes = [_vp, _vp, _i64, _Kernel, C.c_int, _vp, C.POINTER(_vp)]
@@ -175,6 +184,35 @@ def nf_build_stencils(nodes: torch.Tensor, tris: torch.Tensor, k: int) -> torch.
     return out
 
 
+def nf_build_stencils_at(nodes: torch.Tensor, centers: torch.Tensor, k: int) -> torch.Tensor:
+    """k nearest nodes (ascending (d^2, index)) to each given centre.
+    nodes: n x dim float64 CUDA, centers: m x dim float64 CUDA -> m x k int32."""
+    n, dim = nodes.shape
+    m = centers.shape[0]
+    if centers.dim() != 2 or centers.shape[1] != dim:
+        raise ValueError(f"centers must be m x {dim}")
+    out = torch.empty((m, k), dtype=torch.int32, device=nodes.device)
+    _check(lib().nf_build_stencils_at(_dptr(nodes, torch.float64, "nodes"), n, dim,
+                                      _dptr(centers, torch.float64, "centers"), m, int(k),
+                                      _dptr(out, torch.int32, "stencils"), _stream(nodes)))
+    return out
+
+
+def nf_quad_weights_opts(nodes: torch.Tensor, tris: torch.Tensor, stencils: torch.Tensor, opts: dict,
+                         normals: torch.Tensor | None = None) -> torch.Tensor:
+    """nf_quad_weights with an options struct: opts = {dim, phs_order, poly_deg, curved}."""
+    n = nodes.shape[0]
+    m, k = stencils.shape
+    o = _QuadOpts(int(opts["dim"]), int(opts.get("phs_order", 3)), int(opts["poly_deg"]), int(opts["curved"]))
+    q = torch.empty(n, dtype=torch.float64, device=nodes.device)
+    bad = C.c_int64(-1)
+    nptr = _dptr(normals, torch.float64, "normals") if normals is not None else None
+    _check(lib().nf_quad_weights_opts(_dptr(nodes, torch.float64, "nodes"), nptr, n, _dptr(tris, torch.int32, "tris"),
+                                      m, _dptr(stencils, torch.int32, "stencils"), k, C.byref(o),
+                                      _dptr(q, torch.float64, "q"), C.byref(bad), _stream(nodes)))
+    return q
+
+
 def nf_quad_weights(nodes: torch.Tensor, tris: torch.Tensor, stencils: torch.Tensor, deg: int,
                     normals: torch.Tensor | None = None) -> torch.Tensor:
     """RBF-QF node weights (float64, n)."""
@@ -203,6 +241,12 @@ class Forcing:
     @classmethod
     def flat(cls, c=0.1, radius=0.2, sigma=1.1, scale=1.0):
         return cls(FORCE_MMS_FLAT, c=c, radius=radius, sigma=sigma, scale=scale)
+
+    @classmethod
+    def sphere(cls, c=0.5, a0=0.3):
+        """The manufactured solution on the unit sphere, with Y1 = z/2, Y2 = x y and the
+        eigenvalues taken by the library from the operator."""
+        return cls(FORCE_MMS_SPHERE, c=c, a0=a0)
 
     def _struct(self):
         y1 = _dptr(self.Y1, torch.float32, "Y1").value if self.Y1 is not None else None

@@ -142,8 +142,8 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     NF_ARG(B >= 1 && B <= 65535 && C >= 1 && nsteps >= 0, "B, C or nsteps out of range");
     if (op->path != NF_MATRIX_FREE)
         return fail(NF_ERR_UNSUPPORTED, "nf_adjoint needs a matrix-free operator (W^T is applied on the fly)");
-    if (g && g->kind == NF_FORCE_MMS_FLAT)
-        return fail(NF_ERR_UNSUPPORTED, "the flat manufactured forcing depends on the kernel parameters; nf_adjoint "
+    if (g && (g->kind == NF_FORCE_MMS_FLAT || g->kind == NF_FORCE_MMS_SPHERE))
+        return fail(NF_ERR_UNSUPPORTED, "this manufactured forcing depends on the kernel parameters; nf_adjoint "
                                         "treats forcing as data and does not differentiate it");
     if (g && g->kind != NF_FORCE_NONE && g->kind != NF_FORCE_MMS_EIGEN) return fail(NF_ERR_ARG, "unknown forcing");
     if (g && g->kind == NF_FORCE_MMS_EIGEN) NF_ARG(g->Y1 && g->Y2, "forcing: Y1 and Y2 are required");

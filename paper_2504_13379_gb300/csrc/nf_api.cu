@@ -290,15 +290,33 @@ static void destroy_prof_ring(nf_operator *op) {
     op->prof_slots = 0;
 }
 
-static nf_status check_forcing(const nf_operator *op, const nf_forcing *g, const nf_forcing **out) {
+// Validated forcing for a step: *out is the caller's descriptor, or for NF_FORCE_MMS_SPHERE a
+// copy (in *fill) with the Funk-Hecke eigenvalues of the operator's kernel filled in.
+static nf_status check_forcing(const nf_operator *op, const nf_forcing *g, const nf_forcing **out,
+                               nf_forcing *fill) {
     static const nf_forcing none{NF_FORCE_NONE, nullptr, nullptr, 0, 0, 0, 0, 0, 0, 0, 0};
     if (!g) {
         *out = &none;
         return NF_OK;
     }
-    NF_ARG(g->kind == NF_FORCE_NONE || g->kind == NF_FORCE_MMS_EIGEN || g->kind == NF_FORCE_MMS_FLAT,
+    NF_ARG(g->kind == NF_FORCE_NONE || g->kind == NF_FORCE_MMS_EIGEN || g->kind == NF_FORCE_MMS_FLAT ||
+               g->kind == NF_FORCE_MMS_SPHERE,
            "unknown forcing kind %d", g->kind);
     if (g->kind == NF_FORCE_MMS_EIGEN) NF_ARG(g->Y1 && g->Y2, "forcing: Y1 and Y2 are required");
+    if (g->kind == NF_FORCE_MMS_SPHERE) {
+        NF_ARG(op->kp.period == 0.f, "the sphere's manufactured forcing needs the Euclidean (chord) distance");
+        NF_ARG(g->c > 0.0 && g->c + std::fabs(g->a0) * 1.5 < 1.0 && g->c - std::fabs(g->a0) * 1.5 > 0.0,
+               "sphere manufactured forcing: need 0 < c -+ 1.5 |a0| < 1 (z in (0, 1) on the unit sphere)");
+        *fill = *g;
+        double lam[3];
+        NF_TRY(nf_mms_sphere_eigs(op->kp, lam));
+        fill->lam0 = lam[0];
+        fill->lam1 = lam[1];
+        fill->lam2 = lam[2];
+        fill->Y1 = fill->Y2 = nullptr;
+        *out = fill;
+        return NF_OK;
+    }
     if (g->kind == NF_FORCE_MMS_FLAT) {
         NF_ARG(op->kp.period > 0.f, "flat manufactured forcing needs a periodic kernel (period > 0)");
         NF_ARG(g->sigma > 0.0 && g->c > 0.0 && g->c + 1.0 / (2.0 * 3.14159265358979323846 * g->sigma * g->sigma) < 1.0,
@@ -461,7 +479,8 @@ nf_status nf_rk4_advance(nf_operator *op, float *u, int B, double t0, double dt,
     NF_ARG(std::isfinite(t0) && std::isfinite(dt), "t0 and dt must be finite");
     NF_ARG(!ckpt || C >= 1, "checkpoint interval C must be >= 1");
     const nf_forcing *F = nullptr;
-    NF_TRY(check_forcing(op, g, &F));
+    nf_forcing Ffill{};
+    NF_TRY(check_forcing(op, g, &F, &Ffill));
     cudaStream_t s = as_stream(stream);
     if (op->path == NF_GROUPED) {
         NF_ARG(B == group_traj_total(op), "grouped operator: B = %d must equal the group's %d trajectories", B,

@@ -2019,8 +2019,16 @@ __device__ __forceinline__ double forcing_value(const nf_forcing &F, const float
         }
         return dus + us - F.scale * C;
     }
-    if (F.kind != NF_FORCE_MMS_EIGEN) return 0.0;
-    const double Y1 = F.Y1[i], Y2 = F.Y2[i];
+    if (F.kind != NF_FORCE_MMS_EIGEN && F.kind != NF_FORCE_MMS_SPHERE) return 0.0;
+    double Y1, Y2;
+    if (F.kind == NF_FORCE_MMS_SPHERE) {  // Y1 = z / 2 (degree 1), Y2 = x y (degree 2) at the node
+        const float4 xi = x4[i];
+        Y1 = 0.5 * (double)xi.z;
+        Y2 = (double)xi.x * (double)xi.y;
+    } else {
+        Y1 = F.Y1[i];
+        Y2 = F.Y2[i];
+    }
     const double Y = Y1 + Y2;
     const double a = F.a0 * cos(t), da = -F.a0 * sin(t);
     const double z = F.c + a * Y;

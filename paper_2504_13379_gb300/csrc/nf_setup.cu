@@ -139,14 +139,19 @@ __global__ void cell_fill_kernel(int64_t n, const int32_t *cell_of, const int32_
     sorted[pos] = (int32_t)j;
 }
 
+// Query point e: the centroid of triangle e (tris given), or centers[e] (centers given).
 __global__ void knn_query_kernel(const double *__restrict__ nodes, int64_t n, int dim,
-                                 const int32_t *__restrict__ tris, int64_t m, int k, Grid gr,
-                                 const int32_t *__restrict__ start, const int32_t *__restrict__ sorted,
+                                 const int32_t *__restrict__ tris, const double *__restrict__ centers, int64_t m,
+                                 int k, Grid gr, const int32_t *__restrict__ start, const int32_t *__restrict__ sorted,
                                  int32_t *__restrict__ stencils) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m) return;
     double c[3] = {0, 0, 0};
-    centroid_of(nodes, dim, tris + 3 * e, c);
+    if (centers) {
+        for (int d = 0; d < dim; ++d) c[d] = centers[e * dim + d];
+    } else {
+        centroid_of(nodes, dim, tris + 3 * e, c);
+    }
     int cc[3] = {0, 0, 0};
     for (int d = 0; d < dim; ++d) cc[d] = cell_coord(c[d], gr.lo[d], gr.h, gr.G[d]);
     double bd[KNN_KMAX];
@@ -196,27 +201,29 @@ __global__ void knn_query_kernel(const double *__restrict__ nodes, int64_t n, in
 
 using namespace nfi;
 
-extern "C" nf_status nf_build_stencils(const double *nodes, int64_t n, int dim, const int32_t *tris, int64_t m,
-                                       int k, int32_t *stencils, void *stream) {
-    clear_error();
-    NF_ARG(nodes && tris && stencils, "nodes, tris and stencils must be non-NULL");
+// k nearest nodes to each query point: triangle centroids (tris) or given centres (centers).
+// The search grid covers the nodes and, with centres, the centres as well, so that its
+// shell-by-shell stopping rule holds for query points outside the nodes' bounding box.
+static nf_status build_stencils(const double *nodes, int64_t n, int dim, const int32_t *tris, const double *centers,
+                                int64_t m, int k, int32_t *stencils, cudaStream_t s) {
     NF_ARG(dim == 2 || dim == 3, "dim must be 2 or 3 (got %d)", dim);
     NF_ARG(n >= 1 && n < ((int64_t)1 << 31), "n out of range");
     NF_ARG(m >= 1 && m < ((int64_t)1 << 31), "m out of range");
     NF_ARG(k >= 1 && k <= KNN_KMAX && k <= n, "k = %d must satisfy 1 <= k <= min(n, %d)", k, KNN_KMAX);
-    cudaStream_t s = as_stream(stream);
-    // bounding box
+    // bounding box of the nodes (first nb partials) and of the centres (next nbc)
     const int nb = (int)std::min<int64_t>(256, ceil_div(n, 256));
+    const int nbc = centers ? (int)std::min<int64_t>(256, ceil_div(m, 256)) : 0;
     double *dbox = nullptr;
-    NF_CUDA_TRY(cudaMallocAsync(&dbox, sizeof(double) * 6 * nb + 16, s));
-    int *dflag = reinterpret_cast<int *>(dbox + 6 * nb);
+    NF_CUDA_TRY(cudaMallocAsync(&dbox, sizeof(double) * 6 * (nb + nbc) + 16, s));
+    int *dflag = reinterpret_cast<int *>(dbox + 6 * (nb + nbc));
     NF_CUDA_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), s));
-    validate_indices_kernel<<<(unsigned)ceil_div(3 * m, 256), 256, 0, s>>>(tris, 3 * m, n, dflag);
+    if (tris) validate_indices_kernel<<<(unsigned)ceil_div(3 * m, 256), 256, 0, s>>>(tris, 3 * m, n, dflag);
     bbox_partial_kernel<<<nb, 256, 0, s>>>(nodes, n, dim, dbox);
+    if (centers) bbox_partial_kernel<<<nbc, 256, 0, s>>>(centers, m, dim, dbox + 6 * nb);
     NF_CUDA_TRY(cudaGetLastError());
-    std::vector<double> hbox(6 * nb);
+    std::vector<double> hbox(6 * (nb + nbc));
     int hflag = 0;
-    NF_CUDA_TRY(cudaMemcpyAsync(hbox.data(), dbox, sizeof(double) * 6 * nb, cudaMemcpyDeviceToHost, s));
+    NF_CUDA_TRY(cudaMemcpyAsync(hbox.data(), dbox, sizeof(double) * 6 * (nb + nbc), cudaMemcpyDeviceToHost, s));
     NF_CUDA_TRY(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     NF_CUDA_TRY(cudaStreamSynchronize(s));
     if (hflag) {
@@ -224,10 +231,15 @@ extern "C" nf_status nf_build_stencils(const double *nodes, int64_t n, int dim, 
         return fail(NF_ERR_ARG, "tris holds a node index outside [0, n)");
     }
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int b = 0; b < nb; ++b)
+    for (int b = 0; b < nb + nbc; ++b)
         for (int d = 0; d < 3; ++d) {
             lo[d] = std::min(lo[d], hbox[6 * b + d]);
             hi[d] = std::max(hi[d], hbox[6 * b + 3 + d]);
+        }
+    for (int d = 0; d < dim; ++d)
+        if (!std::isfinite(lo[d]) || !std::isfinite(hi[d])) {
+            cudaFreeAsync(dbox, s);
+            return fail(NF_ERR_ARG, "non-finite node or centre coordinates");
         }
     Grid gr{};
     double ext = 0.0;
@@ -251,8 +263,8 @@ extern "C" nf_status nf_build_stencils(const double *nodes, int64_t n, int dim, 
     exclusive_scan_kernel<<<1, 1024, 0, s>>>(counts, gr.ncell, start);
     NF_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * gr.ncell, s));
     cell_fill_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, cell_of, start, counts, sorted);
-    knn_query_kernel<<<(unsigned)ceil_div(m, 128), 128, 0, s>>>(nodes, n, dim, tris, m, k, gr, start, sorted,
-                                                                stencils);
+    knn_query_kernel<<<(unsigned)ceil_div(m, 128), 128, 0, s>>>(nodes, n, dim, tris, centers, m, k, gr, start,
+                                                                sorted, stencils);
     NF_CUDA_TRY(cudaGetLastError());
     cudaFreeAsync(cell_of, s);
     cudaFreeAsync(counts, s);
@@ -260,6 +272,20 @@ extern "C" nf_status nf_build_stencils(const double *nodes, int64_t n, int dim, 
     cudaFreeAsync(sorted, s);
     cudaFreeAsync(dbox, s);
     return NF_OK;
+}
+
+extern "C" nf_status nf_build_stencils(const double *nodes, int64_t n, int dim, const int32_t *tris, int64_t m,
+                                       int k, int32_t *stencils, void *stream) {
+    clear_error();
+    NF_ARG(nodes && tris && stencils, "nodes, tris and stencils must be non-NULL");
+    return build_stencils(nodes, n, dim, tris, nullptr, m, k, stencils, as_stream(stream));
+}
+
+extern "C" nf_status nf_build_stencils_at(const double *nodes, int64_t n, int dim, const double *centers, int64_t m,
+                                          int k, int32_t *stencils, void *stream) {
+    clear_error();
+    NF_ARG(nodes && centers && stencils, "nodes, centers and stencils must be non-NULL");
+    return build_stencils(nodes, n, dim, nullptr, centers, m, k, stencils, as_stream(stream));
 }
 
 // ======================================================================= weights
@@ -820,4 +846,17 @@ extern "C" nf_status nf_quad_weights(const double *nodes, const double *normals,
         return fail(NF_ERR_SINGULAR, "singular interpolation system at element %lld", (long long)hbad);
     }
     return NF_OK;
+}
+
+extern "C" nf_status nf_quad_weights_opts(const double *nodes, const double *normals, int64_t n, const int32_t *tris,
+                                          int64_t m, const int32_t *stencils, int k, const nf_quad_opts *o, double *q,
+                                          int64_t *bad_element, void *stream) {
+    clear_error();
+    NF_ARG(o, "options must be non-NULL");
+    NF_ARG(o->dim == 2 || o->dim == 3, "dim must be 2 or 3 (got %d)", o->dim);
+    NF_ARG(o->curved == (o->dim == 3 ? 1 : 0), "curved must be 1 for dim 3 (surfaces) and 0 for dim 2");
+    if (o->phs_order != 3)
+        return fail(NF_ERR_UNSUPPORTED, "phs_order %d: the polyharmonic spline r^3 is implemented", o->phs_order);
+    return nf_quad_weights(nodes, o->curved ? normals : nullptr, n, o->dim, tris, m, stencils, k, o->poly_deg, q,
+                           bad_element, stream);
 }

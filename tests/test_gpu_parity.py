@@ -251,6 +251,65 @@ def test_rk4_sphere_manufactured_forcing(nf):
     assert rel_l2(got, want) < REL_L2
 
 
+def test_rk4_sphere_manufactured_forcing_from_operator(nf):
+    """The same manufactured problem with the forcing kind that takes Y1, Y2 and the
+    eigenvalues from the operator (the caller passes only c and a0)."""
+    wl = W.sphere(3000)
+    st = oracle.knn(wl.ns.nodes, wl.ns.tris, wl.k)
+    q = oracle.quad_weights(wl.ns.nodes, wl.ns.tris, st, wl.deg, normals=wl.ns.normals).astype(np.float32)
+    X = wl.ns.nodes.astype(np.float32)
+    op = _op(nf, X, q, wl.kernel, 0)
+    u = dev(wl.u0.astype(np.float32), torch.float32)
+    beta, theta = wl.beta.astype(np.float32), wl.theta.astype(np.float32)
+    F = nf.Forcing.sphere(wl.forcing["c"], wl.forcing["a0"])
+    nf.nf_rk4_advance(op, u, 0.0, wl.dt, 40, dev(beta, torch.float32), dev(theta, torch.float32), forcing=F)
+    op.check()
+    Fo = oracle.mms_sphere_forcing(f32(wl.kernel), wl.forcing["c"], wl.forcing["a0"])
+    want = oracle.rk4(f32(X), f32(q), f32(wl.u0), f32(wl.kernel), f32(beta), f32(theta), 0.0, wl.dt, 40, forcing=Fo)
+    assert rel_l2(u.cpu().numpy(), want) < REL_L2
+    ck = torch.zeros((3, 1, X.shape[0]), dtype=torch.float32, device="cuda")
+    with pytest.raises(nf.NFError) as ei:
+        nf.nf_adjoint(op, ck, 1, 0.0, wl.dt, 2, 20.0, 0.2, torch.zeros((1, X.shape[0]), device="cuda"), forcing=F)
+    assert ei.value.name == "NF_ERR_UNSUPPORTED"
+
+
+def test_stencils_at_given_centres(nf):
+    """nf_build_stencils_at: bit-exact against the oracle for arbitrary centres (quantised,
+    with exact ties, some outside the nodes' bounding box), and equal to nf_build_stencils
+    at the triangle centroids."""
+    rng = np.random.default_rng(77)
+    for dim in (2, 3):
+        n = 3000
+        X = np.round(rng.uniform(0, 1, size=(n, dim)) * 32) / 32
+        Cq = np.round(rng.uniform(-0.3, 1.3, size=(700, dim)) * 64) / 64
+        k = 21
+        got = nf.nf_build_stencils_at(dev(X, torch.float64), dev(Cq, torch.float64), k).cpu().numpy()
+        np.testing.assert_array_equal(got, oracle.knn_at(X, Cq, k))
+        tris = rng.integers(0, n, size=(500, 3)).astype(np.int32)
+        cent = ((X[tris[:, 0]] + X[tris[:, 1]]) + X[tris[:, 2]]) / 3.0
+        a = nf.nf_build_stencils_at(dev(X, torch.float64), dev(cent, torch.float64), k).cpu().numpy()
+        b = nf.nf_build_stencils(dev(X, torch.float64), dev(tris, torch.int32), k).cpu().numpy()
+        np.testing.assert_array_equal(a, b)
+
+
+def test_quad_weights_options_struct(nf):
+    """nf_quad_weights_opts gives the same weights as nf_quad_weights; other spline orders
+    are refused."""
+    wl = W.sphere(2000)
+    nodes = dev(wl.ns.nodes, torch.float64)
+    tris = dev(wl.ns.tris, torch.int32)
+    normals = dev(wl.ns.normals, torch.float64)
+    st = nf.nf_build_stencils(nodes, tris, wl.k)
+    a = nf.nf_quad_weights(nodes, tris, st, wl.deg, normals=normals)
+    b = nf.nf_quad_weights_opts(nodes, tris, st, {"dim": 3, "phs_order": 3, "poly_deg": wl.deg, "curved": 1},
+                                normals=normals)
+    assert torch.equal(a, b)
+    with pytest.raises(nf.NFError) as ei:
+        nf.nf_quad_weights_opts(nodes, tris, st, {"dim": 3, "phs_order": 5, "poly_deg": wl.deg, "curved": 1},
+                                normals=normals)
+    assert ei.value.name == "NF_ERR_UNSUPPORTED"
+
+
 def test_rk4_batched_trajectories(nf):
     rng = np.random.default_rng(5)
     ns = nodesets.ellipsoid_fibonacci(2000, seed=9)

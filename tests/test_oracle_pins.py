@@ -74,6 +74,23 @@ def test_knn_matches_full_sort(dim, rng):
         np.testing.assert_array_equal(got[e], want)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_knn_at_matches_full_sort_and_centroid_form(dim, rng):
+    # the §3.1 selection around given centres: quantised nodes and centres (exact ties), some
+    # centres outside the nodes' bounding box; at the centroids it equals knn
+    n = 300
+    X = np.round(rng.uniform(0, 1, size=(n, dim)) * 8) / 8
+    Cq = np.round(rng.uniform(-0.5, 1.5, size=(40, dim)) * 16) / 16
+    k = 13
+    got = oracle.knn_at(X, Cq, k)
+    for e in range(Cq.shape[0]):
+        d2 = ((X - Cq[e]) ** 2).sum(1)
+        np.testing.assert_array_equal(got[e], np.lexsort((np.arange(n), d2))[:k])
+    tris = rng.integers(0, n, size=(30, 3)).astype(np.int32)
+    cent = ((X[tris[:, 0]] + X[tris[:, 1]]) + X[tris[:, 2]]) / 3.0
+    np.testing.assert_array_equal(oracle.knn_at(X, cent, k), oracle.knn(X, tris, k))
+
+
 def test_knn_subset_and_permutation_invariance(rng):
     n = 400
     X = rng.uniform(size=(n, 3))
