@@ -683,10 +683,8 @@ def run_configs(dev):
     q = nf.nf_quad_weights(nodes, tris, st, wl.deg, normals=torch.as_tensor(wl.ns.normals, device=dev))
     X = wl.ns.nodes
     x32 = torch.as_tensor(X.astype(np.float32), device=dev)
-    Y1 = torch.as_tensor((0.5 * X[:, 2]).astype(np.float32), device=dev)
-    Y2 = torch.as_tensor((X[:, 0] * X[:, 1]).astype(np.float32), device=dev)
     c, a0 = wl.forcing["c"], wl.forcing["a0"]
-    F = nf.Forcing(nf.FORCE_MMS_EIGEN, Y1, Y2, c, a0, nf.nf_mms_sphere_eigs(wl.kernel))
+    F = nf.Forcing.sphere(c, a0)  # Y1 = z/2, Y2 = x y and the eigenvalues from the operator
     op = nf.Operator(x32, q.to(torch.float32), wl.kernel, nf.MATRIX_FREE)
     u0 = torch.as_tensor(wl.u0.astype(np.float32), device=dev)
     ms, u = whole_run(op, u0, wl, forcing=F)
