@@ -145,15 +145,15 @@ def peaks():
 
 # Lane operations per ordered pair of the symmetric matrix-free kernel in its expanded form
 # with s2^2 / s1^2 = 4 (the workload's kernel): per unordered pair 3 FMA (exponent) +
-# 2 MUL (e1 = e2^4) + 2 FMA (row sums) + 2 FMA (column sums), plus per column and 8-row
-# pass 3 SUB + 3 FMA (centred column and n_j) and 1 ADD (column sums into shared memory):
-# 9.875 per unordered pair, 4.9375 per ordered pair; and one SFU exponential per unordered
-# pair.  Diagonal block pairs evaluate their ordered pairs one by one, a 1/nb share of the
-# work.  The rates these counts are divided by (FP32 FMA-pipe lane operations and SFU ex2
+# 2 MUL (e1 = e2^4) + 1 FMA (pair weight e2 + c_i e1) + 1 FMA (row sum) + 1 FMA (column
+# sum), plus per column and 8-row pass 3 SUB + 3 FMA (centred column and n_j) and 1 ADD
+# (column sums into shared memory): 8.875 per unordered pair, 4.4375 per ordered pair; and
+# one SFU exponential per unordered pair.  Diagonal block pairs evaluate their ordered
+# pairs one by one, a 1/nb share of the work.  The rates these counts are divided by (FP32 FMA-pipe lane operations and SFU ex2
 # per clock per SM) are measured in the same run by nf_probe_pipe; the nominal figures
 # (128 FP32 lanes, 16 SFU operations per clock per SM) are kept only as a fallback.
 FMA_LANES_PER_CLK_SM_NOMINAL = 128.0
-LANE_OPS_PER_PAIR = 9.875 / 2.0
+LANE_OPS_PER_PAIR = 8.875 / 2.0
 EX2_PER_PAIR = 0.5
 
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels:

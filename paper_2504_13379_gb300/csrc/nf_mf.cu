@@ -503,6 +503,14 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     static_assert(R == 4 || R == 8, "rows per warp");
     static_assert(BLK == 512 || BLK == 1024, "block size");
     constexpr int NPASS = BLK / R;
+    // Integer width ratios combine the two Gaussians per pair: with the row factors f1, f2,
+    //   w_ij = A1 f1 e1 - A2 f2 e2 = (-A2 f2) (e2 + c_i e1),  c_i = -(A1 f1) / (A2 f2),
+    // so one FMA forms the pair weight u = e2 + c_i e1 and one FMA each adds u g_j to the
+    // row sum and u (-A2 f2 g_i) to the column sum: 8 FMA-pipe lane operations per
+    // unordered pair instead of 9 (separate e1 and e2 row sums, two column FMAs).  The
+    // host takes this form only while |A1 / A2| stays far from FP32 overflow (f1 <= f2
+    // for M >= 2, so |c_i| <= |A1 / A2|); other kernels take the general form M = 0.
+    constexpr bool CW = M >= 2;
     extern __shared__ __align__(16) float ms_smem[];
     float *xs = ms_smem, *ys = xs + BLK, *zs = ys + BLK, *gs = zs + BLK;
     int *cnode = reinterpret_cast<int *>(gs + BLK);
@@ -596,7 +604,8 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
             rmx[k] = x;
             rmy[k] = y;
             rmz[k] = z;
-            rh1[k] = A1 * f1 * gi;
+            // CW: h1 holds the ratio c_i of the two terms (the combined pair weight below)
+            rh1[k] = CW ? -(A1 * f1) / (A2 * f2) : A1 * f1 * gi;
             rh2[k] = -A2 * f2 * gi;
             rf1[k] = A1 * f1;
             rf2[k] = -A2 * f2;
@@ -637,6 +646,21 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         const float4 c = pc[ps];
         const int form = (int)c.w;  // warp-uniform
         u64 xi[R], yi[R], zi[R], h1[R], h2[R], a1[R], a2[R];
+        // one pair's contribution to row r's sums and to the column sum cacc
+        auto accum = [&](int r, u64 e1, u64 e2, u64 gj, u64 &cacc) {
+            if constexpr (M == 1) {
+                a1[r] = f2_fma(e1, gj, a1[r]);
+                cacc = f2_fma(e1, h1[r], cacc);
+            } else if constexpr (CW) {
+                const u64 u = f2_fma(e1, h1[r], e2);
+                a1[r] = f2_fma(u, gj, a1[r]);
+                cacc = f2_fma(u, h2[r], cacc);
+            } else {
+                a1[r] = f2_fma(e1, gj, a1[r]);
+                a2[r] = f2_fma(e2, gj, a2[r]);
+                cacc = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc));
+            }
+        };
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             xi[r] = f2_pack(rmx[r0 + r], rmx[r0 + r]);
@@ -689,13 +713,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                         const u64 sij = f2_fma(xi[r], xt[h], f2_fma(yi[r], yt[h], zz));
                         u64 e1, e2;
                         exps(sij, e1, e2);
-                        a1[r] = f2_fma(e1, gj[h], a1[r]);
-                        if constexpr (M == 1) {
-                            cacc[h] = f2_fma(e1, h1[r], cacc[h]);
-                        } else {
-                            a2[r] = f2_fma(e2, gj[h], a2[r]);
-                            cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
-                        }
+                        accum(r, e1, e2, gj[h], cacc[h]);
                     }
                 }
                 add_cols(q, cacc);
@@ -735,13 +753,7 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                         const u64 r2s = D2 ? r2xy : f2_fma(dz, dz, r2xy);
                         u64 e1, e2;
                         exps(r2s, e1, e2);
-                        a1[r] = f2_fma(e1, gj[h], a1[r]);
-                        if constexpr (M == 1) {
-                            cacc[h] = f2_fma(e1, h1[r], cacc[h]);
-                        } else {
-                            a2[r] = f2_fma(e2, gj[h], a2[r]);
-                            cacc[h] = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc[h]));
-                        }
+                        accum(r, e1, e2, gj[h], cacc[h]);
                     }
                 }
                 add_cols(q, cacc);
@@ -771,8 +783,12 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         for (int r = 0; r < R; ++r) {
             float p0, p1, q0, q1;
             f2_unpack(a1[r], p0, p1);
-            f2_unpack(a2[r], q0, q1);
-            v[r] = rf1[r0 + r] * (p0 + p1) + rf2[r0 + r] * (q0 + q1);
+            if constexpr (CW) {
+                v[r] = rf2[r0 + r] * (p0 + p1);
+            } else {
+                f2_unpack(a2[r], q0, q1);
+                v[r] = rf1[r0 + r] * (p0 + p1) + rf2[r0 + r] * (q0 + q1);
+            }
         }
         int row;
         const float tot = warp_reduce_rows<R>(v, lane, row);
@@ -1200,8 +1216,15 @@ static float scaled_period(const nf_kernel &k) {
 }
 
 // Form of the symmetric kernel: 1 for a single Gaussian (A2 = 0), else the width ratio.
+// The width-ratio forms combine the two Gaussians through the ratio -A1 f1 / (A2 f2) per
+// row, which stays finite while |A1 / A2| <= 2^100; beyond that the general form.
 static int mf_width_ratio(const nf_kernel &k);
-static int sym_form(const nf_kernel &k) { return k.A2 == 0.f ? 1 : mf_width_ratio(k); }
+static int sym_form(const nf_kernel &k) {
+    if (k.A2 == 0.f) return 1;
+    const int m = mf_width_ratio(k);
+    if (m >= 2 && !(std::fabs((double)k.A1) <= 0x1p100 * std::fabs((double)k.A2))) return 0;
+    return m;
+}
 
 // Integer width ratio m = s2^2 / s1^2 in {2, 3, 4} (to FP32 rounding of the k2 the kernel
 // receives), else 0: selects the one-exponential form of the packed kernel.

@@ -187,6 +187,27 @@ def test_nonlocal_apply_width_ratios_and_blocks(nf, ratio, n, sched):
     assert np.abs(got - want).max() / np.abs(want).max() < REL_L2
 
 
+@pytest.mark.parametrize("A1,A2", [(1.0, 1e-35), (1e-30, 1.0), (-0.7, 0.3), (0.0, 0.8), (2.0, -0.5)])
+def test_nonlocal_apply_amplitude_extremes(nf, A1, A2):
+    """The symmetric kernel with an integer width ratio combines the two Gaussians through
+    the per-row ratio -A1 f1 / (A2 f2); amplitude ratios far outside FP32's range (here
+    1e35) take the general form instead.  Both sides of that limit, a vanishing ratio, an
+    A1 of zero and signs flipped, against the oracle."""
+    rng = np.random.default_rng(77)
+    n = 3000
+    X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    q = rng.uniform(0.5, 1.5, n).astype(np.float32) / n
+    u = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
+    s1 = 0.15
+    kern = (A1, s1, A2, float(np.float32(s1) * np.float32(2.0)))
+    op = _op(nf, X, q, kern, 0).mf_schedule(nf.MF_SYMMETRIC)
+    got = nf.nf_nonlocal_apply(op, dev(u, torch.float32), 20.0, 0.2).cpu().numpy()
+    op.check()
+    want = oracle.nonlocal_sum(f32(X), f32(q), f32(u), f32(kern), 20.0, float(np.float32(0.2)))
+    assert np.isfinite(got).all()
+    assert rel_l2(got, want) < REL_L2
+
+
 def test_nonlocal_apply_paper_kernel_torus_sampled_full_size(nf):
     """Full precision-workload size (n = 100,000 torus nodes), the launch
     configuration the benchmark times; the oracle evaluates 384 sampled rows."""
