@@ -646,6 +646,16 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         const float4 c = pc[ps];
         const int form = (int)c.w;  // warp-uniform
         u64 xi[R], yi[R], zi[R], h1[R], h2[R], a1[R], a2[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            xi[r] = f2_pack(rmx[r0 + r], rmx[r0 + r]);
+            yi[r] = f2_pack(rmy[r0 + r], rmy[r0 + r]);
+            zi[r] = f2_pack(rmz[r0 + r], rmz[r0 + r]);
+            h1[r] = f2_pack(rh1[r0 + r], rh1[r0 + r]);
+            h2[r] = f2_pack(rh2[r0 + r], rh2[r0 + r]);
+            a1[r] = 0ull;
+            a2[r] = 0ull;
+        }
         // one pair's contribution to row r's sums and to the column sum cacc
         auto accum = [&](int r, u64 e1, u64 e2, u64 gj, u64 &cacc) {
             if constexpr (M == 1) {
@@ -661,16 +671,6 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
                 cacc = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc));
             }
         };
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            xi[r] = f2_pack(rmx[r0 + r], rmx[r0 + r]);
-            yi[r] = f2_pack(rmy[r0 + r], rmy[r0 + r]);
-            zi[r] = f2_pack(rmz[r0 + r], rmz[r0 + r]);
-            h1[r] = f2_pack(rh1[r0 + r], rh1[r0 + r]);
-            h2[r] = f2_pack(rh2[r0 + r], rh2[r0 + r]);
-            a1[r] = 0ull;
-            a2[r] = 0ull;
-        }
         const u64 cxp = f2_pack(c.x, c.x), cyp = f2_pack(c.y, c.y), czp = f2_pack(c.z, c.z);
         auto add_cols = [&](int q, const u64 (&cacc)[2]) {
             if (!diag) {
