@@ -837,6 +837,14 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
     static_assert(R == 4 || R == 8, "rows per warp");
     static_assert(BLK == 512 || BLK == 1024, "block size");
     constexpr int NPASS = BLK / R;
+    // CW (integer width ratios, A2 != 0): per pair the W nu sums take the combined weight
+    // u = e2 + c_i e1 (c_i = -A1 f1 / (A2 f2), as in mf_sym_kernel), and the parameter sums
+    // the symmetric pair weight p_ij = nu_i g_j + g_i nu_j, formed once per pair: per row
+    // the lane keeps U = sum u nu_j (the W nu row sum), sum e1 p, sum e2 p, sum arg e1 p and
+    // sum arg e2 p -- 16 FMA-pipe instructions per row and column pair instead of 17, and
+    // five accumulators per row instead of eight.  The host takes this form only while
+    // |A1 / A2| <= 2^100; otherwise, and for A2 = 0, the general form M = 0.
+    constexpr bool CW = M >= 2;
     extern __shared__ __align__(16) float as_smem[];
     // column block: x, y, z, nu, g (floats), node (int)
     float *xs = as_smem, *ys = xs + BLK, *zs = ys + BLK, *vs = zs + BLK, *gsm = vs + BLK;
@@ -911,8 +919,13 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             const float nu = rgw[k].x, gi = rgw[k].y;
             rgeo[k] = make_float4(x, y, z, ni);
             const float h1 = A1 * f1 * nu, h2 = -A2 * f2 * nu;
-            rwn[k] = make_float4(h1, h1, h2, h2);
-            rgw[k] = make_float4(f1 * nu, diag ? 0.f : f1 * gi, f2 * nu, diag ? 0.f : f2 * gi);
+            if constexpr (CW) {  // (c_i, -, h2): ratio and column weight; (nu_i, g_i): pair weight
+                rwn[k] = make_float4(-(A1 * f1) / (A2 * f2), 0.f, h2, h2);
+                rgw[k] = make_float4(nu, diag ? 0.f : gi, 0.f, 0.f);
+            } else {
+                rwn[k] = make_float4(h1, h1, h2, h2);
+                rgw[k] = make_float4(f1 * nu, diag ? 0.f : f1 * gi, f2 * nu, diag ? 0.f : f2 * gi);
+            }
         }
     }
     __syncthreads();
@@ -943,7 +956,9 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         const bool local = c.w != 0.f;
         // per row, over the lane's columns j (e1, e2 without the row factors):
         //   a = sum e nu_j, b = sum e g_j, c = sum arg e g_j, d = sum arg e nu_j
+        // CW: a1 = U, b1, b2 = sum e p, c1, c2 = sum arg e p; pn, pg = nu_i, g_i; h1 = c_i
         u64 xi[R], yi[R], zi[R], h1[R], h2[R], a1[R], a2[R], b1[R], b2[R], c1[R], c2[R], d1[R], d2[R];
+        u64 pn[R], pg[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float4 p = rgeo[r0 + r], w = rwn[r0 + r];
@@ -952,7 +967,14 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
             zi[r] = f2_pack(p.z, p.z);
             h1[r] = f2_pack(w.x, w.x);
             h2[r] = f2_pack(w.z, w.z);
-            a1[r] = a2[r] = b1[r] = b2[r] = c1[r] = c2[r] = d1[r] = d2[r] = 0ull;
+            if constexpr (CW) {
+                const float4 q = rgw[r0 + r];
+                pn[r] = f2_pack(q.x, q.x);
+                pg[r] = f2_pack(q.y, q.y);
+                a1[r] = b1[r] = b2[r] = c1[r] = c2[r] = 0ull;
+            } else {
+                a1[r] = a2[r] = b1[r] = b2[r] = c1[r] = c2[r] = d1[r] = d2[r] = 0ull;
+            }
         }
         const u64 cxp = f2_pack(c.x, c.x), cyp = f2_pack(c.y, c.y), czp = f2_pack(c.z, c.z);
         // per (row, column pair): e1, e2 from the exponent argument arg (r^2 - n_i in the
@@ -960,16 +982,27 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         auto pair = [&](int r, u64 arg, u64 vj, u64 gj, u64 &cacc) {
             u64 e1, e2;
             exps(arg, e1, e2);
-            a1[r] = f2_fma(e1, vj, a1[r]);
-            a2[r] = f2_fma(e2, vj, a2[r]);
-            cacc = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc));
-            b1[r] = f2_fma(e1, gj, b1[r]);
-            b2[r] = f2_fma(e2, gj, b2[r]);
             const u64 s1e = f2_mul(arg, e1), s2e = f2_mul(arg, e2);
-            c1[r] = f2_fma(s1e, gj, c1[r]);
-            d1[r] = f2_fma(s1e, vj, d1[r]);
-            c2[r] = f2_fma(s2e, gj, c2[r]);
-            d2[r] = f2_fma(s2e, vj, d2[r]);
+            if constexpr (CW) {
+                const u64 u = f2_fma(e1, h1[r], e2);
+                a1[r] = f2_fma(u, vj, a1[r]);
+                cacc = f2_fma(u, h2[r], cacc);
+                const u64 pw = f2_fma(pn[r], gj, f2_mul(pg[r], vj));
+                b1[r] = f2_fma(e1, pw, b1[r]);
+                b2[r] = f2_fma(e2, pw, b2[r]);
+                c1[r] = f2_fma(s1e, pw, c1[r]);
+                c2[r] = f2_fma(s2e, pw, c2[r]);
+            } else {
+                a1[r] = f2_fma(e1, vj, a1[r]);
+                a2[r] = f2_fma(e2, vj, a2[r]);
+                cacc = f2_fma(e1, h1[r], f2_fma(e2, h2[r], cacc));
+                b1[r] = f2_fma(e1, gj, b1[r]);
+                b2[r] = f2_fma(e2, gj, b2[r]);
+                c1[r] = f2_fma(s1e, gj, c1[r]);
+                d1[r] = f2_fma(s1e, vj, d1[r]);
+                c2[r] = f2_fma(s2e, gj, c2[r]);
+                d2[r] = f2_fma(s2e, vj, d2[r]);
+            }
         };
         auto sweep_local = [&](auto lim) {
 #pragma unroll 1
@@ -1022,12 +1055,21 @@ adj_sym_kernel(const float *__restrict__ xyz, const float2 *__restrict__ vg_all,
         float v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float A1s = fold(a1[r]), A2s = fold(a2[r]), B1s = fold(b1[r]), B2s = fold(b2[r]);
-            const float4 q = rgw[r0 + r];
             const float ni = rgeo[r0 + r].w;
             // the row factors 2^(-n_i) of e1 and e2 as in the pass set-up (n_i = 0 outside
             // the expanded form, so both are 1 there)
             const float f1 = exp2f(M > 0 ? -(float)M * ni : -ni), f2 = exp2f(M > 0 ? -ni : -k2 * ni);
+            if constexpr (CW) {
+                const float P1s = fold(b1[r]), P2s = fold(b2[r]);
+                v[r] = (-A2 * f2) * fold(a1[r]);
+                P1 += f1 * P1s;
+                Q1 += f1 * (fold(c1[r]) + ni * P1s);
+                P2 += f2 * P2s;
+                Q2 += f2 * (fold(c2[r]) + ni * P2s);
+                continue;
+            }
+            const float A1s = fold(a1[r]), A2s = fold(a2[r]), B1s = fold(b1[r]), B2s = fold(b2[r]);
+            const float4 q = rgw[r0 + r];
             v[r] = (A1 * f1) * A1s + (-A2 * f2) * A2s;
             // pair weight e (nu_i g_j + g_i nu_j) with the row factors: q = (f1 nu_i, f1 g_i,
             // f2 nu_i, f2 g_i), g_i = 0 on diagonal block pairs; r^2 = arg + n_i
@@ -1385,11 +1427,19 @@ static bool use_sym(const nf_operator *op) {
     return 3 * sym_pairs_1024(op) >= 2 * (int64_t)num_sms() && sym_layout_fits(op);
 }
 
+// Form of the adjoint kernel: the width ratio m in {2, 3, 4} (combined W nu weight through the
+// ratio -A1 f1 / (A2 f2)) while A2 != 0 and |A1 / A2| <= 2^100, else the general form 0.
+static int adj_form(const nf_kernel &k) {
+    const int m = mf_width_ratio(k);
+    if (m >= 2 && (k.A2 == 0.f || !(std::fabs((double)k.A1) <= 0x1p100 * std::fabs((double)k.A2)))) return 0;
+    return m;
+}
+
 nf_status launch_adj_sym(nf_operator *op, const float2 *vg, int B, int b, float *wpart, float *gpart,
                          float *r2_phys, cudaStream_t s) {
     const nf_kernel &k = op->kp;
     const float k2 = (k.s1 * k.s1) / (k.s2 * k.s2);
-    const int m = mf_width_ratio(k);
+    const int m = adj_form(k);
     const double L2E = 1.4426950408889634;
     *r2_phys = (float)((m > 0 ? (double)k.s2 * k.s2 : (double)k.s1 * k.s1) / L2E);
     const bool cull = op->mf_cull && op->adj_pairs;
@@ -1442,7 +1492,7 @@ nf_status adj_autotune(nf_operator *op, const float2 *vg, int B, float *wpart, f
     static std::map<std::tuple<int, int64_t, int, bool>, std::pair<int, int>> cache;
     const bool cull = op->mf_cull && op->adj_pairs;
     const bool try512 = !cull && op->mf_sched == NF_MF_AUTO && sym_pairs_1024(op) < 8 * (int64_t)num_sms();
-    const auto key = std::make_tuple(op->device, op->n_pad, mf_width_ratio(op->kp), try512);
+    const auto key = std::make_tuple(op->device, op->n_pad, adj_form(op->kp), try512);
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
