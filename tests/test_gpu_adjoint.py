@@ -29,10 +29,17 @@ def dev(a):
 
 M4 = (1.0, 0.1, 0.5, 0.2)          # s2 = 2 s1: e1 = e2^4 inside the kernels
 GENERAL = (1.2, 0.08, 0.6, 0.25)   # non-integer width ratio: two exponentials per pair
+# width ratio 4 with a negative amplitude ratio (combined weight with c_i > 0), with A2 = 0
+# and with |A1 / A2| beyond 2^100 (both taken by the general form: the parameter sums of A2
+# and s2 still need e2)
+M4_SIGNS = (-0.7, 0.1, 0.3, 0.2)
+M4_A2ZERO = (1.0, 0.1, 0.0, 0.2)
+M4_TINY_A2 = (1.0, 0.1, 1e-35, 0.2)
 
 
 @pytest.mark.parametrize("n,B,nsteps,C,kern", [(900, 1, 12, 5, M4), (1500, 2, 10, 10, M4), (2100, 1, 7, 3, M4),
-                                               (1300, 1, 6, 3, GENERAL)])
+                                               (1300, 1, 6, 3, GENERAL), (1100, 1, 6, 3, M4_SIGNS),
+                                               (1100, 1, 6, 3, M4_A2ZERO), (1100, 1, 6, 3, M4_TINY_A2)])
 def test_adjoint_matches_oracle(nf, n, B, nsteps, C, kern):
     ns = nodesets.torus_lattice(n if n % 2 == 0 else n + 1, seed=n)
     n = ns.n
