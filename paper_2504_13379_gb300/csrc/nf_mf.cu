@@ -443,8 +443,8 @@ mf_pair_packed_kernel(const float *__restrict__ xyz, const float *__restrict__ g
 // (I, J) go to partial slot J, column sums to slot I; a diagonal pair (I = I) sweeps all
 // ordered pairs of the block and writes rows only.  Every (slot, node) entry is written
 // exactly once, and the stage kernel adds the n_pad / BLK slots in a fixed order, so
-// results are deterministic.  Per unordered pair (expanded form, M > 0) this costs one
-// exponential and 9 FMA-pipe lane operations for two ordered pairs.
+// results are deterministic.  Per unordered pair (expanded form, M >= 2) this costs one
+// exponential and 8 FMA-pipe lane operations for two ordered pairs.
 constexpr int MS_BLK = 1024;
 constexpr int MS_THREADS = 256;
 constexpr int MS_WARPS = MS_THREADS / 32;
@@ -623,8 +623,9 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
     // e1, e2 of two pairs from the exponent argument (expanded s_ij or r^2)
     // e1 = e2^M by squaring on the FMA pipe.  Taking it from the SFU instead (ex2 of -M s:
     // one multiply and two more exponentials in place of two multiplies) measured slower,
-    // 1.772-1.776 against 1.720 ms per sum on the 100,000-node torus, for half or all of
-    // the column pairs: the SFU results' register moves cost more than the multiply saved.
+    // 1.772-1.776 against 1.720 ms per sum on the 100,000-node torus (before the combined
+    // pair weight), for half or all of the column pairs: the SFU results' register moves
+    // cost more than the multiply saved.
     auto exps = [&](u64 arg, u64 &e1, u64 &e2) {
         float s0, s1v;
         f2_unpack(arg, s0, s1v);
@@ -762,7 +763,8 @@ mf_sym_kernel(const float *__restrict__ xyz, const float *__restrict__ g_all, co
         // each lane takes 4 consecutive columns (two f32x2 pairs) per step.  Every block is
         // swept in full, padding included (g = 0 there): a second, trimmed copy of the loops
         // for the last block measured 2.5 % slower on the 100,000-node torus (1.763 against
-        // 1.720 ms per sum), more than its 0.7 % of padded pairs
+        // 1.720 ms per sum, before the combined pair weight), more than its 0.7 % of padded
+        // pairs
         auto run = [&](auto lim) {
             if (form == 1) {
                 if (per > 0.f)
