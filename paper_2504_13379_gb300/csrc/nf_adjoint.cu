@@ -13,7 +13,11 @@
 // four parameter sums sum_ij nu_i g_j (e1, r^2 e1, e2, r^2 e2) as per-CTA partials.  The
 // epilogue adds the slots, applies the recurrences and prepares (nu, g) of the next stage;
 // a fixed-order FP64 reduction accumulates the parameter gradients.  Stage inputs are
-// recomputed segment by segment from checkpoints.
+// recomputed segment by segment from checkpoints, on a second stream: while segment k is
+// reversed on the caller's stream, segment k - 1 is recomputed into the other of two stage
+// buffers, so each launch's last, partly filled wave and the small elementwise kernels of
+// one stream overlap the other's pair kernels.  The results do not depend on the overlap
+// (every kernel's summation order is fixed).
 #include "nf_internal.cuh"
 
 #include <algorithm>
@@ -129,6 +133,36 @@ struct StreamScratch {
     }
 };
 
+// A second stream forked from the caller's, on which checkpoint segments are recomputed
+// while the previous segment is reversed on the caller's stream.  Events: fork, join, and per
+// stage buffer "recomputed" and "reversed".  The destructor joins the side stream back into
+// the caller's stream (on every return path, before the scratch buffers are released), so
+// the call stays stream-ordered, and capturable, as a whole.
+struct SideStream {
+    cudaStream_t main, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, rec[2] = {}, rev[2] = {};
+    bool forked = false;
+    explicit SideStream(cudaStream_t m) : main(m) {}
+    SideStream(const SideStream &) = delete;
+    SideStream &operator=(const SideStream &) = delete;
+    cudaError_t start() {
+        cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        cudaEvent_t *evs[6] = {&fork, &join, &rec[0], &rec[1], &rev[0], &rev[1]};
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(evs[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, main);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+        forked = e == cudaSuccess;
+        return e;
+    }
+    ~SideStream() {
+        if (forked && cudaEventRecord(join, side) == cudaSuccess) cudaStreamWaitEvent(main, join, 0);
+        cudaEvent_t evs[6] = {fork, join, rec[0], rec[1], rev[0], rev[1]};
+        for (cudaEvent_t ev : evs)
+            if (ev) cudaEventDestroy(ev);
+        if (side) cudaStreamDestroy(side);
+    }
+};
+
 }  // namespace nfi
 
 using namespace nfi;
@@ -159,7 +193,10 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     float2 *vg = nullptr;
     double *gk = nullptr;
     StreamScratch scratch(s);  // freed (stream-ordered) on every return below
-    NF_CUDA_TRY(scratch.alloc(&stages, sizeof(float) * BN * 4 * Cseg));
+    // two stage buffers: segment k - 1 is recomputed into one while segment k is reversed
+    // from the other
+    const size_t seg_elems = BN * 4 * (size_t)Cseg;
+    NF_CUDA_TRY(scratch.alloc(&stages, sizeof(float) * 2 * seg_elems));
     NF_CUDA_TRY(scratch.alloc(&lam, sizeof(float) * BN));
     NF_CUDA_TRY(scratch.alloc(&acc, sizeof(float) * BN));
     NF_CUDA_TRY(scratch.alloc(&ubuf, sizeof(float) * BN));
@@ -181,19 +218,19 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
     const int T = 256;
     const unsigned eg = (unsigned)ceil_div((int64_t)BN, T);
     const int nseg = (nsteps + C - 1) / C;
-    for (int seg = nseg - 1; seg >= 0; --seg) {
+    // ---- recompute segment seg forward into st, keeping every stage input (stream ss)
+    auto recompute = [&](int seg, float *st, cudaStream_t ss) -> nf_status {
         const int s0 = seg * C;
         const int cnt = std::min(C, nsteps - s0);
-        // ---- recompute the segment forward, keeping every stage input
-        NF_CUDA_TRY(cudaMemcpyAsync(ubuf, ckpt + (size_t)seg * BN, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
-        NF_TRY(launch_prep_g(op, ubuf, B, beta, theta, true, s));
-        NF_TRY(launch_set_clock(op, t0 + (double)s0 * dt, s));
+        NF_CUDA_TRY(cudaMemcpyAsync(ubuf, ckpt + (size_t)seg * BN, sizeof(float) * BN, cudaMemcpyDeviceToDevice, ss));
+        NF_TRY(launch_prep_g(op, ubuf, B, beta, theta, true, ss));
+        NF_TRY(launch_set_clock(op, t0 + (double)s0 * dt, ss));
         for (int j = 0; j < cnt; ++j) {
-            float *Sj = stages + (size_t)j * 4 * BN;
-            NF_CUDA_TRY(cudaMemcpyAsync(Sj, ubuf, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
+            float *Sj = st + (size_t)j * 4 * BN;
+            NF_CUDA_TRY(cudaMemcpyAsync(Sj, ubuf, sizeof(float) * BN, cudaMemcpyDeviceToDevice, ss));
             for (int stage = 1; stage <= 4; ++stage) {
                 int splits = 1;
-                NF_TRY(launch_mf_pair(op, B, s, &splits));
+                NF_TRY(launch_mf_pair(op, B, ss, &splits));
                 StageParams p{};
                 p.u = ubuf;
                 p.beta = beta;
@@ -204,14 +241,34 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
                 p.ckpt = nullptr;
                 p.C = 1;
                 p.splits = splits;
-                NF_TRY(launch_stage(op, B, p, s));
+                NF_TRY(launch_stage(op, B, p, ss));
                 if (stage < 4)
                     NF_CUDA_TRY(cudaMemcpyAsync(Sj + (size_t)stage * BN, op->U, sizeof(float) * BN,
-                                                cudaMemcpyDeviceToDevice, s));
+                                                cudaMemcpyDeviceToDevice, ss));
             }
         }
+        return NF_OK;
+    };
+    SideStream side(s);  // joined into s before the scratch buffers are released
+    if (nseg > 0) {
+        NF_CUDA_TRY(side.start());
+        NF_TRY(recompute(nseg - 1, stages + (size_t)((nseg - 1) & 1) * seg_elems, side.side));
+        NF_CUDA_TRY(cudaEventRecord(side.rec[(nseg - 1) & 1], side.side));
+    }
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int cnt = std::min(C, nsteps - seg * C);
+        const int bufi = seg & 1;
+        // the next segment back is recomputed on the side stream while this one is reversed;
+        // its buffer was last read by the reverse pass of segment seg + 1
+        if (seg >= 1) {
+            if (seg + 1 < nseg) NF_CUDA_TRY(cudaStreamWaitEvent(side.side, side.rev[(seg + 1) & 1], 0));
+            NF_TRY(recompute(seg - 1, stages + (size_t)((seg - 1) & 1) * seg_elems, side.side));
+            NF_CUDA_TRY(cudaEventRecord(side.rec[(seg - 1) & 1], side.side));
+        }
+        NF_CUDA_TRY(cudaStreamWaitEvent(s, side.rec[bufi], 0));
+        float *const segst = stages + (size_t)bufi * seg_elems;
         // ---- reverse through the segment
-        adj_prep_kernel<<<eg, T, 0, s>>>(lam, stages + ((size_t)(cnt - 1) * 4 + 3) * BN, op->q, beta, theta, n,
+        adj_prep_kernel<<<eg, T, 0, s>>>(lam, segst + ((size_t)(cnt - 1) * 4 + 3) * BN, op->q, beta, theta, n,
                                          n_pad, B, (float)(dt / 6.0), vg);
         NF_CUDA_TRY(cudaGetLastError());
         for (int j = cnt - 1; j >= 0; --j) {
@@ -228,9 +285,9 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
                 ea.n_pad = n_pad;
                 ea.B = B;
                 ea.stg = stg;
-                ea.Ucur = stages + ((size_t)j * 4 + stg) * BN;
-                ea.Uprev = (stg > 0) ? stages + ((size_t)j * 4 + stg - 1) * BN
-                                     : (j > 0 ? stages + ((size_t)(j - 1) * 4 + 3) * BN : nullptr);
+                ea.Ucur = segst + ((size_t)j * 4 + stg) * BN;
+                ea.Uprev = (stg > 0) ? segst + ((size_t)j * 4 + stg - 1) * BN
+                                     : (j > 0 ? segst + ((size_t)(j - 1) * 4 + 3) * BN : nullptr);
                 ea.lam = lam;
                 ea.acc = acc;
                 ea.vg = vg;
@@ -245,6 +302,7 @@ extern "C" nf_status nf_adjoint(nf_operator *op, const float *ckpt, int C, int B
                 NF_CUDA_TRY(cudaGetLastError());
             }
         }
+        NF_CUDA_TRY(cudaEventRecord(side.rev[bufi], s));  // segst may now be overwritten
     }
     NF_CUDA_TRY(cudaMemcpyAsync(grad_u0, lam, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s));
     adj_finish_kernel<<<(unsigned)ceil_div(4 * B, 256), 256, 0, s>>>(gk, 4 * B, grad_kernel);
