@@ -137,7 +137,7 @@ struct StreamScratch {
 // while the previous segment is reversed on the caller's stream.  Events: fork, join, and per
 // stage buffer "recomputed" and "reversed".  The destructor joins the side stream back into
 // the caller's stream (on every return path, before the scratch buffers are released), so
-// the call stays stream-ordered, and capturable, as a whole.
+// the call stays stream-ordered on the caller's stream as a whole.
 struct SideStream {
     cudaStream_t main, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, rec[2] = {}, rev[2] = {};
