@@ -433,7 +433,10 @@ NF_API nf_status nf_field_advance(nf_operator *op, const nf_model *model, int in
  *   ckpt      checkpoints written by nf_rk4_advance with the same arguments
  *   grad_u0   B x n FP32   output dL/du_0
  *   grad_kernel B x 4 FP32 output dL/d(A1, s1, A2, s2), per trajectory
- * Stages are recomputed segment by segment from the checkpoints.  The transposed pair
+ * Stages are recomputed segment by segment from the checkpoints, on an internal stream
+ * forked from `stream` and joined back into it before the call returns (the work stays
+ * ordered on `stream`; scratch memory is allocated stream-ordered on it and released at
+ * the end, so the call is not for use inside a stream capture).  The transposed pair
  * sum uses the symmetry of the radial kernel (W^T = W).  A manufactured forcing on the
  * sphere enters as given (its eigenvalues are inputs, not functions of the kernel
  * parameters here).
