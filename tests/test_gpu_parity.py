@@ -260,6 +260,33 @@ def test_rk4_flat_workload_full(nf, path):
     assert rel_l2(got, want) < REL_L2
 
 
+@pytest.mark.parametrize("n,nsteps,C", [(1, 3, 1), (7, 5, 2), (1500, 30, 7), (4000, 12, 5), (8192, 6, 3), (8193, 6, 3)])
+def test_rk4_small_sets_checkpoints(nf, n, nsteps, C):
+    """Small node sets (1 and 7 nodes in a padded block, up to one past 8,192) on the
+    automatic and the packed schedule: trajectory and every checkpoint against the oracle,
+    and the two schedules' checkpoints against each other."""
+    rng = np.random.default_rng(n + 17)
+    X = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    q = rng.uniform(0.5, 1.5, n).astype(np.float32) / max(n, 1) * 8.0
+    u0 = rng.normal(0.3, 0.4, size=(1, n)).astype(np.float32)
+    kern = (1.0, 0.15, 0.5, 0.3)
+    dt = 0.05
+    want = oracle.rk4(f32(X), f32(q), f32(u0), f32(kern), f32([20.0]), f32([0.2]), 0.0, dt, nsteps)
+    res = {}
+    for sched in (nf.MF_AUTO, nf.MF_PACKED):
+        op = _op(nf, X, q, kern, 0).mf_schedule(sched)
+        u = dev(u0, torch.float32)
+        ck = torch.zeros((nsteps // C + 1, 1, n), dtype=torch.float32, device="cuda")
+        nf.nf_rk4_advance(op, u, 0.0, dt, nsteps, 20.0, 0.2, ckpt=ck, C_every=C)
+        op.check()
+        res[sched] = (u.cpu().numpy(), ck.cpu().numpy())
+        assert rel_l2(res[sched][0], want) < REL_L2
+    for c in range(1, nsteps // C + 1):
+        wc = oracle.rk4(f32(X), f32(q), f32(u0), f32(kern), f32([20.0]), f32([0.2]), 0.0, dt, c * C)
+        assert rel_l2(res[nf.MF_AUTO][1][c], wc) < REL_L2
+        assert rel_l2(res[nf.MF_AUTO][1][c], res[nf.MF_PACKED][1][c]) < REL_L2
+
+
 def test_rk4_sphere_manufactured_forcing(nf):
     wl = W.sphere(3000)
     st = oracle.knn(wl.ns.nodes, wl.ns.tris, wl.k)
