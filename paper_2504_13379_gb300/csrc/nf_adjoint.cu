@@ -58,8 +58,7 @@ __global__ void adj_epilogue_kernel(AdjEpiArgs a) {
     if (idx >= (int64_t)a.B * a.n) return;
     const int b = (int)(idx / a.n);
     const int64_t i = idx - (int64_t)b * a.n;
-    float Wnu = 0.f;
-    for (int sp = 0; sp < a.slots; ++sp) Wnu += a.wpart[((int64_t)sp * a.B + b) * a.n_pad + i];
+    const float Wnu = sum_slots(a.wpart + (int64_t)b * a.n_pad + i, (int64_t)a.B * a.n_pad, a.slots);
     const int64_t vi = (int64_t)b * a.n_pad + i;
     const float nu = a.vg[vi].x;
     const float bb = a.beta[b], th = a.theta[b];

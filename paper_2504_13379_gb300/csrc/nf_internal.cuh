@@ -146,6 +146,24 @@ struct CInt {
     __device__ constexpr operator int() const { return V; }
 };
 
+// Sum of base[k * stride] over k = 0 .. count - 1, added in ascending k.  The loads are
+// issued eight at a time before their adds (the order of the adds, hence the result, is that
+// of the plain loop), so each thread keeps several slot reads in flight.  base must not be
+// written by the calling kernel (read-only cache path).
+__device__ __forceinline__ float sum_slots(const float *__restrict__ base, int64_t stride, int count) {
+    float s = 0.f;
+    int k = 0;
+    for (; k + 8 <= count; k += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ldg(base + (int64_t)(k + j) * stride);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += v[j];
+    }
+    for (; k < count; ++k) s += __ldg(base + (int64_t)k * stride);
+    return s;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -2008,8 +2008,7 @@ __global__ void reduce_I_kernel(const float *__restrict__ partial, int splits, i
     if (idx >= (int64_t)B * n) return;
     const int b = (int)(idx / n);
     const int64_t i = idx - (int64_t)b * n;
-    float acc = 0.f;
-    for (int sp = 0; sp < splits; ++sp) acc += partial[((int64_t)sp * B + b) * n_pad + i];
+    const float acc = sum_slots(partial + (int64_t)b * n_pad + i, (int64_t)B * n_pad, splits);
     I[idx] = rs ? acc * rs[i] : acc;
 }
 
@@ -2118,8 +2117,7 @@ __global__ void rk4_stage_kernel(StageKArgs a) {
     if (idx < (int64_t)a.B * a.n) {
         const int b = (int)(idx / a.n);
         const int64_t i = idx - (int64_t)b * a.n;
-        float I = 0.f;
-        for (int sp = 0; sp < a.splits; ++sp) I += a.partial[((int64_t)sp * a.B + b) * a.n_pad + i];
+        float I = sum_slots(a.partial + (int64_t)b * a.n_pad + i, (int64_t)a.B * a.n_pad, a.splits);
         if (a.rs) I *= a.rs[i];
         const double cs = (a.stage == 1) ? 0.0 : (a.stage == 4 ? 1.0 : 0.5);
         const double ts = *a.t0 + (double)step * a.dt + cs * a.dt;

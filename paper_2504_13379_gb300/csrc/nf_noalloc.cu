@@ -91,8 +91,7 @@ __global__ void noalloc_reduce_kernel(const float *__restrict__ partial, int spl
         I[i] = __int_as_float(0x7fc00000);
         return;
     }
-    float acc = 0.f;
-    for (int sp = 0; sp < splits; ++sp) acc += partial[(int64_t)sp * n_pad + i];
+    const float acc = sum_slots(partial + i, n_pad, splits);
     I[i] = acc;
 }
 
