@@ -105,3 +105,25 @@ def test_autograd_function_matches_adjoint_and_oracle(nf):
     gk = kp.grad.numpy()
     want = gk_o.sum(0)
     np.testing.assert_allclose(gk, want, rtol=1e-4, atol=1e-6 * np.abs(want).max())
+
+
+def test_adjoint_repeatable_across_segments(nf):
+    """nf_adjoint recomputes checkpoint segments on a second stream while reversing the
+    previous one, reusing two stage buffers.  Every kernel sums in a fixed order, so two
+    calls on the same inputs must agree bit for bit (a race on a reused buffer would not)."""
+    ns = nodesets.torus_lattice(3000, seed=8)
+    n = ns.n
+    X = ns.nodes.astype(np.float32)
+    q = np.full(n, ns.area / n, dtype=np.float32)
+    u0 = nodesets.spiral_bumps_u0(ns, count=4)[None, :].astype(np.float32)
+    nsteps, C, dt = 17, 3, 0.02  # six segments, the last one short
+    op = nf.Operator(dev(X), dev(q), M4, 0)
+    u = dev(u0)
+    ck = torch.zeros((nsteps // C + 1, 1, n), dtype=torch.float32, device="cuda")
+    nf.nf_rk4_advance(op, u, 0.0, dt, nsteps, 20.0, 0.2, ckpt=ck, C_every=C)
+    lamT = 2.0 * (u - 0.9 * dev(u0))
+    out = [nf.nf_adjoint(op, ck, C, 0.0, dt, nsteps, 20.0, 0.2, lamT) for _ in range(2)]
+    op.check()
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    assert torch.isfinite(out[0][0]).all() and torch.isfinite(out[0][1]).all()
